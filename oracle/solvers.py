@@ -1,0 +1,187 @@
+"""Krylov solvers and the block preconditioner P_CH.
+
+TEST INFRASTRUCTURE (see ``oracle/__init__``).
+
+* ``pcg_jacobi``  - conjugate gradients with the diagonal (Jacobi) preconditioner,
+  the inner solver of every preconditioner step (Section 6, Table 2: "PCG",
+  preconditioner "diag", relative tolerance 1e-3).  Reading: zero start,
+  stop when the unpreconditioned residual satisfies ||r||_2 <= rtol ||b||_2.
+* ``fgmres``      - flexible GMRES with right preconditioning (Section 4: the
+  system A P^{-1} (P x) = b; Saad 1993), restart 30 and modified Gram-Schmidt
+  (Section 6).  Reading: zero initial guess; Givens rotations on the Hessenberg
+  matrix; after each cycle the true residual b - A x is recomputed and the
+  solve stops once ||b - A x||_2 <= tol ||b||_2.
+* ``PCH``         - the block preconditioner of Eq. (4.1) with the Cahn-Hilliard
+  approximation S_CH of the Schur complement (Section 4.2), applied in the
+  steps (1), (2), (3.1), (3.2), (4), (5).
+
+Readings of garbled or silent passages (each applies to ``PCH.apply``):
+
+* Step (2) prints ``b_1 - tau K y_1`` on its right-hand side; the forward
+  substitution with the lower factor of Eq. (4.1) needs ``b_1 - tau K y_0``,
+  which is what is used.
+* The preconditioner is derived for gamma = 1 (Section 4).  In a Rosenbrock
+  stage the (psi, psi) block is M/gamma, so the second block row is scaled by
+  gamma: P is built with tau_e = gamma * tau, delta = sqrt(tau_e), and applied to
+  (v0, gamma * v1, v2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class PCGResult:
+    x: np.ndarray
+    iterations: int
+    converged: bool
+
+
+def pcg_jacobi(A: sp.csr_matrix, b: np.ndarray, rtol: float, maxit: int) -> PCGResult:
+    """Jacobi-preconditioned CG for SPD A from x0 = 0."""
+    dinv = 1.0 / A.diagonal()
+    x = np.zeros_like(b)
+    bnorm = math.sqrt(float(b @ b))
+    if bnorm == 0.0:
+        return PCGResult(x, 0, True)
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    for it in range(1, maxit + 1):
+        q = A @ p
+        alpha = rz / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        if math.sqrt(float(r @ r)) <= rtol * bnorm:
+            return PCGResult(x, it, True)
+        z = dinv * r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return PCGResult(x, maxit, False)
+
+
+@dataclass
+class FGMRESStats:
+    outer_iterations: int = 0
+    restarts: int = 0
+    rel_residual: float = float("nan")
+    converged: bool = False
+    history: list = field(default_factory=list)   # Givens residual estimates / ||b||
+
+
+def fgmres(apply_A, b: np.ndarray, apply_Pinv, tol: float, restart: int = 30,
+           max_outer: int = 1000) -> tuple[np.ndarray, FGMRESStats]:
+    """Right-preconditioned flexible GMRES(restart) with modified Gram-Schmidt."""
+    st = FGMRESStats()
+    x = np.zeros_like(b)
+    bnorm = math.sqrt(float(b @ b))
+    if bnorm == 0.0:
+        st.rel_residual, st.converged = 0.0, True
+        return x, st
+    while True:
+        r = b - apply_A(x)
+        beta = math.sqrt(float(r @ r))
+        st.rel_residual = beta / bnorm
+        if beta <= tol * bnorm:
+            st.converged = True
+            return x, st
+        if st.outer_iterations >= max_outer:
+            return x, st
+        m = restart
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m))
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            z = apply_Pinv(V[j])
+            Z.append(z)
+            w = apply_A(z)
+            for i in range(j + 1):            # modified Gram-Schmidt
+                H[i, j] = float(w @ V[i])
+                w = w - H[i, j] * V[i]
+            hnext = math.sqrt(float(w @ w))
+            H[j + 1, j] = hnext
+            for i in range(j):                # previous Givens rotations on column j
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den
+            sn[j] = H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            st.outer_iterations += 1
+            k = j + 1
+            st.history.append(abs(g[j + 1]) / bnorm)
+            if abs(g[j + 1]) <= tol * bnorm or hnext == 0.0 or st.outer_iterations >= max_outer:
+                break
+            V.append(w / hnext)
+        y = np.zeros(k)                       # back substitution with the rotated H
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        for i in range(k):
+            x = x + y[i] * Z[i]
+        st.restarts += 1
+
+
+@dataclass
+class InnerLog:
+    calls: int = 0
+    iterations: int = 0
+    per_call: list = field(default_factory=list)
+
+
+class PCH:
+    """Block preconditioner P(S_CH) (Eq. 4.1, Section 4.2) for one Rosenbrock stage matrix.
+
+    ``inner`` chooses the SPD solves: "pcg" (Jacobi-PCG, rtol 1e-3 by default, as
+    in Table 2) or "exact" (sparse direct solves; used by the spectral tests).
+    """
+
+    def __init__(self, M, K, tau: float, gamma: float, inner: str = "pcg",
+                 inner_rtol: float = 1e-3, max_inner: int = 10000):
+        self.M, self.K = M.tocsr(), K.tocsr()
+        self.gamma = gamma
+        self.tau_e = gamma * tau
+        self.delta = math.sqrt(self.tau_e)
+        self.MdK = (self.M + self.delta * self.K).tocsr()            # step (2)
+        self.MsK = (self.M + math.sqrt(self.delta) * self.K).tocsr() # steps (3.1), (3.2)
+        self.inner, self.inner_rtol, self.max_inner = inner, inner_rtol, max_inner
+        self.log = InnerLog()
+        self.n = M.shape[0]
+        if inner == "exact":
+            import scipy.sparse.linalg as spla
+            self._lu = {id(A): spla.splu(A.tocsc()) for A in (self.M, self.MdK, self.MsK)}
+
+    def _solve(self, A, b):
+        if self.inner == "exact":
+            return self._lu[id(A)].solve(b)
+        res = pcg_jacobi(A, b, self.inner_rtol, self.max_inner)
+        self.log.calls += 1
+        self.log.iterations += res.iterations
+        self.log.per_call.append(res.iterations)
+        return res.x
+
+    def apply(self, v: np.ndarray) -> np.ndarray:
+        n = self.n
+        v0, v1, v2 = v[:n], v[n:2 * n], v[2 * n:]
+        y0 = self._solve(self.M, v0)                                       # (1)  M y0 = v0
+        y1 = self._solve(self.MdK, self.gamma * v1 - self.tau_e * (self.K @ y0))  # (2)
+        w = self._solve(self.MsK, self.M @ y1)                             # (3.1)
+        x1 = self._solve(self.MsK, self.M @ w)                             # (3.2)
+        x0 = y0 + (y1 - x1) / self.delta                                   # (4)
+        x2 = self._solve(self.M, v2 - self.K @ x1)                         # (5)
+        return np.concatenate([x0, x1, x2])
