@@ -1,0 +1,184 @@
+/*
+ * pfc.h - C ABI of the GB300 (sm_103a) PFC stage solver.
+ *
+ * The library solves the linear systems of the Ros3Pw Rosenbrock stages of the
+ * P2 finite-element phase-field-crystal (PFC2, H^-1 gradient flow) equation of
+ * Praetorius & Voigt, "Development and Analysis of a Block-Preconditioner for
+ * the Phase-Field Crystal Equation" (arXiv:1501.06852), with FGMRES(restart)
+ * around the approximate-factorisation block preconditioner P_CH (Eq. 4.1 with
+ * the Cahn-Hilliard Schur approximation of Section 4.2), whose steps are
+ * Jacobi-PCG solves with M, M + delta K and M + sqrt(delta) K.
+ *
+ * Conventions shared by every entry point
+ * - Unknowns per field: n = (2 side + 1)^dim P2 dofs of a structured mesh of
+ *   [0, length]^dim (2D: each square cut into 2 triangles along the diagonal
+ *   from (i, j) to (i+1, j+1); 3D: each cube cut into the 6 Kuhn tetrahedra).
+ *   Dofs are numbered lexicographically on the half-spacing lattice, x fastest.
+ * - A state or stage vector has 3n doubles: [mu (n) | psi (n) | omega (n)]
+ *   (the unknowns x = (mu, psi, omega) of Section 3).
+ * - Every vector argument is a DEVICE pointer (cudaMalloc'd or from a framework
+ *   allocator) to float64 data owned by the caller; the library never frees it.
+ *   Pointers must stay valid until the call returns (the calls that read back a
+ *   scalar synchronise the context stream before returning).
+ * - All work is enqueued on the CUDA stream given to pfc_setup_mesh.
+ * - No call aborts.  Errors return a status; pfc_last_error describes the most
+ *   recent one.  After PFC_ERR_CUDA the context must be destroyed.
+ * - A context is not thread safe; distinct contexts are independent.
+ */
+#ifndef PFC_H
+#define PFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfc_ctx pfc_ctx;
+
+typedef enum {
+  PFC_OK = 0,
+  PFC_ERR_INVALID = 1,        /* bad argument or call order */
+  PFC_ERR_OOM = 2,            /* device allocation failed */
+  PFC_ERR_CUDA = 3,           /* CUDA runtime error; context unusable */
+  PFC_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; outputs hold the last iterate */
+  PFC_ERR_NONFINITE = 5,      /* NaN/Inf met in a reduction */
+  PFC_ERR_TIMEOUT = 6         /* a device-side grid barrier gave up waiting */
+} pfc_status;
+
+/* Precision of the inner preconditioner solves (the outer FGMRES, its residuals,
+ * Arnoldi/Givens and step control are always float64). */
+typedef enum {
+  PFC_PREC_FP64 = 0,          /* inner PCG in float64 */
+  PFC_PREC_FP32 = 1,          /* inner PCG with float32 matrix values and vectors */
+  PFC_PREC_FP16 = 2           /* float16 matrix values, float32 vectors and accumulation */
+} pfc_precision;
+
+typedef struct {
+  double r;           /* model parameter r of Eq. (2.1) */
+  double outer_tol;   /* FGMRES stop: ||b - A^R y||_2 <= outer_tol ||b||_2 */
+  double inner_rtol;  /* PCG stop: ||r||_2 <= inner_rtol ||rhs||_2 (Table 2: 1e-3) */
+  int restart;        /* FGMRES restart length (Section 6: 30); 1..40 */
+  int max_outer;      /* cap on FGMRES iterations per stage solve */
+  int max_inner;      /* cap on PCG iterations per inner solve */
+  int precision;      /* pfc_precision */
+  double step_atol;   /* step-size control tolerances (1e-3, 1e-3) */
+  double step_rtol;
+  double tau_max;     /* upper bound for the next time-step width */
+  int blocks_per_sm;  /* persistent-kernel residency; 0 = as many as fit */
+} pfc_options;
+
+typedef struct {
+  int outer_its;        /* FGMRES iterations */
+  int restarts;         /* completed restart cycles */
+  long long inner_its;  /* total PCG iterations over all preconditioner applications */
+  int inner_calls;      /* number of PCG solves */
+  int inner_capped;     /* PCG solves that hit max_inner */
+  double rel_residual;  /* final true ||b - A^R y||_2 / ||b||_2, recomputed in float64 */
+  int status;           /* pfc_status of this solve */
+} pfc_solve_stats;
+
+/* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
+ * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
+ * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0. */
+void pfc_default_options(pfc_options* opt);
+
+/* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the
+ * constant M and K (Section 3, the matrices below Eq. 3.4).  dim is 2 or 3,
+ * side >= 1, length > 0.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns all device memory of the instance.  On failure
+ * *out may still receive a context that holds only the error text: read it with
+ * pfc_last_error and release it with pfc_destroy. */
+pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length,
+                          const pfc_options* opt, void* cuda_stream);
+
+/* Dofs per field n of a set-up context (0 for NULL). */
+int64_t pfc_num_dofs(const pfc_ctx* ctx);
+
+/* Device bytes a context with these sizes would hold (for admission control). */
+size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt);
+
+/* Per-step assembly at the state x^k (3n, device): the (mu, psi) block
+ * A01 = -(1+r) M + 2 K + N(psi^k), N(psi)_ij = (-3 psi^2 phi_j, phi_i)
+ * (Eq. 3.12 with K_+ = K, F = 0 for PFC2), and for the step width tau the
+ * inner matrices M + delta K and M + sqrt(delta) K with delta = sqrt(gamma tau)
+ * and their Jacobi diagonals (Section 4, Table 2).  Must precede the stage
+ * calls; the matrices stay until the next pfc_assemble. */
+pfc_status pfc_assemble(pfc_ctx* ctx, const double* state, double tau);
+
+/* Right-hand side b_i^R of Eq. (3.12) for stage i = nprev (0, 1 or 2) at the
+ * stage value x_i (3n, device):
+ *   b0 = -M mu_i + (1+r) M psi_i - 2 K psi_i - K omega_i + (psi_i^3, phi)
+ *   b1 = -tau K mu_i + sum_{j<i} c_ij M dpsi_j
+ *   b2 = -M omega_i - K psi_i
+ * y_prev holds the nprev previous stage increments back to back (nprev x 3n,
+ * device; may be NULL when nprev == 0); c_ij are the Ros3Pw coefficients of
+ * Table 1.  Writes b (3n, device). */
+pfc_status pfc_stage_rhs(pfc_ctx* ctx, int nprev, const double* x_stage,
+                         const double* y_prev, double* b);
+
+/* Solves A^R y = b (Eq. 3.12) for the last assembled psi^k and tau with
+ * FGMRES(restart), modified Gram-Schmidt and right preconditioner P_CH
+ * (Sections 4 and 6), zero initial guess.  b, y: 3n doubles on the device.
+ * Synchronises the stream to fill *stats (may be NULL).  Returns
+ * PFC_ERR_NOT_CONVERGED with the last iterate in y when max_outer is hit. */
+pfc_status pfc_stage_solve(pfc_ctx* ctx, const double* b, double* y,
+                           pfc_solve_stats* stats);
+
+/* One attempted Ros3Pw step (Eq. 3.6, 3.7, 3.12): assembly at the state,
+ * three stage solves, x^{k+1} = x^k + sum m_j y_j and the embedded error
+ * estimate err = RMS_j( e_j / (atol + rtol max(|psi^k_j|, |psi^{k+1}_j|)) ) with
+ * e = sum (mhat_j - m_j) dpsi_j.  If err <= 1 the step is accepted and state
+ * (3n, device, in/out) is overwritten with x^{k+1}; otherwise state is left
+ * unchanged.  *tau (in/out) becomes tau * min(5, max(0.2, 0.9 err^(-1/3))),
+ * capped at tau_max.  stats (may be NULL) receives 3 entries.  One host
+ * synchronisation per call. */
+pfc_status pfc_step(pfc_ctx* ctx, double* state, double* tau, int* accepted,
+                    double* err, pfc_solve_stats* stats);
+
+/* Consistent initial state from psi0 (n doubles, device): solves
+ * M omega0 = -K psi0 and M mu0 = (psi0^3, phi) + (1+r) M psi0 - 2 K psi0 - K omega0
+ * (the algebraic rows of Eq. 2.4) with float64 Jacobi-PCG to 1e-14 and writes
+ * state = [mu0 | psi0 | omega0] (3n, device). */
+pfc_status pfc_init_state(pfc_ctx* ctx, const double* psi0, double* state);
+
+/* Operators for checking the path piece by piece (all after pfc_assemble):
+ * y = op(x) with op = PFC_OP_M, PFC_OP_K, PFC_OP_A01 (n -> n), PFC_OP_AR (the
+ * stage matrix A^R, 3n -> 3n) or PFC_OP_PCH (one application of the
+ * preconditioner, 3n -> 3n, with the context's inner precision). */
+enum { PFC_OP_M = 0, PFC_OP_K = 1, PFC_OP_A01 = 2, PFC_OP_AR = 3, PFC_OP_PCH = 4 };
+pfc_status pfc_apply(pfc_ctx* ctx, int op, const double* x, double* y);
+
+/* One Jacobi-PCG solve (Table 2) A x = b with A = M (which = 0),
+ * M + delta K (1) or M + sqrt(delta) K (2), zero start, relative tolerance
+ * rtol, in the context's inner precision.  b, x: n doubles on the device.
+ * *iterations (may be NULL) receives the iteration count. */
+pfc_status pfc_pcg(pfc_ctx* ctx, int which, const double* b, double* x, double rtol,
+                   int* iterations);
+
+/* Failure-detection self-test: launches a PCG whose grid barriers wait for one
+ * block more than the grid holds, so every wait runs out after limit_seconds
+ * (0 < limit <= 10).  The kernel sets its timeout bit and returns; the context
+ * stays usable.  Returns PFC_ERR_TIMEOUT when the bounded wait works.  (Not a
+ * step of the paper's method: it checks the persistent kernel's bounded waits.) */
+pfc_status pfc_selftest_barrier_timeout(pfc_ctx* ctx, double limit_seconds);
+
+/* Host-only inspection of the mesh/pattern builder (no GPU needed):
+ * out4 = {n, nnz of one block, stored SELL slots, elements}. */
+pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
+
+/* Text of the most recent error of ctx ("" if none; static text for NULL). */
+const char* pfc_last_error(const pfc_ctx* ctx);
+
+/* Name of a status code. */
+const char* pfc_status_string(int status);
+
+/* Frees every device buffer of ctx.  NULL is ignored. */
+void pfc_destroy(pfc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFC_H */

@@ -1,0 +1,245 @@
+"""GB300 (sm_103a) solver for the Rosenbrock stages of the P2 phase-field-crystal equation.
+
+Thin Python binding over the C ABI of ``libpfc.so`` (declared in ``include/pfc.h``):
+argument marshalling only.  Every step of the method (assembly, stage
+right-hand side, FGMRES with the P_CH block preconditioner, Jacobi-PCG, the
+Ros3Pw step and its error estimate) runs in the library's CUDA kernels.
+PyTorch provides device memory and the CUDA stream.
+
+Importing the package loads the library; a missing library is an error (there
+is no fallback): build it with ``python -m paper_1501_06852_gb300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+from .build import LIB as _LIB_PATH
+
+__all__ = ["PFCSolver", "PFCError", "SolveStats", "lib", "critical_tau", "ROS3PW_GAMMA",
+           "OP_M", "OP_K", "OP_A01", "OP_AR", "OP_PCH", "PRECISIONS"]
+
+OP_M, OP_K, OP_A01, OP_AR, OP_PCH = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
+ROS3PW_GAMMA = 0.78867513459481287
+STATUS = {0: "PFC_OK", 1: "PFC_ERR_INVALID", 2: "PFC_ERR_OOM", 3: "PFC_ERR_CUDA",
+          4: "PFC_ERR_NOT_CONVERGED", 5: "PFC_ERR_NONFINITE", 6: "PFC_ERR_TIMEOUT"}
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("outer_tol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("precision", ctypes.c_int), ("step_atol", ctypes.c_double), ("step_rtol", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("blocks_per_sm", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("outer_its", ctypes.c_int), ("restarts", ctypes.c_int), ("inner_its", ctypes.c_longlong),
+                ("inner_calls", ctypes.c_int), ("inner_capped", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_1501_06852_gb300.build`")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, None
+    sig = {
+        "pfc_default_options": (V, [ctypes.POINTER(_Options)]),
+        "pfc_setup_mesh": (I, [ctypes.POINTER(P), I, I, D, ctypes.POINTER(_Options), P]),
+        "pfc_num_dofs": (ctypes.c_int64, [P]),
+        "pfc_footprint_bytes": (ctypes.c_size_t, [I, I, ctypes.POINTER(_Options)]),
+        "pfc_assemble": (I, [P, P, D]),
+        "pfc_stage_rhs": (I, [P, I, P, P, P]),
+        "pfc_stage_solve": (I, [P, P, P, ctypes.POINTER(_Stats)]),
+        "pfc_step": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
+        "pfc_init_state": (I, [P, P, P]),
+        "pfc_apply": (I, [P, I, P, P]),
+        "pfc_pcg": (I, [P, I, P, P, D, ctypes.POINTER(I)]),
+        "pfc_selftest_barrier_timeout": (I, [P, D]),
+        "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_last_error": (ctypes.c_char_p, [P]),
+        "pfc_status_string": (ctypes.c_char_p, [I]),
+        "pfc_destroy": (V, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+class PFCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class SolveStats:
+    outer_its: int
+    restarts: int
+    inner_its: int
+    inner_calls: int
+    inner_capped: int
+    rel_residual: float
+    status: int
+
+    @classmethod
+    def _from(cls, s: _Stats) -> "SolveStats":
+        return cls(s.outer_its, s.restarts, s.inner_its, s.inner_calls, s.inner_capped, s.rel_residual, s.status)
+
+
+def critical_tau(r: float, psi_bar: float) -> float:
+    """Critical time-step width of the linearised operator (Lemma 3):
+    27 / (2 (sqrt(a) - 1)(sqrt(a) + 2)^2) with a = 1 - 3 r - 9 psi_bar^2; inf if a <= 1."""
+    a = 1.0 - 3.0 * r - 9.0 * psi_bar * psi_bar
+    if a <= 1.0:
+        return math.inf
+    s = math.sqrt(a)
+    return 27.0 / (2.0 * (s - 1.0) * (s + 2.0) ** 2)
+
+
+def default_options() -> dict:
+    o = _Options()
+    lib.pfc_default_options(ctypes.byref(o))
+    return {k: getattr(o, k) for k, _ in _Options._fields_}
+
+
+def host_pattern(dim: int, side: int, length: float = 1.0) -> dict:
+    """Sizes from the host mesh/pattern builder (no GPU needed)."""
+    out = (ctypes.c_int64 * 4)()
+    st = lib.pfc_host_pattern(dim, side, float(length), out)
+    if st != 0:
+        raise PFCError(st, "host_pattern")
+    return {"n": out[0], "nnz": out[1], "nnz_sell": out[2], "elements": out[3]}
+
+
+class PFCSolver:
+    """One PFC simulation instance on the current CUDA device.
+
+    Vectors are float64 CUDA tensors in lexicographic P2 dof order; a state has
+    3n entries [mu | psi | omega].  All work runs on the CUDA stream current at
+    construction (or ``stream``)."""
+
+    def __init__(self, dim: int, side: int, length: float, r: float = -0.4, precision: str = "fp64",
+                 outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
+                 max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
+                 tau_max: float = 1e9, blocks_per_sm: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise PFCError(3, "no CUDA device: the PFC solver runs only on the GPU")
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        o = _Options()
+        lib.pfc_default_options(ctypes.byref(o))
+        o.r, o.outer_tol, o.inner_rtol = r, outer_tol, inner_rtol
+        o.restart, o.max_outer, o.max_inner = restart, max_outer, max_inner
+        o.precision = PRECISIONS[precision]
+        o.step_atol, o.step_rtol, o.tau_max, o.blocks_per_sm = step_atol, step_rtol, tau_max, blocks_per_sm
+        self.options = o
+        self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
+        h = ctypes.c_void_p()
+        st = lib.pfc_setup_mesh(ctypes.byref(h), dim, side, float(length), ctypes.byref(o),
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            msg = lib.pfc_last_error(h).decode() if h.value else ""
+            if h.value:
+                lib.pfc_destroy(h)
+            raise PFCError(st, msg)
+        self._h = h
+        self.n = int(lib.pfc_num_dofs(h))
+
+    # --- marshalling helpers ------------------------------------------------
+    def _vec(self, t, count: int, name: str):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.device != self.device:
+            raise TypeError(f"{name} must be a float64 tensor on {self.device}")
+        if not t.is_contiguous() or t.numel() != count:
+            raise ValueError(f"{name} must be contiguous with {count} entries")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _new(self, count: int):
+        return self._torch.empty(count, dtype=self._torch.float64, device=self.device)
+
+    def _check(self, st: int):
+        if st != 0:
+            raise PFCError(st, lib.pfc_last_error(self._h).decode())
+
+    # --- API ------------------------------------------------------------------
+    def init_state(self, psi0):
+        state = self._new(3 * self.n)
+        self._check(lib.pfc_init_state(self._h, self._vec(psi0, self.n, "psi0"), self._vec(state, 3 * self.n, "state")))
+        return state
+
+    def assemble(self, state, tau: float):
+        self._check(lib.pfc_assemble(self._h, self._vec(state, 3 * self.n, "state"), float(tau)))
+
+    def stage_rhs(self, nprev: int, x_stage, y_prev=None):
+        b = self._new(3 * self.n)
+        yp = self._vec(y_prev, nprev * 3 * self.n, "y_prev") if nprev > 0 else None
+        self._check(lib.pfc_stage_rhs(self._h, nprev, self._vec(x_stage, 3 * self.n, "x_stage"), yp,
+                                      self._vec(b, 3 * self.n, "b")))
+        return b
+
+    def stage_solve(self, b, y=None, check: bool = True):
+        y = self._new(3 * self.n) if y is None else y
+        s = _Stats()
+        st = lib.pfc_stage_solve(self._h, self._vec(b, 3 * self.n, "b"), self._vec(y, 3 * self.n, "y"),
+                                 ctypes.byref(s))
+        if check:
+            self._check(st)
+        return y, SolveStats._from(s)
+
+    def step(self, state, tau: float, check: bool = True):
+        """One Ros3Pw step attempt; state (device, 3n) is updated in place if accepted.
+        Returns (accepted, err, tau_next, [SolveStats] * 3)."""
+        t = ctypes.c_double(tau)
+        acc = ctypes.c_int(0)
+        err = ctypes.c_double(0.0)
+        stats = (_Stats * 3)()
+        st = lib.pfc_step(self._h, self._vec(state, 3 * self.n, "state"), ctypes.byref(t), ctypes.byref(acc),
+                          ctypes.byref(err), stats)
+        if check:
+            self._check(st)
+        return bool(acc.value), err.value, t.value, [SolveStats._from(s) for s in stats]
+
+    def apply(self, op: int, x):
+        m = 3 * self.n if op in (OP_AR, OP_PCH) else self.n
+        y = self._new(m)
+        self._check(lib.pfc_apply(self._h, op, self._vec(x, m, "x"), self._vec(y, m, "y")))
+        return y
+
+    def pcg(self, which: int, b, rtol: float):
+        x = self._new(self.n)
+        its = ctypes.c_int(0)
+        self._check(lib.pfc_pcg(self._h, which, self._vec(b, self.n, "b"), self._vec(x, self.n, "x"), float(rtol),
+                                ctypes.byref(its)))
+        return x, its.value
+
+    def selftest_barrier_timeout(self, limit_seconds: float = 0.2) -> int:
+        return int(lib.pfc_selftest_barrier_timeout(self._h, float(limit_seconds)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.pfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

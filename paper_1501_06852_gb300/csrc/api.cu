@@ -1,0 +1,734 @@
+// C ABI of the PFC stage solver: context set-up, per-step assembly, stage
+// right-hand side, stage solve and the Ros3Pw step (see include/pfc.h).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "device.cuh"
+#include "internal.h"
+#include "launch.h"
+#include "pfc.h"
+
+namespace {
+
+// Ros3Pw in the modified Rosenbrock form (Table 1 of Praetorius & Voigt).  The
+// printed diagonal entries "a22", "a33", "c11", "c22", "c33" are stage-time sums
+// of the standard form; the PFC system is autonomous, so they are unused.
+constexpr double kGamma = 0.78867513459481287;
+constexpr double kA[3][2] = {{0.0, 0.0}, {2.0, 0.0}, {0.633974596215561, 0.0}};
+constexpr double kC[3][2] = {{0.0, 0.0}, {-2.53589838486225, 0.0}, {-1.62740473580836, -0.274519052838329}};
+constexpr double kM[3] = {1.63397459621556, 0.294228634059948, 1.07179676972449};
+constexpr double kMhat[3] = {1.99444650053487, 0.654700538379252, 1.07179676972449};
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+std::mutex g_const_mutex;
+bool g_const_done[2][64] = {};
+
+}  // namespace
+
+struct pfc_ctx {
+  pfc_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int dim = 0, side = 0;
+  double length = 0.0;
+  int n = 0, n_pad = 0, nslices = 0, E = 0, nl = 0, np = 0, ntypes = 0;
+  long long nnz_sell = 0, nnz = 0, ncontrib = 0;
+  int prec = 0;
+  double vol = 0.0;
+  int G = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  // pattern and maps
+  int *slice_ptr = nullptr, *cols = nullptr, *diag = nullptr, *perm = nullptr, *elem = nullptr;
+  int *cptr = nullptr, *cidx = nullptr, *dptr = nullptr, *didx = nullptr, *blk = nullptr;
+  double *mass_tab = nullptr, *stiff_tab = nullptr;
+  // float64 matrices
+  double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
+  double *dM = nullptr, *dMdK = nullptr, *dMsK = nullptr;
+  // inner (float32 / float16) matrices and float32 Jacobi inverses
+  void *iM = nullptr, *iK = nullptr, *iMdK = nullptr, *iMsK = nullptr;
+  float *fdM = nullptr, *fdMdK = nullptr, *fdMsK = nullptr;
+  // vectors in internal order
+  double *xk = nullptr, *xi = nullptr, *ys = nullptr, *bv = nullptr, *xnew = nullptr, *tmp3 = nullptr;
+  double *dvec = nullptr, *lvec = nullptr, *tmpn = nullptr, *ebuf = nullptr;
+  double *V = nullptr, *Z = nullptr;
+  void* ivec = nullptr;
+  // control
+  unsigned* arrive = nullptr;
+  int* errw = nullptr;
+  double2* part = nullptr;
+  pfc::DevStats* stats = nullptr;   // 4 slots
+  double* step_part = nullptr;
+  double* err_scalar = nullptr;
+  // pinned host mirrors
+  pfc::DevStats* h_stats = nullptr;
+  double* h_err = nullptr;
+  int* h_errw = nullptr;
+  bool assembled = false;
+  double tau = 0.0, delta = 0.0;
+  std::string last_error;
+};
+
+namespace {
+
+pfc_status fail(pfc_ctx* c, pfc_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(c, PFC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+size_t inner_elem_bytes(int prec) { return prec == 1 ? 4 : prec == 2 ? 2 : 8; }
+
+pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
+  pfc::SolveArgs a{};
+  a.n_pad = c->n_pad;
+  a.slice_ptr = c->slice_ptr;
+  a.cols = c->cols;
+  a.blk = c->blk;
+  a.Mv = c->Mv;
+  a.Kv = c->Kv;
+  a.Av = c->Av;
+  if (prec == 0) {
+    a.iM = c->Mv;
+    a.iK = c->Kv;
+    a.iMdK = c->MdKv;
+    a.iMsK = c->MsKv;
+    a.dM = c->dM;
+    a.dMdK = c->dMdK;
+    a.dMsK = c->dMsK;
+  } else {
+    a.iM = c->iM;
+    a.iK = c->iK;
+    a.iMdK = c->iMdK;
+    a.iMsK = c->iMsK;
+    a.dM = c->fdM;
+    a.dMdK = c->fdMdK;
+    a.dMsK = c->fdMsK;
+  }
+  a.tau = c->tau;
+  a.gamma = kGamma;
+  a.inv_gamma = 1.0 / kGamma;
+  a.tau_e = kGamma * c->tau;
+  a.inv_delta = c->delta > 0 ? 1.0 / c->delta : 0.0;
+  a.tol = c->opt.outer_tol;
+  a.inner_rtol = c->opt.inner_rtol;
+  a.restart = c->opt.restart;
+  a.max_outer = c->opt.max_outer;
+  a.max_inner = c->opt.max_inner;
+  a.V = c->V;
+  a.Z = c->Z;
+  a.ivec = c->ivec;
+  a.arrive = c->arrive;
+  a.err = c->errw;
+  a.part = c->part;
+  a.stats = c->stats;
+  a.spin_limit_ns = 2000000000ULL;
+  a.barrier_extra = 0;
+  return a;
+}
+
+pfc_status status_from_err(int err) {
+  if (err & pfc::kErrTimeout) return PFC_ERR_TIMEOUT;
+  if (err & pfc::kErrNonfinite) return PFC_ERR_NONFINITE;
+  if (err & pfc::kErrOuterCap) return PFC_ERR_NOT_CONVERGED;
+  return PFC_OK;
+}
+
+// Enqueue one persistent-kernel launch; stats go to c->stats[slot].
+pfc_status run_solver(pfc_ctx* c, pfc::SolveArgs a, int prec, int slot) {
+  a.stats = c->stats + slot;
+  CK(cudaMemsetAsync(c->arrive, 0, sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->errw + slot, 0, sizeof(int), c->stream));
+  CK(cudaMemsetAsync(a.stats, 0, sizeof(pfc::DevStats), c->stream));
+  a.err = c->errw + slot;
+  CK(pfc::launch_solve(prec, c->G, a, c->stream));
+  return PFC_OK;
+}
+
+void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
+  if (!s) return;
+  s->outer_its = d.outer_its;
+  s->restarts = d.restarts;
+  s->inner_its = d.inner_its;
+  s->inner_calls = d.inner_calls;
+  s->inner_capped = d.inner_capped;
+  s->rel_residual = d.rel_residual;
+  s->status = status_from_err(err);
+}
+
+// b_i^R for stage nprev from c->xi (stage value) and the increments c->ys.
+pfc_status stage_rhs_internal(pfc_ctx* c, int nprev) {
+  const int np = c->n_pad;
+  const double c0 = nprev > 0 ? kC[nprev][0] : 0.0, c1 = nprev > 1 ? kC[nprev][1] : 0.0;
+  if (nprev > 0) CK(pfc::launch_combine_field(np, c->ys + np, c0, nprev > 1 ? c->ys + 3 * np + np : nullptr, c1, c->dvec, c->stream));
+  CK(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+  CK(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
+                     nprev > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
+  return PFC_OK;
+}
+
+pfc_status assemble_internal(pfc_ctx* c, double tau) {
+  const int np = c->n_pad;
+  CK(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
+  CK(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
+  c->tau = tau;
+  c->delta = std::sqrt(kGamma * tau);
+  const double sdelta = std::sqrt(c->delta);
+  CK(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
+                            c->stream));
+  CK(pfc::launch_diag_inv(np, c->diag, c->MdKv, c->dMdK, c->prec ? c->fdMdK : nullptr, c->stream));
+  CK(pfc::launch_diag_inv(np, c->diag, c->MsKv, c->dMsK, c->prec ? c->fdMsK : nullptr, c->stream));
+  c->assembled = true;
+  return PFC_OK;
+}
+
+pfc_status check_ctx(pfc_ctx* c) {
+  if (!c) return PFC_ERR_INVALID;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return fail(c, PFC_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+  return PFC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pfc_default_options(pfc_options* o) {
+  if (!o) return;
+  o->r = -0.4;
+  o->outer_tol = 1e-10;
+  o->inner_rtol = 1e-3;
+  o->restart = 30;
+  o->max_outer = 600;
+  o->max_inner = 1000;
+  o->precision = PFC_PREC_FP64;
+  o->step_atol = 1e-3;
+  o->step_rtol = 1e-3;
+  o->tau_max = 1e9;
+  o->blocks_per_sm = 0;
+}
+
+const char* pfc_status_string(int s) {
+  switch (s) {
+    case PFC_OK: return "PFC_OK";
+    case PFC_ERR_INVALID: return "PFC_ERR_INVALID";
+    case PFC_ERR_OOM: return "PFC_ERR_OOM";
+    case PFC_ERR_CUDA: return "PFC_ERR_CUDA";
+    case PFC_ERR_NOT_CONVERGED: return "PFC_ERR_NOT_CONVERGED";
+    case PFC_ERR_NONFINITE: return "PFC_ERR_NONFINITE";
+    case PFC_ERR_TIMEOUT: return "PFC_ERR_TIMEOUT";
+    default: return "PFC_UNKNOWN";
+  }
+}
+
+const char* pfc_last_error(const pfc_ctx* c) {
+  if (!c) return "null context";
+  return c->last_error.c_str();
+}
+
+int64_t pfc_num_dofs(const pfc_ctx* c) { return c ? (int64_t)c->n : 0; }
+
+size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt) {
+  pfc_options o;
+  pfc_default_options(&o);
+  if (opt) o = *opt;
+  if ((dim != 2 && dim != 3) || side < 1) return 0;
+  return pfc::footprint_estimate(dim, side, o.restart, o.precision);
+}
+
+void pfc_destroy(pfc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->arena) cudaFree(c->arena);
+  if (c->h_stats) cudaFreeHost(c->h_stats);
+  delete c;
+}
+
+pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const pfc_options* opt,
+                          void* cuda_stream) {
+  if (!out) return PFC_ERR_INVALID;
+  *out = nullptr;
+  pfc_ctx* c = new (std::nothrow) pfc_ctx();
+  if (!c) return PFC_ERR_OOM;
+  pfc_default_options(&c->opt);
+  if (opt) c->opt = *opt;
+  auto bail = [&](pfc_status st) {
+    if (st != PFC_OK) {
+      *out = c;  // keep the context so that pfc_last_error can be read; caller destroys it
+    }
+    return st;
+  };
+  if ((dim != 2 && dim != 3) || side < 1 || !(length > 0.0))
+    return bail(fail(c, PFC_ERR_INVALID, "dim must be 2 or 3, side >= 1, length > 0"));
+  if (c->opt.restart < 1 || c->opt.restart > pfc::kMaxRestart)
+    return bail(fail(c, PFC_ERR_INVALID, "restart must be in 1..40"));
+  if (c->opt.precision < 0 || c->opt.precision > 2) return bail(fail(c, PFC_ERR_INVALID, "precision must be 0, 1 or 2"));
+  if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
+    return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
+  c->stream = (cudaStream_t)cuda_stream;
+  c->dim = dim;
+  c->side = side;
+  c->length = length;
+  c->prec = c->opt.precision;
+  {
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return bail(fail(c, PFC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e)));
+  }
+
+  pfc::HostSetup S;
+  std::string err;
+  if (!pfc::build_setup(dim, side, length, S, err)) return bail(fail(c, PFC_ERR_INVALID, err));
+  c->n = S.n;
+  c->n_pad = S.n_pad;
+  c->nslices = S.nslices;
+  c->E = S.E;
+  c->nl = S.nl;
+  c->np = S.ref.npairs;
+  c->ntypes = S.ntypes;
+  c->nnz_sell = S.nnz_sell;
+  c->nnz = S.nnz;
+  c->ncontrib = (long long)S.contrib_idx.size();
+  c->vol = S.ref.vol;
+
+  // persistent grid: co-resident blocks, no more blocks than slices
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms < 1)
+    return bail(fail(c, PFC_ERR_CUDA, "cannot query the SM count"));
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+  if (!coop) return bail(fail(c, PFC_ERR_CUDA, "device does not support cooperative launch"));
+  int occ0 = 0, occ1 = 0;
+  if (pfc::solve_occupancy(0, &occ0) != cudaSuccess) return bail(fail(c, PFC_ERR_CUDA, "occupancy query failed"));
+  occ1 = occ0;
+  if (c->prec != 0 && pfc::solve_occupancy(c->prec, &occ1) != cudaSuccess)
+    return bail(fail(c, PFC_ERR_CUDA, "occupancy query failed"));
+  int bps = std::min(occ0, occ1);
+  if (c->opt.blocks_per_sm > 0) bps = std::min(bps, c->opt.blocks_per_sm);
+  if (bps < 1) return bail(fail(c, PFC_ERR_CUDA, "solver kernel does not fit on an SM"));
+  c->G = std::max(1, std::min(sms * bps, c->nslices));
+  std::vector<int> blk(c->G + 1, 0);
+  {
+    const long long total = S.slice_ptr[S.nslices];
+    int s = 0;
+    for (int b = 1; b < c->G; ++b) {
+      const long long target = total * b / c->G;
+      while (s < S.nslices && S.slice_ptr[s] < target) ++s;
+      blk[b] = std::max(s, blk[b - 1]);
+    }
+    blk[c->G] = S.nslices;
+  }
+
+  // ---- device layout (one allocation) ----
+  const size_t np3 = 3 * (size_t)c->n_pad;
+  const size_t ib = inner_elem_bytes(c->prec);
+  Layout L;
+  const size_t o_slice = L.take(sizeof(int) * (S.nslices + 1));
+  const size_t o_cols = L.take(sizeof(int) * S.nnz_sell);
+  const size_t o_diag = L.take(sizeof(int) * S.n_pad);
+  const size_t o_perm = L.take(sizeof(int) * S.n_pad);
+  const size_t o_elem = L.take(sizeof(int) * S.elem_int.size());
+  const size_t o_cptr = L.take(sizeof(int) * S.contrib_ptr.size());
+  const size_t o_cidx = L.take(sizeof(int) * std::max<size_t>(1, S.contrib_idx.size()));
+  const size_t o_dptr = L.take(sizeof(int) * S.dof_ptr.size());
+  const size_t o_didx = L.take(sizeof(int) * std::max<size_t>(1, S.dof_idx.size()));
+  const size_t o_blk = L.take(sizeof(int) * blk.size());
+  const size_t o_mt = L.take(sizeof(double) * S.ref.mass.size());
+  const size_t o_st = L.take(sizeof(double) * S.ref.stiff.size());
+  const size_t vals = sizeof(double) * S.nnz_sell;
+  const size_t o_M = L.take(vals), o_K = L.take(vals), o_A = L.take(vals), o_MdK = L.take(vals), o_MsK = L.take(vals);
+  const size_t o_dM = L.take(sizeof(double) * c->n_pad), o_dMdK = L.take(sizeof(double) * c->n_pad),
+               o_dMsK = L.take(sizeof(double) * c->n_pad);
+  size_t o_iM = 0, o_iK = 0, o_iMdK = 0, o_iMsK = 0, o_f1 = 0, o_f2 = 0, o_f3 = 0;
+  if (c->prec) {
+    o_iM = L.take(ib * S.nnz_sell);
+    o_iK = L.take(ib * S.nnz_sell);
+    o_iMdK = L.take(ib * S.nnz_sell);
+    o_iMsK = L.take(ib * S.nnz_sell);
+    o_f1 = L.take(sizeof(float) * c->n_pad);
+    o_f2 = L.take(sizeof(float) * c->n_pad);
+    o_f3 = L.take(sizeof(float) * c->n_pad);
+  }
+  const size_t vec_begin = L.take(0);
+  const size_t o_xk = L.take(sizeof(double) * np3), o_xi = L.take(sizeof(double) * np3),
+               o_ys = L.take(sizeof(double) * np3 * 3), o_bv = L.take(sizeof(double) * np3),
+               o_xnew = L.take(sizeof(double) * np3), o_tmp3 = L.take(sizeof(double) * np3);
+  const size_t o_dvec = L.take(sizeof(double) * c->n_pad), o_lvec = L.take(sizeof(double) * c->n_pad),
+               o_tmpn = L.take(sizeof(double) * c->n_pad);
+  const size_t o_ebuf = L.take(sizeof(double) * (size_t)c->np * c->E);
+  const size_t o_V = L.take(sizeof(double) * np3 * (c->opt.restart + 1));
+  const size_t o_Z = L.take(sizeof(double) * np3 * c->opt.restart);
+  const size_t o_ivec = L.take(8 * (size_t)c->n_pad * 8);
+  const size_t vec_end = L.take(0);
+  const size_t o_arr = L.take(sizeof(unsigned) * 4);
+  const size_t o_errw = L.take(sizeof(int) * 8);
+  const size_t o_part = L.take(sizeof(double2) * pfc::solve_ring() * c->G);
+  const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);
+  const size_t o_sp = L.take(sizeof(double) * pfc::step_partials());
+  const size_t o_es = L.take(sizeof(double) * 2);
+  c->arena_bytes = L.take(0);
+  {
+    cudaError_t e = cudaMalloc((void**)&c->arena, c->arena_bytes);
+    if (e != cudaSuccess) {
+      c->arena = nullptr;
+      cudaGetLastError();
+      return bail(fail(c, PFC_ERR_OOM, "cudaMalloc of " + std::to_string(c->arena_bytes) + " bytes failed"));
+    }
+  }
+  char* A = c->arena;
+  c->slice_ptr = (int*)(A + o_slice);
+  c->cols = (int*)(A + o_cols);
+  c->diag = (int*)(A + o_diag);
+  c->perm = (int*)(A + o_perm);
+  c->elem = (int*)(A + o_elem);
+  c->cptr = (int*)(A + o_cptr);
+  c->cidx = (int*)(A + o_cidx);
+  c->dptr = (int*)(A + o_dptr);
+  c->didx = (int*)(A + o_didx);
+  c->blk = (int*)(A + o_blk);
+  c->mass_tab = (double*)(A + o_mt);
+  c->stiff_tab = (double*)(A + o_st);
+  c->Mv = (double*)(A + o_M);
+  c->Kv = (double*)(A + o_K);
+  c->Av = (double*)(A + o_A);
+  c->MdKv = (double*)(A + o_MdK);
+  c->MsKv = (double*)(A + o_MsK);
+  c->dM = (double*)(A + o_dM);
+  c->dMdK = (double*)(A + o_dMdK);
+  c->dMsK = (double*)(A + o_dMsK);
+  if (c->prec) {
+    c->iM = A + o_iM;
+    c->iK = A + o_iK;
+    c->iMdK = A + o_iMdK;
+    c->iMsK = A + o_iMsK;
+    c->fdM = (float*)(A + o_f1);
+    c->fdMdK = (float*)(A + o_f2);
+    c->fdMsK = (float*)(A + o_f3);
+  }
+  c->xk = (double*)(A + o_xk);
+  c->xi = (double*)(A + o_xi);
+  c->ys = (double*)(A + o_ys);
+  c->bv = (double*)(A + o_bv);
+  c->xnew = (double*)(A + o_xnew);
+  c->tmp3 = (double*)(A + o_tmp3);
+  c->dvec = (double*)(A + o_dvec);
+  c->lvec = (double*)(A + o_lvec);
+  c->tmpn = (double*)(A + o_tmpn);
+  c->ebuf = (double*)(A + o_ebuf);
+  c->V = (double*)(A + o_V);
+  c->Z = (double*)(A + o_Z);
+  c->ivec = (void*)(A + o_ivec);
+  c->arrive = (unsigned*)(A + o_arr);
+  c->errw = (int*)(A + o_errw);
+  c->part = (double2*)(A + o_part);
+  c->stats = (pfc::DevStats*)(A + o_stats);
+  c->step_part = (double*)(A + o_sp);
+  c->err_scalar = (double*)(A + o_es);
+  {
+    cudaError_t e = cudaMallocHost((void**)&c->h_stats, sizeof(pfc::DevStats) * 4 + sizeof(double) * 2 + sizeof(int) * 8);
+    if (e != cudaSuccess) return bail(fail(c, PFC_ERR_OOM, "cudaMallocHost failed"));
+    c->h_err = (double*)(c->h_stats + 4);
+    c->h_errw = (int*)(c->h_err + 2);
+  }
+
+  // ---- uploads ----
+  std::vector<int> perm_pad(S.n_pad, 0);
+  std::copy(S.perm.begin(), S.perm.end(), perm_pad.begin());
+#define UP(dst, vec) CK_SETUP(cudaMemcpy(dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice))
+#define CK_SETUP(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return bail(fail(c, PFC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  UP(c->slice_ptr, S.slice_ptr);
+  UP(c->cols, S.cols);
+  UP(c->diag, S.diag_pos);
+  UP(c->perm, perm_pad);
+  UP(c->elem, S.elem_int);
+  UP(c->cptr, S.contrib_ptr);
+  if (!S.contrib_idx.empty()) UP(c->cidx, S.contrib_idx);
+  UP(c->dptr, S.dof_ptr);
+  if (!S.dof_idx.empty()) UP(c->didx, S.dof_idx);
+  UP(c->blk, blk);
+  UP(c->mass_tab, S.ref.mass);
+  UP(c->stiff_tab, S.ref.stiff);
+  {
+    std::lock_guard<std::mutex> lk(g_const_mutex);
+    const int di = dim - 2;
+    if (c->device < 0 || c->device >= 64) return bail(fail(c, PFC_ERR_INVALID, "device index out of range"));
+    if (!g_const_done[di][c->device]) {
+      std::vector<double> unit(S.ref.quartic.size());
+      for (size_t q = 0; q < unit.size(); ++q) unit[q] = S.ref.quartic[q] / S.ref.vol;
+      CK_SETUP(pfc::upload_quartic(dim, unit.data(), S.ref.npairs));
+      g_const_done[di][c->device] = true;
+    }
+  }
+  CK_SETUP(cudaMemsetAsync(A + vec_begin, 0, vec_end - vec_begin, c->stream));
+  CK_SETUP(cudaMemsetAsync(A + o_arr, 0, c->arena_bytes - o_arr, c->stream));
+  CK_SETUP(pfc::launch_assemble_mk(c->nnz_sell, c->cptr, c->cidx, c->E, c->ntypes, c->np, c->mass_tab, c->stiff_tab,
+                                   c->Mv, c->Kv, c->stream));
+  CK_SETUP(pfc::launch_diag_inv(c->n_pad, c->diag, c->Mv, c->dM, c->prec ? c->fdM : nullptr, c->stream));
+  if (c->prec) {
+    CK_SETUP(pfc::launch_convert(c->prec, c->nnz_sell, c->Mv, c->iM, c->stream));
+    CK_SETUP(pfc::launch_convert(c->prec, c->nnz_sell, c->Kv, c->iK, c->stream));
+  }
+  CK_SETUP(cudaStreamSynchronize(c->stream));
+#undef UP
+#undef CK_SETUP
+  *out = c;
+  return PFC_OK;
+}
+
+pfc_status pfc_assemble(pfc_ctx* c, const double* state, double tau) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "state must be non-null and tau > 0");
+  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, state, c->xk, c->stream));
+  return assemble_internal(c, tau);
+}
+
+pfc_status pfc_stage_rhs(pfc_ctx* c, int nprev, const double* x_stage, const double* y_prev, double* b) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
+  if (nprev < 0 || nprev > 2 || !x_stage || !b || (nprev > 0 && !y_prev))
+    return fail(c, PFC_ERR_INVALID, "bad stage_rhs arguments");
+  const size_t n3 = 3 * (size_t)c->n;
+  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, x_stage, c->xi, c->stream));
+  for (int j = 0; j < nprev; ++j)
+    CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, y_prev + j * n3, c->ys + (size_t)j * 3 * c->n_pad, c->stream));
+  st = stage_rhs_internal(c, nprev);
+  if (st != PFC_OK) return st;
+  CK(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->bv, b, c->stream));
+  return PFC_OK;
+}
+
+pfc_status pfc_stage_solve(pfc_ctx* c, const double* b, double* y, pfc_solve_stats* stats) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
+  if (!b || !y) return fail(c, PFC_ERR_INVALID, "null vector");
+  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, b, c->bv, c->stream));
+  pfc::SolveArgs a = base_args(c, c->prec);
+  a.mode = 0;
+  a.b = c->bv;
+  a.y = c->tmp3;
+  st = run_solver(c, a, c->prec, 0);
+  if (st != PFC_OK) return st;
+  CK(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->tmp3, y, c->stream));
+  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  fill_stats(c->h_stats[0], c->h_errw[0], stats);
+  st = status_from_err(c->h_errw[0]);
+  if (st != PFC_OK) return fail(c, st, std::string("stage solve: ") + pfc_status_string(st));
+  return PFC_OK;
+}
+
+pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, double* err, pfc_solve_stats* stats) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!state || !tau || !(*tau > 0.0) || !std::isfinite(*tau)) return fail(c, PFC_ERR_INVALID, "bad step arguments");
+  const int np = c->n_pad;
+  const size_t np3 = 3 * (size_t)np;
+  CK(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
+  st = assemble_internal(c, *tau);
+  if (st != PFC_OK) return st;
+  for (int i = 0; i < 3; ++i) {
+    CK(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1], c->xi,
+                                 c->dvec, c->stream));
+    // d = sum_j c_ij dpsi_j comes from stage_combine; the RHS kernel reads it
+    CK(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+    CK(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
+                       i > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
+    pfc::SolveArgs a = base_args(c, c->prec);
+    a.mode = 0;
+    a.b = c->bv;
+    a.y = c->ys + i * np3;
+    st = run_solver(c, a, c->prec, i);
+    if (st != PFC_OK) return st;
+  }
+  double e[3];
+  for (int j = 0; j < 3; ++j) e[j] = kMhat[j] - kM[j];
+  CK(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
+                              c->xnew, c->step_part, pfc::step_partials(), c->stream));
+  CK(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
+  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int werr = 0;
+  for (int i = 0; i < 3; ++i) {
+    fill_stats(c->h_stats[i], c->h_errw[i], stats ? stats + i : nullptr);
+    werr |= c->h_errw[i];
+  }
+  const double ev = c->h_err[0];
+  if (err) *err = ev;
+  st = status_from_err(werr);
+  if (st == PFC_ERR_TIMEOUT || st == PFC_ERR_NONFINITE || !std::isfinite(ev)) {
+    if (accepted) *accepted = 0;
+    return fail(c, st == PFC_OK ? PFC_ERR_NONFINITE : st, "step failed in a stage solve");
+  }
+  const bool acc = ev <= 1.0 && st == PFC_OK;
+  if (accepted) *accepted = acc ? 1 : 0;
+  if (acc) CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
+  double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
+  *tau = std::min(*tau * fac, c->opt.tau_max);
+  if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
+  return PFC_OK;
+}
+
+pfc_status pfc_init_state(pfc_ctx* c, const double* psi0, double* state) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!psi0 || !state) return fail(c, PFC_ERR_INVALID, "null vector");
+  const int np = c->n_pad;
+  double* mu = c->xk;
+  double* psi = c->xk + np;
+  double* om = c->xk + 2 * np;
+  CK(pfc::launch_gather_in(c->n, np, 1, c->perm, psi0, psi, c->stream));
+  CK(pfc::launch_elem_load(c->dim, c->E, c->elem, psi, c->vol, c->ebuf, c->stream));
+  CK(pfc::launch_dof_gather(np, c->dptr, c->didx, c->ebuf, c->lvec, c->stream));
+  // M omega = -K psi
+  CK(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 0.0, nullptr, -1.0, psi, 0.0, nullptr, 0.0,
+                            nullptr, c->tmpn, c->stream));
+  pfc::SolveArgs a = base_args(c, 0);
+  a.mode = 2;
+  a.which = 0;
+  a.inner_rtol = 1e-14;
+  a.max_inner = 5000;
+  a.b = c->tmpn;
+  a.y = om;
+  st = run_solver(c, a, 0, 3);
+  if (st != PFC_OK) return st;
+  // M mu = l(psi^3) + (1+r) M psi - 2 K psi - K omega
+  CK(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 1.0 + c->opt.r, psi, -2.0, psi, -1.0, om,
+                            1.0, c->lvec, c->tmpn, c->stream));
+  a.y = mu;
+  st = run_solver(c, a, 0, 3);
+  if (st != PFC_OK) return st;
+  CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xk, state, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  st = status_from_err(c->h_errw[0]);
+  if (st != PFC_OK) return fail(c, st, "consistent initialisation failed");
+  return PFC_OK;
+}
+
+pfc_status pfc_apply(pfc_ctx* c, int op, const double* x, double* y) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!x || !y) return fail(c, PFC_ERR_INVALID, "null vector");
+  if ((op == PFC_OP_A01 || op == PFC_OP_AR || op == PFC_OP_PCH) && !c->assembled)
+    return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
+  const int np = c->n_pad;
+  if (op == PFC_OP_M || op == PFC_OP_K || op == PFC_OP_A01) {
+    CK(pfc::launch_gather_in(c->n, np, 1, c->perm, x, c->tmp3, c->stream));
+    const double* vals = op == PFC_OP_M ? c->Mv : op == PFC_OP_K ? c->Kv : c->Av;
+    CK(pfc::launch_spmv(c->nslices, c->slice_ptr, c->cols, vals, c->tmp3, c->xnew, c->stream));
+    CK(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, y, c->stream));
+  } else if (op == PFC_OP_AR) {
+    CK(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
+    CK(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / kGamma, c->tmp3,
+                           c->xnew, c->stream));
+    CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
+  } else if (op == PFC_OP_PCH) {
+    CK(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
+    pfc::SolveArgs a = base_args(c, c->prec);
+    a.mode = 1;
+    a.b = c->tmp3;
+    a.y = c->xnew;
+    st = run_solver(c, a, c->prec, 0);
+    if (st != PFC_OK) return st;
+    CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
+  } else {
+    return fail(c, PFC_ERR_INVALID, "unknown operator");
+  }
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  st = op == PFC_OP_PCH ? status_from_err(c->h_errw[0]) : PFC_OK;
+  if (st != PFC_OK) return fail(c, st, "preconditioner application failed");
+  return PFC_OK;
+}
+
+pfc_status pfc_pcg(pfc_ctx* c, int which, const double* b, double* x, double rtol, int* iterations) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
+  if (!b || !x || which < 0 || which > 2 || !(rtol > 0.0)) return fail(c, PFC_ERR_INVALID, "bad pcg arguments");
+  const int np = c->n_pad;
+  CK(pfc::launch_gather_in(c->n, np, 1, c->perm, b, c->tmp3, c->stream));
+  pfc::SolveArgs a = base_args(c, c->prec);
+  a.mode = 2;
+  a.which = which;
+  a.inner_rtol = rtol;
+  a.b = c->tmp3;
+  a.y = c->xnew;
+  st = run_solver(c, a, c->prec, 0);
+  if (st != PFC_OK) return st;
+  CK(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, x, c->stream));
+  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (iterations) *iterations = c->h_stats[0].last_its;
+  st = status_from_err(c->h_errw[0]);
+  if (st != PFC_OK) return fail(c, st, "pcg failed");
+  return PFC_OK;
+}
+
+pfc_status pfc_selftest_barrier_timeout(pfc_ctx* c, double limit_seconds) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!(limit_seconds > 0.0) || limit_seconds > 10.0) return fail(c, PFC_ERR_INVALID, "limit must be in (0, 10] s");
+  // A PCG launch whose barriers wait for one block more than the grid has: every
+  // wait runs out after limit_seconds, the kernel sets the timeout bit and returns.
+  pfc::SolveArgs a = base_args(c, 0);
+  a.mode = 2;
+  a.which = 0;
+  a.b = c->tmpn;
+  a.y = c->xnew;
+  a.barrier_extra = 1;
+  a.spin_limit_ns = (unsigned long long)(limit_seconds * 1e9);
+  st = run_solver(c, a, 0, 0);
+  if (st != PFC_OK) return st;
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return status_from_err(c->h_errw[0]);
+}
+
+pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4) {
+  if (!out4) return PFC_ERR_INVALID;
+  pfc::HostSetup S;
+  std::string err;
+  if (!pfc::build_setup(dim, side, length, S, err)) return PFC_ERR_INVALID;
+  out4[0] = S.n;
+  out4[1] = S.nnz;
+  out4[2] = S.nnz_sell;
+  out4[3] = S.E;
+  return PFC_OK;
+}
+
+}  // extern "C"

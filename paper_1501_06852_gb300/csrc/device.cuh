@@ -1,0 +1,111 @@
+// Device helpers shared by the kernels of the PFC stage solver.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pfc {
+
+// Device error bits (DevStats::err and the context error word).
+enum : int {
+  kErrTimeout = 1,     // a grid barrier stopped waiting
+  kErrNonfinite = 2,   // NaN/Inf in a reduction
+  kErrOuterCap = 4,    // FGMRES hit max_outer
+  kErrBreakdown = 8    // p^T A p <= 0 in PCG (matrix not SPD or underflow)
+};
+
+struct DevStats {
+  int outer_its;
+  int restarts;
+  int inner_calls;
+  int inner_capped;
+  long long inner_its;
+  double rel_residual;
+  double bnorm;
+  int err;
+  int last_its;        // iterations of a single PCG solve (pcg mode)
+};
+
+// Arguments of the persistent solver kernel.  Inner arrays are typed by the
+// kernel instantiation (TM for matrix values, TV for inner vectors).
+struct SolveArgs {
+  int n_pad;
+  const int* slice_ptr;
+  const int* cols;
+  const int* blk;          // gridDim.x + 1 slice boundaries (nnz balanced)
+  const double* Mv;        // float64 M, K, A01 values (outer operator A^R)
+  const double* Kv;
+  const double* Av;
+  const void* iM;          // inner values M, K, M + delta K, M + sqrt(delta) K
+  const void* iK;
+  const void* iMdK;
+  const void* iMsK;
+  const void* dM;          // inner Jacobi inverses of M, M + delta K, M + sqrt(delta) K
+  const void* dMdK;
+  const void* dMsK;
+  double tau, gamma, inv_gamma, tau_e, inv_delta;
+  double tol, inner_rtol;
+  int restart, max_outer, max_inner;
+  int mode;                // 0 FGMRES stage solve, 1 one P_CH application, 2 one PCG solve
+  int which;               // mode 2: 0 M, 1 M + delta K, 2 M + sqrt(delta) K
+  const double* b;         // 3 n_pad (modes 0, 1) or n_pad (mode 2)
+  double* y;
+  double* V;               // (restart + 1) x 3 n_pad
+  double* Z;               // restart x 3 n_pad
+  void* ivec;              // 8 inner vectors of n_pad TV each
+  unsigned* arrive;        // grid barrier counter (zeroed before each launch)
+  int* err;                // error word (zeroed before each launch)
+  double2* part;           // reduction partials, kRing x gridDim.x
+  DevStats* stats;
+  unsigned long long spin_limit_ns;  // a barrier wait gives up after this long
+  int barrier_extra;       // 0; > 0 only in the timeout self-test (waits cannot complete)
+};
+
+template <class T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+template <class A> __device__ __forceinline__ A ld_val(const double* p) { return (A)__ldg(p); }
+template <class A> __device__ __forceinline__ A ld_val(const float* p) { return (A)__ldg(p); }
+template <class A> __device__ __forceinline__ A ld_val(const __half* p) { return (A)__half2float(__ldg(p)); }
+
+template <class T> __device__ __forceinline__ T from_acc(double v) { return (T)v; }
+template <class T> __device__ __forceinline__ T from_acc(float v) { return (T)v; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// y_row = sum_j vals[j] x[cols[j]] over one SELL-32 row (slot stride 32).
+// Matrix data is read-only for the kernel lifetime (__ldg); x is written by
+// other blocks during persistent kernels, so it is read with plain loads.
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ Acc sell_row(const int* __restrict__ slice_ptr, const int* __restrict__ cols,
+                                        const TM* __restrict__ vals, const TX* x, int s, int lane) {
+  const int beg = __ldg(slice_ptr + s) + lane;
+  const int end = __ldg(slice_ptr + s + 1);
+  Acc acc = Acc(0);
+#pragma unroll 4
+  for (int idx = beg; idx < end; idx += 32) {
+    const int c = __ldg(cols + idx);
+    acc = fma(ld_val<Acc>(vals + idx), (Acc)x[c], acc);
+  }
+  return acc;
+}
+
+}  // namespace pfc

@@ -1,0 +1,252 @@
+// Structured simplicial mesh, P2 dof lattice, SELL-C-sigma pattern and the
+// gather maps of the assembly kernels (host side, once per instance).
+//
+// Mesh (Section 3 and Section 6 use regular simplicial meshes): side^dim cells of
+// width h = length / side; cell c splits into the simplices whose vertices follow
+// a monotone lattice path from the cell's low corner to its high corner (2 in 2D,
+// the 6 Kuhn tetrahedra in 3D).  P2 dofs are the half-spacing lattice points,
+// numbered lexicographically (x fastest); the node of edge (a, b) is the lattice
+// midpoint of its end points.
+//
+// Device layout.  All blocks of the stage matrix (M, K, A01 and the inner
+// matrices) share one sparsity pattern, stored once as SELL-32-sigma: rows are
+// sorted by length (descending) inside windows of kSellSigma lexicographic rows,
+// grouped in slices of 32 rows, and each slice is stored column-major with the
+// width of its longest row.  The sorted row order IS the internal dof order of
+// every device vector, so a SpMV writes y[row] coalesced and a vector update
+// touches 32 consecutive rows per warp.  Padding slots point at their own row
+// with value 0.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace pfc {
+
+void element_path(int dim, int t, int verts[4][3]);
+void local_edge(int dim, int e, int& a, int& b);
+
+bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err) {
+  if (dim != 2 && dim != 3) {
+    err = "dim must be 2 or 3";
+    return false;
+  }
+  if (side < 1 || !(length > 0.0)) {
+    err = "side must be >= 1 and length > 0";
+    return false;
+  }
+  const int64_t lat = 2 * (int64_t)side + 1;
+  const int64_t n64 = dim == 2 ? lat * lat : lat * lat * lat;
+  const int64_t cells64 = dim == 2 ? (int64_t)side * side : (int64_t)side * side * side;
+  const int ntypes = dim == 2 ? 2 : 6;
+  const int nl = dim == 2 ? 6 : 10;
+  const int np = nl * (nl + 1) / 2;
+  if (n64 > (1LL << 28) || cells64 * ntypes * np > (1LL << 31) - 1) {
+    err = "mesh too large for 32-bit indices";
+    return false;
+  }
+  S = HostSetup{};
+  S.dim = dim;
+  S.side = side;
+  S.length = length;
+  S.h = length / side;
+  S.lat = (int)lat;
+  S.n = (int)n64;
+  S.ntypes = ntypes;
+  S.nl = nl;
+  if (!build_reference(dim, S.h, S.ref, err)) return false;
+  const int n = S.n;
+  const int E = (int)(cells64 * ntypes);
+  S.E = E;
+
+  // --- elements: cell-major (x fastest), types inner ---------------------------
+  std::vector<int> elem_lex((size_t)E * nl);
+  int path[6][4][3];
+  for (int t = 0; t < ntypes; ++t) element_path(dim, t, path[t]);
+  for (int64_t c = 0; c < cells64; ++c) {
+    int ci = (int)(c % side), cj = (int)((c / side) % side), ck = dim == 3 ? (int)(c / ((int64_t)side * side)) : 0;
+    for (int t = 0; t < ntypes; ++t) {
+      int e = (int)(c * ntypes + t);
+      int L[10][3];
+      for (int k = 0; k <= dim; ++k) {
+        L[k][0] = 2 * (ci + path[t][k][0]);
+        L[k][1] = 2 * (cj + path[t][k][1]);
+        L[k][2] = 2 * (ck + path[t][k][2]);
+      }
+      int ne = dim == 2 ? 3 : 6;
+      for (int q = 0; q < ne; ++q) {
+        int a, b;
+        local_edge(dim, q, a, b);
+        for (int x = 0; x < 3; ++x) L[dim + 1 + q][x] = (L[a][x] + L[b][x]) / 2;
+      }
+      for (int l = 0; l < nl; ++l)
+        elem_lex[(size_t)e * nl + l] = (int)(L[l][0] + lat * (L[l][1] + lat * (int64_t)L[l][2]));
+    }
+  }
+
+  // --- dof -> (element, local) incidence ---------------------------------------
+  std::vector<int> inc_ptr(n + 1, 0), inc(E * (size_t)nl);
+  for (size_t q = 0; q < elem_lex.size(); ++q) inc_ptr[elem_lex[q] + 1]++;
+  for (int i = 0; i < n; ++i) inc_ptr[i + 1] += inc_ptr[i];
+  {
+    std::vector<int> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int e = 0; e < E; ++e)
+      for (int l = 0; l < nl; ++l) inc[fill[elem_lex[(size_t)e * nl + l]]++] = l * E + e;
+  }
+
+  // --- row lengths (lexicographic) ---------------------------------------------
+  std::vector<int> len(n);
+#pragma omp parallel
+  {
+    std::vector<int> buf;
+#pragma omp for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      buf.clear();
+      for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+        int e = inc[q] % E;
+        for (int l = 0; l < nl; ++l) buf.push_back(elem_lex[(size_t)e * nl + l]);
+      }
+      std::sort(buf.begin(), buf.end());
+      len[i] = (int)(std::unique(buf.begin(), buf.end()) - buf.begin());
+    }
+  }
+  S.nnz = 0;
+  for (int i = 0; i < n; ++i) S.nnz += len[i];
+
+  // --- SELL-32-sigma ordering -------------------------------------------------
+  S.perm.resize(n);
+  std::iota(S.perm.begin(), S.perm.end(), 0);
+  for (int w0 = 0; w0 < n; w0 += kSellSigma) {
+    int w1 = std::min(n, w0 + kSellSigma);
+    std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
+  }
+  S.iperm.resize(n);
+  for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
+  S.nslices = (n + kSellC - 1) / kSellC;
+  S.n_pad = S.nslices * kSellC;
+  S.slice_ptr.assign(S.nslices + 1, 0);
+  for (int s = 0; s < S.nslices; ++s) {
+    int w = 0;
+    for (int l = 0; l < kSellC; ++l) {
+      int p = s * kSellC + l;
+      if (p < n) w = std::max(w, len[S.perm[p]]);
+    }
+    S.slice_ptr[s + 1] = S.slice_ptr[s] + w * kSellC;
+  }
+  S.nnz_sell = S.slice_ptr[S.nslices];
+  if (S.nnz_sell > (1LL << 31) - 1) {
+    err = "too many nonzeros for 32-bit slot indices";
+    return false;
+  }
+
+  // --- columns, diagonal positions, slot contributions ---------------------------
+  S.cols.assign(S.nnz_sell, 0);
+  S.diag_pos.assign(S.n_pad, -1);
+  std::vector<int> ccount(S.nnz_sell + 1, 0);
+  S.elem_int.resize((size_t)nl * E);
+  for (int e = 0; e < E; ++e)
+    for (int l = 0; l < nl; ++l) S.elem_int[(size_t)l * E + e] = S.iperm[elem_lex[(size_t)e * nl + l]];
+
+  auto row_cols = [&](int i, std::vector<int>& buf) {
+    buf.clear();
+    for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+      int e = inc[q] % E;
+      for (int l = 0; l < nl; ++l) buf.push_back(S.iperm[elem_lex[(size_t)e * nl + l]]);
+    }
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+  };
+  const RefTensors& R = S.ref;
+  // pass 1: columns, diagonal, contribution counts
+#pragma omp parallel
+  {
+    std::vector<int> buf;
+#pragma omp for schedule(static)
+    for (int p = 0; p < S.n_pad; ++p) {
+      int s = p / kSellC, lane = p % kSellC;
+      int base = S.slice_ptr[s] + lane;
+      int w = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / kSellC;
+      if (p >= n) {
+        for (int j = 0; j < w; ++j) S.cols[base + j * kSellC] = p;
+        continue;
+      }
+      int i = S.perm[p];
+      row_cols(i, buf);
+      for (int j = 0; j < w; ++j) S.cols[base + j * kSellC] = j < (int)buf.size() ? buf[j] : p;
+      for (int j = 0; j < (int)buf.size(); ++j)
+        if (buf[j] == p) S.diag_pos[p] = base + j * kSellC;
+      for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+        int e = inc[q] % E;
+        for (int lc = 0; lc < nl; ++lc) {
+          int col = S.elem_int[(size_t)lc * E + e];
+          int j = (int)(std::lower_bound(buf.begin(), buf.end(), col) - buf.begin());
+          ccount[base + j * kSellC + 1]++;
+        }
+      }
+    }
+  }
+  for (int64_t q = 0; q < S.nnz_sell; ++q) ccount[q + 1] += ccount[q];
+  S.contrib_ptr = ccount;
+  S.contrib_idx.assign(S.contrib_ptr[S.nnz_sell], 0);
+  // pass 2: contribution lists (each row owns its slots, so rows run in parallel)
+#pragma omp parallel
+  {
+    std::vector<int> buf;
+#pragma omp for schedule(static)
+    for (int p = 0; p < n; ++p) {
+      int s = p / kSellC, lane = p % kSellC;
+      int base = S.slice_ptr[s] + lane;
+      int i = S.perm[p];
+      row_cols(i, buf);
+      std::vector<int> next(buf.size(), 0);
+      for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
+        int e = inc[q] % E, li = inc[q] / E;
+        for (int lc = 0; lc < nl; ++lc) {
+          int col = S.elem_int[(size_t)lc * E + e];
+          int j = (int)(std::lower_bound(buf.begin(), buf.end(), col) - buf.begin());
+          int slot = base + j * kSellC;
+          int pr = R.pair_index[li * nl + lc];
+          S.contrib_idx[S.contrib_ptr[slot] + next[j]++] = pr * E + e;
+        }
+      }
+    }
+  }
+
+  // --- dof gather map for element load vectors ---------------------------------
+  S.dof_ptr.assign(S.n_pad + 1, 0);
+  for (int p = 0; p < S.n_pad; ++p) {
+    int c = p < n ? inc_ptr[S.perm[p] + 1] - inc_ptr[S.perm[p]] : 0;
+    S.dof_ptr[p + 1] = S.dof_ptr[p] + c;
+  }
+  S.dof_idx.resize(S.dof_ptr[S.n_pad]);
+  for (int p = 0; p < n; ++p) {
+    int i = S.perm[p];
+    std::copy(inc.begin() + inc_ptr[i], inc.begin() + inc_ptr[i + 1], S.dof_idx.begin() + S.dof_ptr[p]);
+  }
+  return true;
+}
+
+size_t footprint_estimate(int dim, int side, int restart, int precision) {
+  const double lat = 2.0 * side + 1.0;
+  const double n = dim == 2 ? lat * lat : lat * lat * lat;
+  const double nnz_row = dim == 2 ? 11.6 : 28.6;      // stored slots per row incl. padding
+  const double nnz = n * nnz_row;
+  const double E = dim == 2 ? 2.0 * side * side : 6.0 * side * side * side;
+  const double np = dim == 2 ? 21 : 55, nl = dim == 2 ? 6 : 10;
+  double b = 0;
+  b += nnz * 4;                             // columns
+  b += nnz * 8 * 5;                         // M, K, A01, M+dK, M+sK (float64)
+  b += precision == 0 ? 0 : nnz * (precision == 1 ? 4 : 2) * 4;
+  b += nnz * 4 + E * nl * nl * 4;           // contribution map
+  b += E * np * 8 + E * nl * 4 * 2;         // element buffer, element dofs, dof map
+  b += n * 8 * 3 * (2.0 * restart + 1 + 8); // Krylov bases and step vectors
+  b += n * 8 * 12;                          // inner vectors, diagonals
+  return (size_t)(b * 1.05) + (64u << 20);
+}
+
+}  // namespace pfc

@@ -1,0 +1,61 @@
+// Internal declarations of the PFC stage-solver library (host and device).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace pfc {
+
+constexpr int kSellC = 32;          // SELL slice height = warp width
+constexpr int kSellSigma = 1024;    // rows sorted by length inside windows of this size
+constexpr int kMaxRestart = 40;     // FGMRES restart cap (shared-memory Hessenberg)
+constexpr int kMaxLocal = 10;       // P2 nodes per tetrahedron
+constexpr int kMaxPairs = 55;       // unordered local pairs for tetrahedra
+
+// Exact integrals of P2 basis products on one simplex type, built from
+// barycentric monomials: int_T lambda^e = |T| d! prod(e_k!) / (|e| + d)!.
+struct RefTensors {
+  int dim = 0, nl = 0, npairs = 0, ntypes = 0;
+  double vol = 0.0;                          // |T| of every element of the structured mesh
+  std::vector<int> pair_i, pair_j;           // unordered pair p -> (i <= j)
+  std::vector<int> pair_index;               // nl*nl -> p
+  std::vector<double> mass;                  // ntypes x npairs: int phi_i phi_j
+  std::vector<double> stiff;                 // ntypes x npairs: int grad phi_i . grad phi_j
+  std::vector<double> quartic;               // npairs(ab) x npairs(ij): w_ab int phi_a phi_b phi_i phi_j, w_ab = 2 (a != b), 1
+};
+
+// Structured mesh, P2 dofs, SELL-C-sigma pattern and the maps the assembly
+// kernels gather through.  All indices are int32.
+struct HostSetup {
+  int dim = 0, side = 0;
+  double length = 0.0, h = 0.0;
+  int lat = 0;                    // 2 side + 1 lattice points per axis
+  int n = 0;                      // dofs per field
+  int n_pad = 0;                  // n rounded up to a multiple of kSellC
+  int nslices = 0;
+  int64_t nnz = 0;                // true nonzeros of one block
+  int64_t nnz_sell = 0;           // stored slots (with padding)
+  int E = 0;                      // elements
+  int nl = 0;                     // local nodes per element
+  int ntypes = 0;                 // element types per cell (2 or 6)
+  std::vector<int> perm;          // internal row -> lexicographic dof (size n)
+  std::vector<int> iperm;         // lexicographic dof -> internal row
+  std::vector<int> slice_ptr;     // nslices + 1 (slot offsets)
+  std::vector<int> cols;          // nnz_sell internal column indices (padding: the row itself)
+  std::vector<int> diag_pos;      // n_pad (-1 for padding rows)
+  std::vector<int> elem_int;      // nl x E (SoA) internal dof of local node l of element e
+  std::vector<int> contrib_ptr;   // nnz_sell + 1
+  std::vector<int> contrib_idx;   // p * E + e for each element pair landing on a slot
+  std::vector<int> dof_ptr;       // n_pad + 1
+  std::vector<int> dof_idx;       // l * E + e for each element incident to a row
+  RefTensors ref;
+};
+
+bool build_reference(int dim, double h, RefTensors& out, std::string& err);
+bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err);
+
+// Bytes of device memory a context of this size holds (estimate used for admission).
+size_t footprint_estimate(int dim, int side, int restart, int precision);
+
+}  // namespace pfc

@@ -1,0 +1,309 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the GPU.
+
+Every comparison uses the same seeded inputs from ``synth`` on both sides.
+Tolerances:
+* sparse operators and right-hand sides: |gpu - oracle| <= 1e-12 (|A| |x|) entrywise
+  (float64 sums in another order);
+* stage solutions: relative L2 error <= 1e-8 against the oracle solved to 1e-13
+  (the accuracy target of the method's hot path);
+* single PCG solves and one preconditioner application with tight inner
+  tolerances: <= 1e-9 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import assembly
+from oracle.mesh import structured_mesh
+from oracle.rosenbrock import ROS3PW, PFCProblem, StepControl, pfc_step
+from oracle.solvers import PCH, pcg_jacobi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1501_06852_gb300 as pfc  # noqa: E402
+
+CASES = [
+    (2, 32, 32.0, -0.4, -0.3, 0.1),    # 2D, 4225 dofs/field: the small benchmark configuration
+    (2, 5, 5.0, -0.4, -0.3, 0.1),      # ragged: 121 dofs, a partial last slice
+    (3, 4, 4.0, -0.3, -0.35, 0.05),    # 3D Kuhn tetrahedra, 729 dofs
+    (2, 1, 1.0, -0.4, -0.3, 0.1),      # smallest 2D mesh: 9 dofs
+    (3, 1, 1.0, -0.3, -0.35, 0.05),    # smallest 3D mesh: 27 dofs
+]
+IDS = [f"{c[0]}d-s{c[1]}" for c in CASES]
+
+_probs = {}
+
+
+def problem(dim, side, L, r):
+    key = (dim, side, L, r)
+    if key not in _probs:
+        _probs[key] = PFCProblem(structured_mesh(dim, side, L), r)
+    return _probs[key]
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def state_for(prob, dim, side, psi_mean, amp, seed=1):
+    n = prob.n
+    psi = synth.initial_psi(dim, side, psi_mean, amp, seed)
+    return np.concatenate([synth.random_vector(n, seed + 100), psi, synth.random_vector(n, seed + 200)])
+
+
+def assert_close_scaled(got, want, scale, tol=1e-12):
+    err = np.abs(got - want)
+    bound = tol * (scale + 1e-300)
+    assert np.all(err <= bound + tol * np.abs(want).max() * 1e-3), (err / (scale + 1e-300)).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_operators_match_oracle(case):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    x = state_for(prob, dim, side, pm, amp)
+    tau = 0.1
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        s.assemble(cuda(x), tau)
+        v = synth.random_vector(prob.n, 5)
+        A01 = prob.a01(x[prob.n:2 * prob.n])
+        for op, A in ((pfc.OP_M, prob.M), (pfc.OP_K, prob.K), (pfc.OP_A01, A01)):
+            got = host(s.apply(op, cuda(v)))
+            assert_close_scaled(got, A @ v, abs(A) @ np.abs(v))
+        AR = prob.stage_matrix(x[prob.n:2 * prob.n], tau)
+        v3 = synth.random_vector(3 * prob.n, 6)
+        got = host(s.apply(pfc.OP_AR, cuda(v3)))
+        assert_close_scaled(got, AR @ v3, abs(AR) @ np.abs(v3))
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_stage_rhs_matches_oracle(case):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    n = prob.n
+    x = state_for(prob, dim, side, pm, amp)
+    tau = 0.37
+    ys = [synth.random_vector(3 * n, 40 + j) * 0.01 for j in range(2)]
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        s.assemble(cuda(x), tau)
+        for i in range(3):
+            xi = x + sum(ROS3PW.a(i, j) * ys[j] for j in range(i))
+            want = prob.stage_rhs(xi, [y[n:2 * n] for y in ys[:i]], [ROS3PW.c(i, j) for j in range(i)], tau)
+            yp = cuda(np.concatenate(ys[:i])) if i else None
+            got = host(s.stage_rhs(i, cuda(xi), yp))
+            M, K = prob.M, prob.K
+            aM, aK = abs(M), abs(K)
+            mu, psi, om = np.abs(xi[:n]), np.abs(xi[n:2 * n]), np.abs(xi[2 * n:])
+            l3 = assembly.load_cubed(prob.mesh, np.abs(xi[n:2 * n]), prob.ref)
+            s0 = aM @ mu + 1.6 * (aM @ psi) + 2 * (aK @ psi) + aK @ om + np.abs(l3)
+            s1 = tau * (aK @ mu) + sum(abs(ROS3PW.c(i, j)) * (aM @ np.abs(ys[j][n:2 * n])) for j in range(i))
+            s2 = aM @ om + aK @ psi
+            assert_close_scaled(got, want, np.concatenate([s0, s1, s2]))
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_pcg_matches_oracle(case):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    x = state_for(prob, dim, side, pm, amp)
+    tau = 0.1
+    delta = math.sqrt(ROS3PW.gamma * tau)
+    mats = [prob.M, (prob.M + delta * prob.K).tocsr(), (prob.M + math.sqrt(delta) * prob.K).tocsr()]
+    b = synth.random_vector(prob.n, 8)
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        s.assemble(cuda(x), tau)
+        for which, A in enumerate(mats):
+            for rtol in (1e-3, 1e-10):
+                got, its = s.pcg(which, cuda(b), rtol)
+                got = host(got)
+                ref = pcg_jacobi(A, b, rtol, 10000)
+                assert np.linalg.norm(b - A @ got) <= rtol * np.linalg.norm(b) * (1 + 1e-6)
+                assert abs(its - ref.iterations) <= 1
+                if its == ref.iterations:
+                    assert np.linalg.norm(got - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_mixed_precision_pcg_meets_tolerance(precision):
+    dim, side, L, r, pm, amp = CASES[0]
+    prob = problem(dim, side, L, r)
+    x = state_for(prob, dim, side, pm, amp)
+    tau = 0.1
+    delta = math.sqrt(ROS3PW.gamma * tau)
+    A = (prob.M + delta * prob.K).tocsr()
+    b = synth.random_vector(prob.n, 8)
+    with pfc.PFCSolver(dim, side, L, r=r, precision=precision) as s:
+        s.assemble(cuda(x), tau)
+        got, its = s.pcg(1, cuda(b), 1e-3)
+        got = host(got)
+        # float16 values perturb A by ~1e-3 relative: the residual of the float64 system is looser
+        slack = 1.05 if precision == "fp32" else 3.0
+        assert np.linalg.norm(b - A @ got) <= 1e-3 * np.linalg.norm(b) * slack
+        assert its < 200
+
+
+@pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
+def test_preconditioner_matches_oracle(case):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    x = state_for(prob, dim, side, pm, amp)
+    tau = 0.25
+    v = synth.random_vector(3 * prob.n, 9)
+    ref = PCH(prob.M, prob.K, tau, ROS3PW.gamma, inner="exact").apply(v)
+    with pfc.PFCSolver(dim, side, L, r=r, inner_rtol=1e-13) as s:
+        s.assemble(cuda(x), tau)
+        got = host(s.apply(pfc.OP_PCH, cuda(v)))
+    assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+_ref_solutions = {}
+
+
+def oracle_stage(case, tau, stage_seed=1):
+    key = (case, tau, stage_seed)
+    if key not in _ref_solutions:
+        dim, side, L, r, pm, amp = case
+        prob = problem(dim, side, L, r)
+        x = prob.consistent_state(synth.initial_psi(dim, side, pm, amp, stage_seed))
+        A = prob.stage_matrix(x[prob.n:2 * prob.n], tau)
+        b = prob.stage_rhs(x, [], [], tau)
+        y, st = prob.stage_solve(A, b, tau, tol=1e-13)
+        assert st.converged
+        _ref_solutions[key] = (x, b, y)
+    return _ref_solutions[key]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_stage_solve_parity(case, precision):
+    dim, side, L, r, pm, amp = case
+    tau = 0.1
+    x, b, yref = oracle_stage(case, tau)
+    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11) as s:
+        s.assemble(cuda(x), tau)
+        y, st = s.stage_solve(cuda(b))
+        y = host(y)
+    err = np.linalg.norm(y - yref) / np.linalg.norm(yref)
+    assert st.status == 0 and st.rel_residual <= 1e-11
+    assert err <= 1e-8, (err, st)
+    assert st.outer_its > 0 and st.inner_calls == 5 * st.outer_its
+
+
+@pytest.mark.parametrize("tau", [1.0, 4.0])
+def test_stage_solve_parity_large_tau(tau):
+    case = CASES[0]
+    dim, side, L, r, pm, amp = case
+    x, b, yref = oracle_stage(case, tau)
+    with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", outer_tol=1e-12) as s:
+        s.assemble(cuda(x), tau)
+        y, st = s.stage_solve(cuda(b))
+        y = host(y)
+    assert np.linalg.norm(y - yref) / np.linalg.norm(yref) <= 1e-8
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2]], ids=[IDS[0], IDS[2]])
+def test_init_state_matches_oracle(case):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    psi0 = synth.initial_psi(dim, side, pm, amp, 3)
+    want = prob.consistent_state(psi0)
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        got = host(s.init_state(cuda(psi0)))
+    assert np.linalg.norm(got - want) <= 1e-11 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", [CASES[0], CASES[2]], ids=[IDS[0], IDS[2]])
+def test_step_parity(case, precision):
+    dim, side, L, r, pm, amp = case
+    prob = problem(dim, side, L, r)
+    x0 = prob.consistent_state(synth.initial_psi(dim, side, pm, amp, 1))
+    ref = pfc_step(prob, x0, 0.1, StepControl(), tol=1e-13)
+    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11) as s:
+        st = cuda(x0)
+        acc, err, tau_next, stats = s.step(st, 0.1)
+        got = host(st)
+    assert acc == ref.accepted
+    assert err == pytest.approx(ref.err, rel=1e-6)
+    assert tau_next == pytest.approx(ref.tau_next, rel=1e-6)
+    if acc:
+        d = got - x0
+        dref = ref.x_new - x0
+        assert np.linalg.norm(d - dref) <= 1e-8 * np.linalg.norm(dref)
+        assert abs(prob.mass(got) - prob.mass(x0)) <= 1e-9 * abs(prob.mass(x0))
+    assert all(s_.status == 0 for s_ in stats)
+
+
+def test_rejected_step_leaves_state():
+    dim, side, L, r, pm, amp = CASES[0]
+    prob = problem(dim, side, L, r)
+    x0 = prob.consistent_state(synth.initial_psi(dim, side, pm, amp, 1))
+    with pfc.PFCSolver(dim, side, L, r=r, step_atol=1e-9, step_rtol=1e-9) as s:
+        st = cuda(x0)
+        acc, err, tau_next, _ = s.step(st, 0.5)
+        got = host(st)
+    assert not acc and err > 1.0 and tau_next < 0.5
+    assert np.array_equal(got, x0)
+
+
+def test_solve_is_deterministic():
+    case = CASES[0]
+    dim, side, L, r, pm, amp = case
+    x, b, _ = oracle_stage(case, 0.1)
+    with pfc.PFCSolver(dim, side, L, r=r, precision="fp32") as s:
+        s.assemble(cuda(x), 0.1)
+        y1, s1 = s.stage_solve(cuda(b))
+        y2, s2 = s.stage_solve(cuda(b))
+        assert torch.equal(y1, y2) and s1 == s2
+
+
+def test_edge_cases_zero_nan_and_caps():
+    case = CASES[1]
+    dim, side, L, r, pm, amp = case
+    x, b, _ = oracle_stage(case, 0.1)
+    with pfc.PFCSolver(dim, side, L, r=r, max_outer=2) as s:
+        s.assemble(cuda(x), 0.1)
+        y, st = s.stage_solve(cuda(np.zeros_like(b)))
+        assert st.status == 0 and st.outer_its == 0 and float(y.abs().max()) == 0.0
+        y, st = s.stage_solve(cuda(b), check=False)
+        assert st.status == 4 and st.outer_its == 2 and st.rel_residual > 1e-11
+        bad = b.copy()
+        bad[3] = np.nan
+        with pytest.raises(pfc.PFCError) as ei:
+            s.stage_solve(cuda(bad))
+        assert ei.value.status == 5
+        # the context stays usable after both failures
+        y, st = s.stage_solve(cuda(np.zeros_like(b)))
+        assert st.status == 0
+
+
+def test_bounded_barrier_wait_returns_timeout_and_context_survives():
+    case = CASES[1]
+    dim, side, L, r, pm, amp = case
+    x, b, yref = oracle_stage(case, 0.1)
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        assert s.selftest_barrier_timeout(0.2) == 6
+        s.assemble(cuda(x), 0.1)
+        y, st = s.stage_solve(cuda(b))
+        assert np.linalg.norm(host(y) - yref) <= 1e-8 * np.linalg.norm(yref)
+
+
+def test_invalid_calls():
+    with pfc.PFCSolver(2, 4, 4.0) as s:
+        with pytest.raises(pfc.PFCError):
+            s.stage_solve(torch.zeros(3 * s.n, dtype=torch.float64, device="cuda"))
+        with pytest.raises(TypeError):
+            s.assemble(torch.zeros(3 * s.n, dtype=torch.float32, device="cuda"), 0.1)
+        with pytest.raises(pfc.PFCError):
+            s.assemble(torch.zeros(3 * s.n, dtype=torch.float64, device="cuda"), -1.0)
