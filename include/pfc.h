@@ -164,6 +164,16 @@ pfc_status pfc_pcg(pfc_ctx* ctx, int which, const double* b, double* x, double r
  * step of the paper's method: it checks the persistent kernel's bounded waits.) */
 pfc_status pfc_selftest_barrier_timeout(pfc_ctx* ctx, double limit_seconds);
 
+/* Accounting for benchmarks.  pfc_set_timing(ctx, 1) makes every later
+ * persistent-solver launch record CUDA events on the context stream around
+ * itself; the elapsed times are summed at the next synchronising call.
+ * pfc_counters reports the number of kernels the context has launched, the
+ * number of persistent-solver launches and the summed solver time (ms).
+ * Either output pointer may be NULL. */
+pfc_status pfc_set_timing(pfc_ctx* ctx, int enable);
+pfc_status pfc_counters(const pfc_ctx* ctx, long long* kernel_launches, long long* solver_launches,
+                        double* solver_ms);
+
 /* Host-only inspection of the mesh/pattern builder (no GPU needed):
  * out4 = {n, nnz of one block, stored SELL slots, elements}. */
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);

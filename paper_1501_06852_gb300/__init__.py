@@ -6,8 +6,9 @@ right-hand side, FGMRES with the P_CH block preconditioner, Jacobi-PCG, the
 Ros3Pw step and its error estimate) runs in the library's CUDA kernels.
 PyTorch provides device memory and the CUDA stream.
 
-Importing the package loads the library; a missing library is an error (there
-is no fallback): build it with ``python -m paper_1501_06852_gb300.build``.
+Importing the package (re)builds ``libpfc.so`` when it is missing or older than
+its sources and then loads it; if it cannot be built or loaded the import fails
+(there is no fallback path).
 """
 from __future__ import annotations
 
@@ -16,6 +17,7 @@ import math
 import os
 from dataclasses import dataclass
 
+from . import build as _build
 from .build import LIB as _LIB_PATH
 
 __all__ = ["PFCSolver", "PFCError", "SolveStats", "lib", "critical_tau", "ROS3PW_GAMMA",
@@ -42,8 +44,10 @@ class _Stats(ctypes.Structure):
 
 
 def _load():
+    if _build._stale():
+        _build.build()
     if not os.path.exists(_LIB_PATH):
-        raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_1501_06852_gb300.build`")
+        raise ImportError(f"{_LIB_PATH} is missing and could not be built")
     L = ctypes.CDLL(_LIB_PATH)
     P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, None
     sig = {
@@ -60,6 +64,9 @@ def _load():
         "pfc_pcg": (I, [P, I, P, P, D, ctypes.POINTER(I)]),
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_set_timing": (I, [P, I]),
+        "pfc_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(D)]),
         "pfc_last_error": (ctypes.c_char_p, [P]),
         "pfc_status_string": (ctypes.c_char_p, [I]),
         "pfc_destroy": (V, [P]),
@@ -223,6 +230,15 @@ class PFCSolver:
         self._check(lib.pfc_pcg(self._h, which, self._vec(b, self.n, "b"), self._vec(x, self.n, "x"), float(rtol),
                                 ctypes.byref(its)))
         return x, its.value
+
+    def set_timing(self, enable: bool = True):
+        self._check(lib.pfc_set_timing(self._h, 1 if enable else 0))
+
+    def counters(self) -> dict:
+        """Kernels launched by this context, persistent-solver launches and their summed event time."""
+        a, b, ms = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_double(0.0)
+        self._check(lib.pfc_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms)))
+        return {"kernel_launches": a.value, "solver_launches": b.value, "solver_ms": ms.value}
 
     def selftest_barrier_timeout(self, limit_seconds: float = 0.2) -> int:
         return int(lib.pfc_selftest_barrier_timeout(self._h, float(limit_seconds)))

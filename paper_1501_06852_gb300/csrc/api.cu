@@ -83,6 +83,12 @@ struct pfc_ctx {
   int* h_errw = nullptr;
   bool assembled = false;
   double tau = 0.0, delta = 0.0;
+  // accounting: kernels launched, persistent-solver launches and their event time
+  long long launches = 0, solver_launches = 0;
+  double solver_ms = 0.0;
+  bool timing = false;
+  cudaEvent_t ev[4][2] = {};
+  bool ev_pending[4] = {};
   std::string last_error;
 };
 
@@ -98,6 +104,13 @@ pfc_status fail(pfc_ctx* c, pfc_status st, const std::string& msg) {
     cudaError_t e_ = (call);                                                                  \
     if (e_ != cudaSuccess)                                                                    \
       return fail(c, PFC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+// A kernel launch through one of the launch wrappers, counted per context.
+#define LAUNCH(call)  \
+  do {                \
+    CK(call);         \
+    c->launches += 1; \
   } while (0)
 
 size_t inner_elem_bytes(int prec) { return prec == 1 ? 4 : prec == 2 ? 2 : 8; }
@@ -164,8 +177,24 @@ pfc_status run_solver(pfc_ctx* c, pfc::SolveArgs a, int prec, int slot) {
   CK(cudaMemsetAsync(c->errw + slot, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(a.stats, 0, sizeof(pfc::DevStats), c->stream));
   a.err = c->errw + slot;
-  CK(pfc::launch_solve(prec, c->G, a, c->stream));
+  if (c->timing) CK(cudaEventRecord(c->ev[slot][0], c->stream));
+  LAUNCH(pfc::launch_solve(prec, c->G, a, c->stream));
+  c->solver_launches += 1;
+  if (c->timing) {
+    CK(cudaEventRecord(c->ev[slot][1], c->stream));
+    c->ev_pending[slot] = true;
+  }
   return PFC_OK;
+}
+
+// After a stream synchronisation: add the event time of the finished solver launches.
+void harvest(pfc_ctx* c) {
+  for (int k = 0; k < 4; ++k) {
+    if (!c->ev_pending[k]) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) c->solver_ms += ms;
+    c->ev_pending[k] = false;
+  }
 }
 
 void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
@@ -183,24 +212,24 @@ void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
 pfc_status stage_rhs_internal(pfc_ctx* c, int nprev) {
   const int np = c->n_pad;
   const double c0 = nprev > 0 ? kC[nprev][0] : 0.0, c1 = nprev > 1 ? kC[nprev][1] : 0.0;
-  if (nprev > 0) CK(pfc::launch_combine_field(np, c->ys + np, c0, nprev > 1 ? c->ys + 3 * np + np : nullptr, c1, c->dvec, c->stream));
-  CK(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
-  CK(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
+  if (nprev > 0) LAUNCH(pfc::launch_combine_field(np, c->ys + np, c0, nprev > 1 ? c->ys + 3 * np + np : nullptr, c1, c->dvec, c->stream));
+  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
                      nprev > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
   return PFC_OK;
 }
 
 pfc_status assemble_internal(pfc_ctx* c, double tau) {
   const int np = c->n_pad;
-  CK(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
-  CK(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
+  LAUNCH(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
   c->tau = tau;
   c->delta = std::sqrt(kGamma * tau);
   const double sdelta = std::sqrt(c->delta);
-  CK(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
+  LAUNCH(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
                             c->stream));
-  CK(pfc::launch_diag_inv(np, c->diag, c->MdKv, c->dMdK, c->prec ? c->fdMdK : nullptr, c->stream));
-  CK(pfc::launch_diag_inv(np, c->diag, c->MsKv, c->dMsK, c->prec ? c->fdMsK : nullptr, c->stream));
+  LAUNCH(pfc::launch_diag_inv(np, c->diag, c->MdKv, c->dMdK, c->prec ? c->fdMdK : nullptr, c->stream));
+  LAUNCH(pfc::launch_diag_inv(np, c->diag, c->MsKv, c->dMsK, c->prec ? c->fdMsK : nullptr, c->stream));
   c->assembled = true;
   return PFC_OK;
 }
@@ -262,6 +291,9 @@ size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt) {
 void pfc_destroy(pfc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (c->ev[k][j]) cudaEventDestroy(c->ev[k][j]);
   if (c->arena) cudaFree(c->arena);
   if (c->h_stats) cudaFreeHost(c->h_stats);
   delete c;
@@ -453,6 +485,10 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     c->h_errw = (int*)(c->h_err + 2);
   }
 
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreate(&c->ev[k][j]) != cudaSuccess) return bail(fail(c, PFC_ERR_CUDA, "cudaEventCreate failed"));
+
   // ---- uploads ----
   std::vector<int> perm_pad(S.n_pad, 0);
   std::copy(S.perm.begin(), S.perm.end(), perm_pad.begin());
@@ -506,7 +542,7 @@ pfc_status pfc_assemble(pfc_ctx* c, const double* state, double tau) {
   pfc_status st = check_ctx(c);
   if (st != PFC_OK) return st;
   if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "state must be non-null and tau > 0");
-  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, state, c->xk, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, state, c->xk, c->stream));
   return assemble_internal(c, tau);
 }
 
@@ -517,12 +553,12 @@ pfc_status pfc_stage_rhs(pfc_ctx* c, int nprev, const double* x_stage, const dou
   if (nprev < 0 || nprev > 2 || !x_stage || !b || (nprev > 0 && !y_prev))
     return fail(c, PFC_ERR_INVALID, "bad stage_rhs arguments");
   const size_t n3 = 3 * (size_t)c->n;
-  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, x_stage, c->xi, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, x_stage, c->xi, c->stream));
   for (int j = 0; j < nprev; ++j)
-    CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, y_prev + j * n3, c->ys + (size_t)j * 3 * c->n_pad, c->stream));
+    LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, y_prev + j * n3, c->ys + (size_t)j * 3 * c->n_pad, c->stream));
   st = stage_rhs_internal(c, nprev);
   if (st != PFC_OK) return st;
-  CK(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->bv, b, c->stream));
+  LAUNCH(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->bv, b, c->stream));
   return PFC_OK;
 }
 
@@ -531,17 +567,18 @@ pfc_status pfc_stage_solve(pfc_ctx* c, const double* b, double* y, pfc_solve_sta
   if (st != PFC_OK) return st;
   if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
   if (!b || !y) return fail(c, PFC_ERR_INVALID, "null vector");
-  CK(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, b, c->bv, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, b, c->bv, c->stream));
   pfc::SolveArgs a = base_args(c, c->prec);
   a.mode = 0;
   a.b = c->bv;
   a.y = c->tmp3;
   st = run_solver(c, a, c->prec, 0);
   if (st != PFC_OK) return st;
-  CK(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->tmp3, y, c->stream));
+  LAUNCH(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->tmp3, y, c->stream));
   CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   fill_stats(c->h_stats[0], c->h_errw[0], stats);
   st = status_from_err(c->h_errw[0]);
   if (st != PFC_OK) return fail(c, st, std::string("stage solve: ") + pfc_status_string(st));
@@ -554,15 +591,15 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   if (!state || !tau || !(*tau > 0.0) || !std::isfinite(*tau)) return fail(c, PFC_ERR_INVALID, "bad step arguments");
   const int np = c->n_pad;
   const size_t np3 = 3 * (size_t)np;
-  CK(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
   st = assemble_internal(c, *tau);
   if (st != PFC_OK) return st;
   for (int i = 0; i < 3; ++i) {
-    CK(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1], c->xi,
+    LAUNCH(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1], c->xi,
                                  c->dvec, c->stream));
     // d = sum_j c_ij dpsi_j comes from stage_combine; the RHS kernel reads it
-    CK(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
-    CK(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
+    LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+    LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
                        i > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
     pfc::SolveArgs a = base_args(c, c->prec);
     a.mode = 0;
@@ -573,13 +610,14 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   }
   double e[3];
   for (int j = 0; j < 3; ++j) e[j] = kMhat[j] - kM[j];
-  CK(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
+  LAUNCH(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
                               c->xnew, c->step_part, pfc::step_partials(), c->stream));
-  CK(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
+  LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
   CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   int werr = 0;
   for (int i = 0; i < 3; ++i) {
     fill_stats(c->h_stats[i], c->h_errw[i], stats ? stats + i : nullptr);
@@ -594,7 +632,7 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   }
   const bool acc = ev <= 1.0 && st == PFC_OK;
   if (accepted) *accepted = acc ? 1 : 0;
-  if (acc) CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
+  if (acc) LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
   double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
   *tau = std::min(*tau * fac, c->opt.tau_max);
   if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
@@ -609,11 +647,11 @@ pfc_status pfc_init_state(pfc_ctx* c, const double* psi0, double* state) {
   double* mu = c->xk;
   double* psi = c->xk + np;
   double* om = c->xk + 2 * np;
-  CK(pfc::launch_gather_in(c->n, np, 1, c->perm, psi0, psi, c->stream));
-  CK(pfc::launch_elem_load(c->dim, c->E, c->elem, psi, c->vol, c->ebuf, c->stream));
-  CK(pfc::launch_dof_gather(np, c->dptr, c->didx, c->ebuf, c->lvec, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, np, 1, c->perm, psi0, psi, c->stream));
+  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, psi, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_dof_gather(np, c->dptr, c->didx, c->ebuf, c->lvec, c->stream));
   // M omega = -K psi
-  CK(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 0.0, nullptr, -1.0, psi, 0.0, nullptr, 0.0,
+  LAUNCH(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 0.0, nullptr, -1.0, psi, 0.0, nullptr, 0.0,
                             nullptr, c->tmpn, c->stream));
   pfc::SolveArgs a = base_args(c, 0);
   a.mode = 2;
@@ -625,14 +663,15 @@ pfc_status pfc_init_state(pfc_ctx* c, const double* psi0, double* state) {
   st = run_solver(c, a, 0, 3);
   if (st != PFC_OK) return st;
   // M mu = l(psi^3) + (1+r) M psi - 2 K psi - K omega
-  CK(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 1.0 + c->opt.r, psi, -2.0, psi, -1.0, om,
+  LAUNCH(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 1.0 + c->opt.r, psi, -2.0, psi, -1.0, om,
                             1.0, c->lvec, c->tmpn, c->stream));
   a.y = mu;
   st = run_solver(c, a, 0, 3);
   if (st != PFC_OK) return st;
-  CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xk, state, c->stream));
+  LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xk, state, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   st = status_from_err(c->h_errw[0]);
   if (st != PFC_OK) return fail(c, st, "consistent initialisation failed");
   return PFC_OK;
@@ -646,29 +685,30 @@ pfc_status pfc_apply(pfc_ctx* c, int op, const double* x, double* y) {
     return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
   const int np = c->n_pad;
   if (op == PFC_OP_M || op == PFC_OP_K || op == PFC_OP_A01) {
-    CK(pfc::launch_gather_in(c->n, np, 1, c->perm, x, c->tmp3, c->stream));
+    LAUNCH(pfc::launch_gather_in(c->n, np, 1, c->perm, x, c->tmp3, c->stream));
     const double* vals = op == PFC_OP_M ? c->Mv : op == PFC_OP_K ? c->Kv : c->Av;
-    CK(pfc::launch_spmv(c->nslices, c->slice_ptr, c->cols, vals, c->tmp3, c->xnew, c->stream));
-    CK(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, y, c->stream));
+    LAUNCH(pfc::launch_spmv(c->nslices, c->slice_ptr, c->cols, vals, c->tmp3, c->xnew, c->stream));
+    LAUNCH(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_AR) {
-    CK(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
-    CK(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / kGamma, c->tmp3,
+    LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
+    LAUNCH(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / kGamma, c->tmp3,
                            c->xnew, c->stream));
-    CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
+    LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_PCH) {
-    CK(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
+    LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
     pfc::SolveArgs a = base_args(c, c->prec);
     a.mode = 1;
     a.b = c->tmp3;
     a.y = c->xnew;
     st = run_solver(c, a, c->prec, 0);
     if (st != PFC_OK) return st;
-    CK(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
+    LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
   } else {
     return fail(c, PFC_ERR_INVALID, "unknown operator");
   }
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   st = op == PFC_OP_PCH ? status_from_err(c->h_errw[0]) : PFC_OK;
   if (st != PFC_OK) return fail(c, st, "preconditioner application failed");
   return PFC_OK;
@@ -680,7 +720,7 @@ pfc_status pfc_pcg(pfc_ctx* c, int which, const double* b, double* x, double rto
   if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
   if (!b || !x || which < 0 || which > 2 || !(rtol > 0.0)) return fail(c, PFC_ERR_INVALID, "bad pcg arguments");
   const int np = c->n_pad;
-  CK(pfc::launch_gather_in(c->n, np, 1, c->perm, b, c->tmp3, c->stream));
+  LAUNCH(pfc::launch_gather_in(c->n, np, 1, c->perm, b, c->tmp3, c->stream));
   pfc::SolveArgs a = base_args(c, c->prec);
   a.mode = 2;
   a.which = which;
@@ -689,10 +729,11 @@ pfc_status pfc_pcg(pfc_ctx* c, int which, const double* b, double* x, double rto
   a.y = c->xnew;
   st = run_solver(c, a, c->prec, 0);
   if (st != PFC_OK) return st;
-  CK(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, x, c->stream));
+  LAUNCH(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, x, c->stream));
   CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   if (iterations) *iterations = c->h_stats[0].last_its;
   st = status_from_err(c->h_errw[0]);
   if (st != PFC_OK) return fail(c, st, "pcg failed");
@@ -716,7 +757,23 @@ pfc_status pfc_selftest_barrier_timeout(pfc_ctx* c, double limit_seconds) {
   if (st != PFC_OK) return st;
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
   return status_from_err(c->h_errw[0]);
+}
+
+pfc_status pfc_set_timing(pfc_ctx* c, int enable) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  c->timing = enable != 0;
+  return PFC_OK;
+}
+
+pfc_status pfc_counters(const pfc_ctx* c, long long* launches, long long* solver_launches, double* solver_ms) {
+  if (!c) return PFC_ERR_INVALID;
+  if (launches) *launches = c->launches;
+  if (solver_launches) *solver_launches = c->solver_launches;
+  if (solver_ms) *solver_ms = c->solver_ms;
+  return PFC_OK;
 }
 
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4) {
