@@ -67,6 +67,9 @@ typedef struct {
   double step_rtol;
   double tau_max;     /* upper bound for the next time-step width */
   int blocks_per_sm;  /* persistent-kernel residency; 0 = as many as fit */
+  int pcg_variant;    /* inner CG form: 0 textbook Jacobi-PCG (3 grid barriers per
+                         iteration), 1 pipelined Jacobi-PCG of Ghysels & Vanroose
+                         (same iterates in exact arithmetic, 1 barrier per iteration) */
 } pfc_options;
 
 typedef struct {
@@ -77,11 +80,14 @@ typedef struct {
   int inner_capped;     /* PCG solves that hit max_inner */
   double rel_residual;  /* final true ||b - A^R y||_2 / ||b||_2, recomputed in float64 */
   int status;           /* pfc_status of this solve */
+  double phase_ms[8];   /* with pfc_set_timing on: block 0's time in [inner SpMV phases,
+                           inner vector phases, outer FGMRES phases, PCG set-up phases]
+                           (work), then the same four classes of barrier waits */
 } pfc_solve_stats;
 
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
- * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0. */
+ * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 1. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

@@ -34,13 +34,13 @@ class _Options(ctypes.Structure):
     _fields_ = [("r", ctypes.c_double), ("outer_tol", ctypes.c_double), ("inner_rtol", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("precision", ctypes.c_int), ("step_atol", ctypes.c_double), ("step_rtol", ctypes.c_double),
-                ("tau_max", ctypes.c_double), ("blocks_per_sm", ctypes.c_int)]
+                ("tau_max", ctypes.c_double), ("blocks_per_sm", ctypes.c_int), ("pcg_variant", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("outer_its", ctypes.c_int), ("restarts", ctypes.c_int), ("inner_its", ctypes.c_longlong),
                 ("inner_calls", ctypes.c_int), ("inner_capped", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int)]
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int), ("phase_ms", ctypes.c_double * 8)]
 
 
 def _load():
@@ -96,10 +96,12 @@ class SolveStats:
     inner_capped: int
     rel_residual: float
     status: int
+    phase_ms: tuple = ()
 
     @classmethod
     def _from(cls, s: _Stats) -> "SolveStats":
-        return cls(s.outer_its, s.restarts, s.inner_its, s.inner_calls, s.inner_capped, s.rel_residual, s.status)
+        return cls(s.outer_its, s.restarts, s.inner_its, s.inner_calls, s.inner_capped, s.rel_residual, s.status,
+                   tuple(s.phase_ms))
 
 
 def critical_tau(r: float, psi_bar: float) -> float:
@@ -137,7 +139,7 @@ class PFCSolver:
     def __init__(self, dim: int, side: int, length: float, r: float = -0.4, precision: str = "fp64",
                  outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
-                 tau_max: float = 1e9, blocks_per_sm: int = 0, stream=None):
+                 tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 1, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -151,6 +153,7 @@ class PFCSolver:
         o.restart, o.max_outer, o.max_inner = restart, max_outer, max_inner
         o.precision = PRECISIONS[precision]
         o.step_atol, o.step_rtol, o.tau_max, o.blocks_per_sm = step_atol, step_rtol, tau_max, blocks_per_sm
+        o.pcg_variant = pcg_variant
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -73,7 +73,7 @@ struct pfc_ctx {
   // control
   unsigned* arrive = nullptr;
   int* errw = nullptr;
-  double2* part = nullptr;
+  double4* part = nullptr;
   pfc::DevStats* stats = nullptr;   // 4 slots
   double* step_part = nullptr;
   double* err_scalar = nullptr;
@@ -160,6 +160,8 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.stats = c->stats;
   a.spin_limit_ns = 2000000000ULL;
   a.barrier_extra = 0;
+  a.pcg_variant = c->opt.pcg_variant;
+  a.prof = c->timing ? 1 : 0;
   return a;
 }
 
@@ -206,6 +208,7 @@ void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
   s->inner_capped = d.inner_capped;
   s->rel_residual = d.rel_residual;
   s->status = status_from_err(err);
+  for (int k = 0; k < 8; ++k) s->phase_ms[k] = d.prof_ns[k] * 1e-6;
 }
 
 // b_i^R for stage nprev from c->xi (stage value) and the increments c->ys.
@@ -258,6 +261,7 @@ void pfc_default_options(pfc_options* o) {
   o->step_rtol = 1e-3;
   o->tau_max = 1e9;
   o->blocks_per_sm = 0;
+  o->pcg_variant = 1;
 }
 
 const char* pfc_status_string(int s) {
@@ -318,6 +322,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (c->opt.restart < 1 || c->opt.restart > pfc::kMaxRestart)
     return bail(fail(c, PFC_ERR_INVALID, "restart must be in 1..40"));
   if (c->opt.precision < 0 || c->opt.precision > 2) return bail(fail(c, PFC_ERR_INVALID, "precision must be 0, 1 or 2"));
+  if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 1) return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0 or 1"));
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
     return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
   c->stream = (cudaStream_t)cuda_stream;
@@ -412,11 +417,11 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_ebuf = L.take(sizeof(double) * (size_t)c->np * c->E);
   const size_t o_V = L.take(sizeof(double) * np3 * (c->opt.restart + 1));
   const size_t o_Z = L.take(sizeof(double) * np3 * c->opt.restart);
-  const size_t o_ivec = L.take(8 * (size_t)c->n_pad * 8);
+  const size_t o_ivec = L.take((size_t)pfc::kInnerVecs * c->n_pad * 8);
   const size_t vec_end = L.take(0);
   const size_t o_arr = L.take(sizeof(unsigned) * 4);
   const size_t o_errw = L.take(sizeof(int) * 8);
-  const size_t o_part = L.take(sizeof(double2) * pfc::solve_ring() * c->G);
+  const size_t o_part = L.take(sizeof(double4) * pfc::solve_ring() * c->G);
   const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);
   const size_t o_sp = L.take(sizeof(double) * pfc::step_partials());
   const size_t o_es = L.take(sizeof(double) * 2);
@@ -474,7 +479,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->ivec = (void*)(A + o_ivec);
   c->arrive = (unsigned*)(A + o_arr);
   c->errw = (int*)(A + o_errw);
-  c->part = (double2*)(A + o_part);
+  c->part = (double4*)(A + o_part);
   c->stats = (pfc::DevStats*)(A + o_stats);
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);

@@ -26,6 +26,7 @@ struct DevStats {
   double bnorm;
   int err;
   int last_its;        // iterations of a single PCG solve (pcg mode)
+  long long prof_ns[8];  // block 0: work / barrier-wait time per phase class (when profiling)
 };
 
 // Arguments of the persistent solver kernel.  Inner arrays are typed by the
@@ -54,14 +55,18 @@ struct SolveArgs {
   double* y;
   double* V;               // (restart + 1) x 3 n_pad
   double* Z;               // restart x 3 n_pad
-  void* ivec;              // 8 inner vectors of n_pad TV each
+  void* ivec;              // kInnerVecs inner vectors of n_pad TV each
   unsigned* arrive;        // grid barrier counter (zeroed before each launch)
   int* err;                // error word (zeroed before each launch)
-  double2* part;           // reduction partials, kRing x gridDim.x
+  double4* part;           // reduction partials, kRing x gridDim.x
   DevStats* stats;
   unsigned long long spin_limit_ns;  // a barrier wait gives up after this long
   int barrier_extra;       // 0; > 0 only in the timeout self-test (waits cannot complete)
+  int pcg_variant;         // 0 standard PCG (3 grid barriers per iteration), 1 pipelined PCG (1)
+  int prof;                // 1: block 0 records per-phase work and wait times
 };
+
+constexpr int kInnerVecs = 16;
 
 template <class T> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };

@@ -19,13 +19,23 @@
 // GB300 design.  The grid is co-resident (cooperative launch, a multiple of the
 // SM count), every block owns a contiguous, nnz-balanced range of SELL-32 slices
 // and the same rows of every vector, and the phases of the algorithm are
-// separated by a grid barrier with a bounded spin.  Dot products reduce in a
-// fixed order (warp shuffles, then block partials summed identically by every
-// block), so all blocks take the same branch decisions and repeated runs are
-// bitwise identical.  The scalar Arnoldi/Givens work is done redundantly by
-// thread 0 of every block in shared memory.  A vector that another block reads
-// (the PCG direction p, the preconditioned basis vector z_j, the iterate y) is
-// only read after a barrier; everything else is touched by its owner only.
+// separated by a grid barrier with a time-bounded spin.  Inside a phase each warp
+// takes groups of kGroup consecutive slices and issues the loads of all of them
+// before it consumes any, so enough bytes are in flight to cover HBM latency.
+// Dot products reduce in a fixed order (warp shuffles, then block partials
+// summed identically by every block), so all blocks take the same branch
+// decisions and repeated runs are bitwise identical.  The scalar Arnoldi/Givens
+// work is done redundantly by thread 0 of every block in shared memory.  A
+// vector that another block reads (the PCG direction, the preconditioned basis
+// vector z_j, the iterate y) is only read after a barrier; everything else is
+// touched by its owner only.
+//
+// The inner CG comes in two arithmetically equivalent forms: the textbook
+// Jacobi-PCG (three barriers per iteration: after q = A p with p.q, after the
+// x/r update with r.z, after the p update), and the pipelined PCG of Ghysels and
+// Vanroose (Parallel Computing 40, 2014), which carries w = A u and m = D w as
+// extra recurrences so that one pass does the SpMV, every vector update and all
+// partial dot products, leaving one barrier per iteration.
 #include <cuda_fp16.h>
 
 #include "device.cuh"
@@ -38,18 +48,32 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 4;
+constexpr int kGroup = 4;   // slices a warp works on at once
+
+// phase classes for the optional profile
+enum : int { kPhSpmv = 0, kPhVec = 1, kPhOuter = 2, kPhInit = 3 };
 
 struct Grid {
   unsigned* arrive;
+  double4* part;
   int* err;
-  double2* part;
   unsigned long long limit_ns;
   int G;
   int expect;      // blocks that arrive at each barrier (G, or more in the timeout self-test)
   unsigned epoch;  // thread 0 only
   int ring;
   int s_lo, s_hi;
+  bool prof;       // block 0, thread 0 (accumulators live in shared memory)
 };
+
+__shared__ unsigned long long s_t_last;
+__shared__ long long s_prof[8];
+
+// Warp-group iteration over this block's slices: groups of kGroup consecutive
+// slices, interleaved across warps.  Inside, rows (s0 + u) * 32 + lane, u < nsl.
+#define FOR_MY_GROUPS(g, s0, nsl)                                                                  \
+  for (int s0 = (g).s_lo + (int)(threadIdx.x >> 5) * kGroup; s0 < (g).s_hi; s0 += kWarps * kGroup) \
+    if (const int nsl = min(kGroup, (g).s_hi - s0); true)
 
 #define FOR_MY_SLICES(g, s) for (int s = (g).s_lo + (int)(threadIdx.x >> 5); s < (g).s_hi; s += kWarps)
 
@@ -63,10 +87,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // completes when the counter reaches k * G.  The wait is bounded in time: after
 // limit_ns the block sets the timeout bit and the kernel unwinds (false), as it
 // does when another block has already flagged a timeout.
-__device__ bool grid_sync(Grid& g) {
+__device__ bool grid_sync(Grid& g, int tag) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    unsigned long long t_in = 0;
+    if (g.prof) {
+      t_in = global_ns();
+      s_prof[tag] += (long long)(t_in - s_t_last);
+    }
     g.epoch += 1;
     const unsigned target = g.epoch * (unsigned)g.expect;
     __threadfence();
@@ -85,43 +114,56 @@ __device__ bool grid_sync(Grid& g) {
           break;
         }
       }
-      __nanosleep(64);
+      __nanosleep(32);
     }
     __threadfence();
     if (ok && (ld_relaxed_i32(g.err) & kErrTimeout)) ok = 0;
     s_ok = ok;
+    if (g.prof) {
+      s_t_last = global_ns();
+      s_prof[4 + tag] += (long long)(s_t_last - t_in);
+    }
   }
   __syncthreads();
   return s_ok != 0;
 }
 
-// Sum of (a, b) over all threads of the grid, identical in every block.
-__device__ bool grid_sum2(Grid& g, double a, double b, double2& out) {
-  __shared__ double2 s_w[kWarps];
-  __shared__ double2 s_res;
+// Sum of up to three values over all threads of the grid, identical in every block.
+__device__ bool grid_sum(Grid& g, double a, double b, double c, double4& out, int tag) {
+  __shared__ double4 s_w[kWarps];
+  __shared__ double4 s_res;
   a = warp_sum(a);
   b = warp_sum(b);
+  c = warp_sum(c);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) s_w[w] = make_double2(a, b);
+  if (l == 0) s_w[w] = make_double4(a, b, c, 0.0);
   __syncthreads();
   const int slot = g.ring;
   g.ring = (g.ring + 1) % kRing;
   if (w == 0) {
-    double2 t = l < kWarps ? s_w[l] : make_double2(0.0, 0.0);
+    double4 t = l < kWarps ? s_w[l] : make_double4(0.0, 0.0, 0.0, 0.0);
     t.x = warp_sum(t.x);
     t.y = warp_sum(t.y);
-    if (l == 0) __stcg(&g.part[slot * g.G + blockIdx.x], t);
+    t.z = warp_sum(t.z);
+    if (l == 0) {
+      double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + blockIdx.x);
+      __stcg(dst, make_double2(t.x, t.y));
+      __stcg(dst + 1, make_double2(t.z, 0.0));
+    }
   }
-  if (!grid_sync(g)) return false;
+  if (!grid_sync(g, tag)) return false;
   if (w == 0) {
-    double2 acc = make_double2(0.0, 0.0);
+    double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
     for (int i = l; i < g.G; i += 32) {
-      const double2 t = __ldcg(&g.part[slot * g.G + i]);
-      acc.x += t.x;
-      acc.y += t.y;
+      const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + i);
+      const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
+      acc.x += t0.x;
+      acc.y += t0.y;
+      acc.z += t1.x;
     }
     acc.x = warp_sum(acc.x);
     acc.y = warp_sum(acc.y);
+    acc.z = warp_sum(acc.z);
     if (l == 0) s_res = acc;
   }
   __syncthreads();
@@ -131,6 +173,39 @@ __device__ bool grid_sum2(Grid& g, double a, double b, double2& out) {
 
 __device__ __forceinline__ void flag(Grid& g, int bit) {
   if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.err, bit);
+}
+
+// One SELL-32 row (lane = row of slice s) times x, loading CH column indices and
+// values of the row before any of the CH gathers, so a row of up to CH
+// nonzeros costs two dependent memory round trips.
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ Acc sell_row_wide(const int* __restrict__ sp, const int* __restrict__ cols,
+                                             const TM* __restrict__ vals, const TX* x, int s, int lane) {
+  constexpr int CH = sizeof(Acc) == 8 ? 10 : 20;
+  const int b = __ldg(sp + s);
+  const int w = (__ldg(sp + s + 1) - b) >> 5;
+  const int beg = b + lane;
+  Acc acc = Acc(0);
+  for (int j0 = 0; j0 < w; j0 += CH) {
+    int cc[CH];
+    Acc vv[CH];
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) {
+      cc[jj] = 0;
+      vv[jj] = Acc(0);
+      if (j0 + jj < w) {
+        const int idx = beg + (j0 + jj) * 32;
+        cc[jj] = __ldg(cols + idx);
+        vv[jj] = ld_val<Acc>(vals + idx);
+      }
+    }
+    Acc xv[CH];
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) xv[jj] = (j0 + jj < w) ? (Acc)x[cc[jj]] : Acc(0);
+#pragma unroll
+    for (int jj = 0; jj < CH; ++jj) acc = fma(vv[jj], xv[jj], acc);
+  }
+  return acc;
 }
 
 struct InnerCount {
@@ -143,60 +218,51 @@ template <class TM, class TV>
 struct Ctx {
   using Acc = typename AccOf<TV>::type;
   const SolveArgs& a;
-  const TM* iM;
-  const TM* iK;
-  const TM* iMdK;
-  const TM* iMsK;
-  const TV* dM;
-  const TV* dMdK;
-  const TV* dMsK;
-  TV *r, *p, *q, *y0, *y1, *wv, *x1, *x2;
-  __device__ explicit Ctx(const SolveArgs& args) : a(args) {
-    iM = (const TM*)a.iM;
-    iK = (const TM*)a.iK;
-    iMdK = (const TM*)a.iMdK;
-    iMsK = (const TM*)a.iMsK;
-    dM = (const TV*)a.dM;
-    dMdK = (const TV*)a.dMdK;
-    dMsK = (const TV*)a.dMsK;
-    TV* base = (TV*)a.ivec;
-    const int np = a.n_pad;
-    r = base;
-    p = base + np;
-    q = base + 2 * np;
-    y0 = base + 3 * np;
-    y1 = base + 4 * np;
-    wv = base + 5 * np;
-    x1 = base + 6 * np;
-    x2 = base + 7 * np;
-  }
+  __device__ explicit Ctx(const SolveArgs& args) : a(args) {}
+  __device__ __forceinline__ const TM* iM() const { return (const TM*)a.iM; }
+  __device__ __forceinline__ const TM* iK() const { return (const TM*)a.iK; }
+  __device__ __forceinline__ const TM* iMdK() const { return (const TM*)a.iMdK; }
+  __device__ __forceinline__ const TM* iMsK() const { return (const TM*)a.iMsK; }
+  __device__ __forceinline__ const TV* dM() const { return (const TV*)a.dM; }
+  __device__ __forceinline__ const TV* dMdK() const { return (const TV*)a.dMdK; }
+  __device__ __forceinline__ const TV* dMsK() const { return (const TV*)a.dMsK; }
+  // inner vectors: PCG work vectors 0..8 (textbook form uses r, p, q), step outputs 9..13
+  __device__ __forceinline__ TV* vec(int k) const { return (TV*)a.ivec + (size_t)k * a.n_pad; }
 };
 
-// Jacobi-PCG for A x = rhs, x0 = 0, stop at ||r||_2 <= rtol ||rhs||_2.
+enum : int { kVr = 0, kVp = 1, kVq = 2, kVu = 3, kVw = 4, kVm0 = 5, kVm1 = 6, kVz = 7, kVs = 8,
+             kVy0 = 9, kVy1 = 10, kVwv = 11, kVx1 = 12, kVx2 = 13 };
+
+// Textbook Jacobi-PCG for A x = rhs, x0 = 0, stop at ||r||_2 <= rtol ||rhs||_2.
 // rhs(s, lane, row) is evaluated once per owned row in the first phase (it may
 // run a SpMV over vectors completed before the call).
 template <class TM, class TV, class RhsF>
-__device__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs, double rtol,
-                    int maxit, InnerCount& cnt, int& its) {
+__device__ bool pcg_standard(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs, double rtol,
+                             int maxit, InnerCount& cnt, int& its) {
   using Acc = typename Ctx<TM, TV>::Acc;
   const SolveArgs& a = c.a;
-  TV* r = c.r;
-  TV* p = c.p;
-  TV* q = c.q;
+  TV* r = c.vec(kVr);
+  TV* p = c.vec(kVp);
+  TV* q = c.vec(kVq);
   const int lane = threadIdx.x & 31;
   double pb = 0.0, pz = 0.0;
-  FOR_MY_SLICES(g, s) {
-    const int row = s * 32 + lane;
-    const TV rv = (TV)rhs(s, lane, row);
-    const TV z = (TV)((Acc)DI[row] * (Acc)rv);
-    x[row] = TV(0);
-    r[row] = rv;
-    p[row] = z;
-    pb += (double)rv * (double)rv;
-    pz += (double)rv * (double)z;
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int s = s0 + uu, row = s * 32 + lane;
+        const TV rv = (TV)rhs(s, lane, row);
+        const TV zz = (TV)((Acc)DI[row] * (Acc)rv);
+        x[row] = TV(0);
+        r[row] = rv;
+        p[row] = zz;
+        pb += (double)rv * (double)rv;
+        pz += (double)rv * (double)zz;
+      }
+    }
   }
-  double2 red;
-  if (!grid_sum2(g, pb, pz, red)) return false;
+  double4 red;
+  if (!grid_sum(g, pb, pz, 0.0, red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -211,11 +277,11 @@ __device__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, 
     double ppq = 0.0;
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
-      const TV qv = (TV)sell_row<Acc>(a.slice_ptr, a.cols, AV, p, s, lane);
+      const TV qv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, p, s, lane);
       q[row] = qv;
       ppq += (double)p[row] * (double)qv;
     }
-    if (!grid_sum2(g, ppq, 0.0, red)) return false;
+    if (!grid_sum(g, ppq, 0.0, 0.0, red, kPhSpmv)) return false;
     const double pq = red.x;
     if (!isfinite(pq)) {
       flag(g, kErrNonfinite);
@@ -229,17 +295,34 @@ __device__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, 
     }
     const Acc alpha = (Acc)(rz / pq);
     double prr = 0.0, prz = 0.0;
-    FOR_MY_SLICES(g, s) {
-      const int row = s * 32 + lane;
-      const Acc xn = (Acc)x[row] + alpha * (Acc)p[row];
-      const Acc rn = (Acc)r[row] - alpha * (Acc)q[row];
-      x[row] = (TV)xn;
-      r[row] = (TV)rn;
-      const Acc z = (Acc)DI[row] * rn;
-      prr += (double)rn * (double)rn;
-      prz += (double)rn * (double)z;
+    FOR_MY_GROUPS(g, s0, nsl) {
+      TV xv[kGroup], pv[kGroup], qv[kGroup], rv[kGroup], dv[kGroup];
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          xv[uu] = x[row];
+          pv[uu] = p[row];
+          qv[uu] = q[row];
+          rv[uu] = r[row];
+          dv[uu] = DI[row];
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc xn = (Acc)xv[uu] + alpha * (Acc)pv[uu];
+          const Acc rn = (Acc)rv[uu] - alpha * (Acc)qv[uu];
+          x[row] = (TV)xn;
+          r[row] = (TV)rn;
+          const Acc zz = (Acc)dv[uu] * rn;
+          prr += (double)rn * (double)rn;
+          prz += (double)rn * (double)zz;
+        }
+      }
     }
-    if (!grid_sum2(g, prr, prz, red)) return false;
+    if (!grid_sum(g, prr, prz, 0.0, red, kPhVec)) return false;
     its = it;
     if (!isfinite(red.x)) {
       flag(g, kErrNonfinite);
@@ -251,15 +334,175 @@ __device__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, 
     }
     const Acc beta = (Acc)(red.y / rz);
     rz = red.y;
-    FOR_MY_SLICES(g, s) {
-      const int row = s * 32 + lane;
-      p[row] = (TV)((Acc)DI[row] * (Acc)r[row] + beta * (Acc)p[row]);
+    FOR_MY_GROUPS(g, s0, nsl) {
+      TV dv[kGroup], rv[kGroup], pv[kGroup];
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          dv[uu] = DI[row];
+          rv[uu] = r[row];
+          pv[uu] = p[row];
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          p[row] = (TV)((Acc)dv[uu] * (Acc)rv[uu] + beta * (Acc)pv[uu]);
+        }
+      }
     }
-    if (!grid_sync(g)) return false;
+    if (!grid_sync(g, kPhVec)) return false;
   }
   cnt.its += maxit;
   cnt.capped += 1;
   return true;
+}
+
+// Pipelined Jacobi-PCG (Ghysels-Vanroose): the same iterates as pcg_standard in
+// exact arithmetic.  Per iteration one pass computes n = A m, the recurrences
+//   z = n + b z, q = m + b q, s = w + b s, p = u + b p,
+//   x += a p, r -= a s, u -= a q, w -= a z, m' = D w
+// and the partial sums of (r, u), (w, u), (r, r); one barrier follows.
+template <class TM, class TV, class RhsF>
+__device__ bool pcg_pipelined(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs, double rtol,
+                              int maxit, InnerCount& cnt, int& its) {
+  using Acc = typename Ctx<TM, TV>::Acc;
+  const SolveArgs& a = c.a;
+  TV* r = c.vec(kVr);
+  TV* u = c.vec(kVu);
+  TV* w = c.vec(kVw);
+  TV* zv = c.vec(kVz);
+  TV* qv = c.vec(kVq);
+  TV* sv = c.vec(kVs);
+  TV* pv = c.vec(kVp);
+  TV* mcur = c.vec(kVm0);
+  TV* mnext = c.vec(kVm1);
+  const int lane = threadIdx.x & 31;
+  // r = b, u = D r, x = 0; recurrences start at zero
+  double pb = 0.0;
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int s = s0 + uu, row = s * 32 + lane;
+        const TV rv = (TV)rhs(s, lane, row);
+        x[row] = TV(0);
+        r[row] = rv;
+        u[row] = (TV)((Acc)DI[row] * (Acc)rv);
+        zv[row] = TV(0);
+        qv[row] = TV(0);
+        sv[row] = TV(0);
+        pv[row] = TV(0);
+        pb += (double)rv * (double)rv;
+      }
+    }
+  }
+  double4 red;
+  if (!grid_sum(g, pb, 0.0, 0.0, red, kPhInit)) return false;
+  its = 0;
+  cnt.calls += 1;
+  const double bb = red.x;
+  if (!isfinite(bb)) {
+    flag(g, kErrNonfinite);
+    return false;
+  }
+  if (bb == 0.0) return true;
+  const double thr = rtol * rtol * bb;
+  // w = A u, m = D w, partial (r, u), (w, u)
+  double pg = 0.0, pd = 0.0;
+  FOR_MY_SLICES(g, s) {
+    const int row = s * 32 + lane;
+    const TV wvv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, u, s, lane);
+    const TV uvv = u[row];
+    w[row] = wvv;
+    mcur[row] = (TV)((Acc)DI[row] * (Acc)wvv);
+    pg += (double)r[row] * (double)uvv;
+    pd += (double)wvv * (double)uvv;
+  }
+  if (!grid_sum(g, pg, pd, 0.0, red, kPhSpmv)) return false;
+  double gamma = red.x, delta = red.y, gamma_old = 1.0, alpha_old = 1.0;
+  for (int it = 0; it < maxit; ++it) {
+    if (!isfinite(gamma) || !isfinite(delta)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    double beta, alpha;
+    if (it == 0) {
+      beta = 0.0;
+      alpha = gamma / delta;
+    } else {
+      beta = gamma / gamma_old;
+      alpha = gamma / (delta - beta * gamma / alpha_old);
+    }
+    if (!(delta > 0.0) || !isfinite(alpha)) {
+      flag(g, kErrBreakdown);
+      its = it;
+      cnt.its += it;
+      return true;
+    }
+    const Acc al = (Acc)alpha, be = (Acc)beta;
+    double prg = 0.0, pwd = 0.0, prr = 0.0;
+    FOR_MY_SLICES(g, s) {
+      const int row = s * 32 + lane;
+      const Acc na = sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, mcur, s, lane);
+      const Acc mv = (Acc)mcur[row];
+      const Acc z1 = na + be * (Acc)zv[row];
+      const Acc q1 = mv + be * (Acc)qv[row];
+      const Acc s1 = (Acc)w[row] + be * (Acc)sv[row];
+      const Acc p1 = (Acc)u[row] + be * (Acc)pv[row];
+      const Acc x1 = (Acc)x[row] + al * p1;
+      const Acc r1 = (Acc)r[row] - al * s1;
+      const Acc u1 = (Acc)u[row] - al * q1;
+      const Acc w1 = (Acc)w[row] - al * z1;
+      zv[row] = (TV)z1;
+      qv[row] = (TV)q1;
+      sv[row] = (TV)s1;
+      pv[row] = (TV)p1;
+      x[row] = (TV)x1;
+      r[row] = (TV)r1;
+      u[row] = (TV)u1;
+      w[row] = (TV)w1;
+      mnext[row] = (TV)((Acc)DI[row] * w1);
+      prg += (double)r1 * (double)u1;
+      pwd += (double)w1 * (double)u1;
+      prr += (double)r1 * (double)r1;
+    }
+    if (!grid_sum(g, prg, pwd, prr, red, kPhSpmv)) return false;
+    its = it + 1;
+    if (!isfinite(red.z)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    if (red.z <= thr) {
+      cnt.its += its;
+      return true;
+    }
+    gamma_old = gamma;
+    alpha_old = alpha;
+    gamma = red.x;
+    delta = red.y;
+    TV* t = mcur;
+    mcur = mnext;
+    mnext = t;
+  }
+  cnt.its += maxit;
+  cnt.capped += 1;
+  return true;
+}
+
+template <class TM, class TV, class RhsF>
+__device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs,
+                                    double rtol, int maxit, InnerCount& cnt, int& its) {
+  if (c.a.pcg_variant == 1) return pcg_pipelined(g, c, AV, DI, x, rhs, rtol, maxit, cnt, its);
+  return pcg_standard(g, c, AV, DI, x, rhs, rtol, maxit, cnt, its);
+}
+
+// One SELL row of a matrix with TM values times a TV vector, as Acc.
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ Acc one_row(const SolveArgs& a, const TM* vals, const TX* x, int s, int lane) {
+  return sell_row_wide<Acc>(a.slice_ptr, a.cols, vals, x, s, lane);
 }
 
 // z = P_CH^{-1} v for 3-field float64 vectors (n_pad per field).  Ends with a
@@ -277,44 +520,49 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
   const int mi = a.max_inner;
   int its;
   // (1) M y0 = v0
-  if (!pcg(g, c, c.iM, c.dM, c.y0, [&](int, int, int row) { return v0[row]; }, rt, mi, cnt, its)) return false;
+  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVy0), [&](int, int, int row) { return v0[row]; }, rt, mi, cnt, its)) return false;
   // (2) (M + delta K) y1 = gamma v1 - tau_e K y0
-  if (!pcg(g, c, c.iMdK, c.dMdK, c.y1,
+  if (!pcg(g, c, c.iMdK(), c.dMdK(), c.vec(kVy1),
            [&](int s, int ln, int row) {
-             const Acc ky = sell_row<Acc>(a.slice_ptr, a.cols, c.iK, c.y0, s, ln);
-             return a.gamma * v1[row] - a.tau_e * (double)ky;
+             return a.gamma * v1[row] - a.tau_e * (double)one_row<Acc>(a, c.iK(), c.vec(kVy0), s, ln);
            },
            rt, mi, cnt, its))
     return false;
   // (3.1) (M + sqrt(delta) K) w = M y1
-  if (!pcg(g, c, c.iMsK, c.dMsK, c.wv,
-           [&](int s, int ln, int) { return (double)sell_row<Acc>(a.slice_ptr, a.cols, c.iM, c.y1, s, ln); }, rt,
-           mi, cnt, its))
-    return false;
-  // (3.2) (M + sqrt(delta) K) x1 = M w
-  if (!pcg(g, c, c.iMsK, c.dMsK, c.x1,
-           [&](int s, int ln, int) { return (double)sell_row<Acc>(a.slice_ptr, a.cols, c.iM, c.wv, s, ln); }, rt,
-           mi, cnt, its))
-    return false;
-  // (4) x0 = y0 + (y1 - x1) / delta, and z = (x0, x1, .)
-  FOR_MY_SLICES(g, s) {
-    const int row = s * 32 + lane;
-    const double xx1 = (double)c.x1[row];
-    z[row] = (double)c.y0[row] + ((double)c.y1[row] - xx1) * a.inv_delta;
-    z[np + row] = xx1;
-  }
-  // (5) M x2 = v2 - K x1
-  if (!pcg(g, c, c.iM, c.dM, c.x2,
-           [&](int s, int ln, int row) {
-             return v2[row] - (double)sell_row<Acc>(a.slice_ptr, a.cols, c.iK, c.x1, s, ln);
-           },
+  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVwv), [&](int s, int ln, int) { return (double)one_row<Acc>(a, c.iM(), c.vec(kVy1), s, ln); },
            rt, mi, cnt, its))
     return false;
-  FOR_MY_SLICES(g, s) {
-    const int row = s * 32 + lane;
-    z[2 * np + row] = (double)c.x2[row];
+  // (3.2) (M + sqrt(delta) K) x1 = M w
+  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVx1), [&](int s, int ln, int) { return (double)one_row<Acc>(a, c.iM(), c.vec(kVwv), s, ln); },
+           rt, mi, cnt, its))
+    return false;
+  // (4) x0 = y0 + (y1 - x1) / delta, and z = (x0, x1, .)
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int row = (s0 + uu) * 32 + lane;
+        const double xx1 = (double)c.vec(kVx1)[row];
+        z[row] = (double)c.vec(kVy0)[row] + ((double)c.vec(kVy1)[row] - xx1) * a.inv_delta;
+        z[np + row] = xx1;
+      }
+    }
   }
-  return grid_sync(g);
+  // (5) M x2 = v2 - K x1
+  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVx2),
+           [&](int s, int ln, int row) { return v2[row] - (double)one_row<Acc>(a, c.iK(), c.vec(kVx1), s, ln); }, rt, mi, cnt,
+           its))
+    return false;
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int row = (s0 + uu) * 32 + lane;
+        z[2 * np + row] = (double)c.vec(kVx2)[row];
+      }
+    }
+  }
+  return grid_sync(g, kPhVec);
 }
 
 // w = A^R z for one owned row (float64, one column-index stream, three value streams).
@@ -324,7 +572,7 @@ __device__ __forceinline__ void block_row(const SolveArgs& a, const double* z, i
   const int beg = __ldg(a.slice_ptr + s) + lane;
   const int end = __ldg(a.slice_ptr + s + 1);
   double m_mu = 0, a_psi = 0, k_om = 0, k_mu = 0, m_psi = 0, k_psi = 0, m_om = 0;
-#pragma unroll 2
+#pragma unroll 4
   for (int idx = beg; idx < end; idx += 32) {
     const int c = __ldg(a.cols + idx);
     const double mv = __ldg(a.Mv + idx), kv = __ldg(a.Kv + idx), av = __ldg(a.Av + idx);
@@ -342,9 +590,8 @@ __device__ __forceinline__ void block_row(const SolveArgs& a, const double* z, i
   w2 = k_psi + m_om;
 }
 
-template <class TM, class TV>
-__device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts, const InnerCount& cnt,
-                            double rel, double bnorm, int last_its) {
+__device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts, const InnerCount& cnt, double rel,
+                            double bnorm, int last_its) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     DevStats st;
     st.outer_its = outer;
@@ -356,6 +603,7 @@ __device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts
     st.bnorm = bnorm;
     st.err = 0;
     st.last_its = last_its;
+    for (int k = 0; k < 8; ++k) st.prof_ns[k] = s_prof[k];
     *a.stats = st;
   }
 }
@@ -369,7 +617,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   const int np = a.n_pad, n3 = 3 * np, m = a.restart, ld = m + 1;
   const int lane = threadIdx.x & 31;
   InnerCount cnt;
-  double2 red;
+  double4 red;
   double pb = 0.0;
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
@@ -380,14 +628,14 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       a.y[f * np + row] = 0.0;
     }
   }
-  if (!grid_sum2(g, pb, 0.0, red)) return;
+  if (!grid_sum(g, pb, 0.0, 0.0, red, kPhOuter)) return;
   const double bnorm = sqrt(red.x);
   if (!isfinite(bnorm)) {
     flag(g, kErrNonfinite);
     return;
   }
   if (bnorm == 0.0) {
-    write_stats<TM, TV>(g, a, 0, 0, cnt, 0.0, 0.0, 0);
+    write_stats(g, a, 0, 0, cnt, 0.0, 0.0, 0);
     return;
   }
   int total = 0, restarts = 0;
@@ -406,7 +654,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       V0[2 * np + row] = r2;
       pr += r0 * r0 + r1 * r1 + r2 * r2;
     }
-    if (!grid_sum2(g, pr, 0.0, red)) return;
+    if (!grid_sum(g, pr, 0.0, 0.0, red, kPhOuter)) return;
     const double beta = sqrt(red.x);
     if (!isfinite(beta)) {
       flag(g, kErrNonfinite);
@@ -414,7 +662,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
     }
     if (beta <= a.tol * bnorm || total >= a.max_outer) {
       if (beta > a.tol * bnorm) flag(g, kErrOuterCap);
-      write_stats<TM, TV>(g, a, total, restarts, cnt, beta / bnorm, bnorm, 0);
+      write_stats(g, a, total, restarts, cnt, beta / bnorm, bnorm, 0);
       return;
     }
     first = false;
@@ -445,7 +693,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
         w[2 * np + row] = w2;
         ph += w0 * V0[row] + w1 * V0[np + row] + w2 * V0[2 * np + row];
       }
-      if (!grid_sum2(g, ph, 0.0, red)) return;
+      if (!grid_sum(g, ph, 0.0, 0.0, red, kPhOuter)) return;
       double hij = red.x;
       for (int i = 0; i <= j; ++i) {
         if (threadIdx.x == 0) H[i + j * ld] = hij;
@@ -461,7 +709,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
             pn += wv * (vn ? vn[f * np + row] : wv);
           }
         }
-        if (!grid_sum2(g, pn, 0.0, red)) return;
+        if (!grid_sum(g, pn, 0.0, 0.0, red, kPhOuter)) return;
         hij = red.x;
       }
       const double hnext = sqrt(hij);
@@ -516,12 +764,12 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       }
     }
     restarts += 1;
-    if (!grid_sync(g)) return;
+    if (!grid_sync(g, kPhOuter)) return;
   }
 }
 
 template <class TM, class TV>
-__global__ void __launch_bounds__(kThreads, 2) solve_kernel(const SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
   Grid g;
   g.arrive = a.arrive;
   g.err = a.err;
@@ -533,26 +781,31 @@ __global__ void __launch_bounds__(kThreads, 2) solve_kernel(const SolveArgs a) {
   g.ring = 0;
   g.s_lo = __ldg(a.blk + blockIdx.x);
   g.s_hi = __ldg(a.blk + blockIdx.x + 1);
+  g.prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 8; ++k) s_prof[k] = 0;
+    s_t_last = global_ns();
+  }
   Ctx<TM, TV> c(a);
   const int lane = threadIdx.x & 31;
   if (a.mode == 0) {
     fgmres(g, c);
   } else if (a.mode == 1) {
     InnerCount cnt;
-    if (apply_pch(g, c, a.b, a.y, cnt)) write_stats<TM, TV>(g, a, 0, 0, cnt, 0.0, 0.0, 0);
+    if (apply_pch(g, c, a.b, a.y, cnt)) write_stats(g, a, 0, 0, cnt, 0.0, 0.0, 0);
   } else {
     InnerCount cnt;
     int its = 0;
-    const TM* AV = a.which == 0 ? c.iM : a.which == 1 ? c.iMdK : c.iMsK;
-    const TV* DI = a.which == 0 ? c.dM : a.which == 1 ? c.dMdK : c.dMsK;
+    const TM* AV = a.which == 0 ? c.iM() : a.which == 1 ? c.iMdK() : c.iMsK();
+    const TV* DI = a.which == 0 ? c.dM() : a.which == 1 ? c.dMdK() : c.dMsK();
     const double* b = a.b;
-    if (!pcg(g, c, AV, DI, c.y0, [&](int, int, int row) { return b[row]; }, a.inner_rtol, a.max_inner, cnt, its))
+    if (!pcg(g, c, AV, DI, c.vec(kVy0), [&](int, int, int row) { return b[row]; }, a.inner_rtol, a.max_inner, cnt, its))
       return;
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
-      a.y[row] = (double)c.y0[row];
+      a.y[row] = (double)c.vec(kVy0)[row];
     }
-    write_stats<TM, TV>(g, a, 0, 0, cnt, 0.0, 0.0, its);
+    write_stats(g, a, 0, 0, cnt, 0.0, 0.0, its);
   }
 }
 

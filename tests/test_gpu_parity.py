@@ -112,8 +112,9 @@ def test_stage_rhs_matches_oracle(case):
             assert_close_scaled(got, want, np.concatenate([s0, s1, s2]))
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["pcg", "pipelined"])
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
-def test_pcg_matches_oracle(case):
+def test_pcg_matches_oracle(case, variant):
     dim, side, L, r, pm, amp = case
     prob = problem(dim, side, L, r)
     x = state_for(prob, dim, side, pm, amp)
@@ -121,7 +122,7 @@ def test_pcg_matches_oracle(case):
     delta = math.sqrt(ROS3PW.gamma * tau)
     mats = [prob.M, (prob.M + delta * prob.K).tocsr(), (prob.M + math.sqrt(delta) * prob.K).tocsr()]
     b = synth.random_vector(prob.n, 8)
-    with pfc.PFCSolver(dim, side, L, r=r) as s:
+    with pfc.PFCSolver(dim, side, L, r=r, pcg_variant=variant) as s:
         s.assemble(cuda(x), tau)
         for which, A in enumerate(mats):
             for rtol in (1e-3, 1e-10):
@@ -131,7 +132,9 @@ def test_pcg_matches_oracle(case):
                 assert np.linalg.norm(b - A @ got) <= rtol * np.linalg.norm(b) * (1 + 1e-6)
                 assert abs(its - ref.iterations) <= 1
                 if its == ref.iterations:
-                    assert np.linalg.norm(got - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+                    # same Krylov iterate; the pipelined recurrences round differently
+                    tol = 1e-9 if variant == 0 else 1e-6 * max(1.0, rtol / 1e-3)
+                    assert np.linalg.norm(got - ref.x) <= tol * np.linalg.norm(ref.x)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
@@ -184,13 +187,14 @@ def oracle_stage(case, tau, stage_seed=1):
     return _ref_solutions[key]
 
 
+@pytest.mark.parametrize("variant", [0, 1], ids=["pcg", "pipelined"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_stage_solve_parity(case, precision):
+def test_stage_solve_parity(case, precision, variant):
     dim, side, L, r, pm, amp = case
     tau = 0.1
     x, b, yref = oracle_stage(case, tau)
-    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11) as s:
+    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11, pcg_variant=variant) as s:
         s.assemble(cuda(x), tau)
         y, st = s.stage_solve(cuda(b))
         y = host(y)
