@@ -31,6 +31,8 @@ def _nvcc() -> str:
 def _flags(verbose: bool) -> list[str]:
     f = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-I", CSRC,
          "-I", os.path.join(ROOT, "include"), "-Xcompiler", "-fPIC,-fopenmp,-O3"] + ARCH
+    # extra preprocessor definitions, e.g. PFC_NVCC_DEFINES="PFC_SOLVER_THREADS=1024 PFC_SPMV_WIDE=1"
+    f += ["-D" + d for d in os.environ.get("PFC_NVCC_DEFINES", "").split() if d]
     if verbose:
         f += ["-Xptxas", "-v"]
     return f

@@ -45,10 +45,26 @@
 namespace pfc {
 namespace {
 
-constexpr int kThreads = 512;
+// Launch shape (compile-time): threads per block, minimum resident blocks per SM
+// (which caps registers per thread), and the SpMV row form (0: rolled loop
+// unrolled by 4; 1: CH loads of a row issued before its gathers).
+#ifndef PFC_SOLVER_THREADS
+#define PFC_SOLVER_THREADS 512
+#endif
+#ifndef PFC_SOLVER_MINBLOCKS
+#define PFC_SOLVER_MINBLOCKS 2
+#endif
+#ifndef PFC_SPMV_WIDE
+#define PFC_SPMV_WIDE 0
+#endif
+#ifndef PFC_GROUP
+#define PFC_GROUP 4
+#endif
+
+constexpr int kThreads = PFC_SOLVER_THREADS;
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 4;
-constexpr int kGroup = 4;   // slices a warp works on at once
+constexpr int kGroup = PFC_GROUP;   // slices a warp stages at once in vector phases
 
 // phase classes for the optional profile
 enum : int { kPhSpmv = 0, kPhVec = 1, kPhOuter = 2, kPhInit = 3 };
@@ -179,9 +195,13 @@ __device__ __forceinline__ void flag(Grid& g, int bit) {
 // values of the row before any of the CH gathers, so a row of up to CH
 // nonzeros costs two dependent memory round trips.
 template <class Acc, class TM, class TX>
-__device__ __forceinline__ Acc sell_row_wide(const int* __restrict__ sp, const int* __restrict__ cols,
+__device__ __forceinline__ Acc sell_row_wide_impl(const int* __restrict__ sp, const int* __restrict__ cols,
                                              const TM* __restrict__ vals, const TX* x, int s, int lane) {
+#ifdef PFC_WIDE_CH
+  constexpr int CH = PFC_WIDE_CH;
+#else
   constexpr int CH = sizeof(Acc) == 8 ? 10 : 20;
+#endif
   const int b = __ldg(sp + s);
   const int w = (__ldg(sp + s + 1) - b) >> 5;
   const int beg = b + lane;
@@ -206,6 +226,16 @@ __device__ __forceinline__ Acc sell_row_wide(const int* __restrict__ sp, const i
     for (int jj = 0; jj < CH; ++jj) acc = fma(vv[jj], xv[jj], acc);
   }
   return acc;
+}
+
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ Acc sell_row_wide(const int* __restrict__ sp, const int* __restrict__ cols,
+                                             const TM* __restrict__ vals, const TX* x, int s, int lane) {
+#if PFC_SPMV_WIDE
+  return sell_row_wide_impl<Acc>(sp, cols, vals, x, s, lane);
+#else
+  return sell_row<Acc>(sp, cols, vals, x, s, lane);
+#endif
 }
 
 struct InnerCount {
@@ -233,14 +263,31 @@ struct Ctx {
 enum : int { kVr = 0, kVp = 1, kVq = 2, kVu = 3, kVw = 4, kVm0 = 5, kVm1 = 6, kVz = 7, kVs = 8,
              kVy0 = 9, kVy1 = 10, kVwv = 11, kVx1 = 12, kVx2 = 13 };
 
+// Right-hand side of an inner solve, per owned row:
+//   rhs(row) = alpha vin[row] + beta (mat x vx)[row]   (either term may be absent)
+// where vx was completed before the call (a SpMV over other blocks' rows).
+template <class TM, class TV>
+struct RhsSpec {
+  const double* vin;
+  double alpha;
+  const TM* mat;
+  const TV* vx;
+  double beta;
+  __device__ __forceinline__ double operator()(const SolveArgs& a, int s, int lane, int row) const {
+    using Acc = typename AccOf<TV>::type;
+    double v = vin ? alpha * vin[row] : 0.0;
+    if (mat) v += beta * (double)sell_row_wide<Acc>(a.slice_ptr, a.cols, mat, vx, s, lane);
+    return v;
+  }
+};
+
 // Textbook Jacobi-PCG for A x = rhs, x0 = 0, stop at ||r||_2 <= rtol ||rhs||_2.
-// rhs(s, lane, row) is evaluated once per owned row in the first phase (it may
-// run a SpMV over vectors completed before the call).
-template <class TM, class TV, class RhsF>
-__device__ bool pcg_standard(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs, double rtol,
-                             int maxit, InnerCount& cnt, int& its) {
+// The right-hand side is evaluated once per owned row in the first phase.
+template <class TM, class TV>
+__device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM* AV, const TV* DI, TV* x,
+                                          RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
+  Ctx<TM, TV> c(a);
   using Acc = typename Ctx<TM, TV>::Acc;
-  const SolveArgs& a = c.a;
   TV* r = c.vec(kVr);
   TV* p = c.vec(kVp);
   TV* q = c.vec(kVq);
@@ -251,7 +298,7 @@ __device__ bool pcg_standard(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
         const int s = s0 + uu, row = s * 32 + lane;
-        const TV rv = (TV)rhs(s, lane, row);
+        const TV rv = (TV)rhs(a, s, lane, row);
         const TV zz = (TV)((Acc)DI[row] * (Acc)rv);
         x[row] = TV(0);
         r[row] = rv;
@@ -365,11 +412,11 @@ __device__ bool pcg_standard(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI
 //   z = n + b z, q = m + b q, s = w + b s, p = u + b p,
 //   x += a p, r -= a s, u -= a q, w -= a z, m' = D w
 // and the partial sums of (r, u), (w, u), (r, r); one barrier follows.
-template <class TM, class TV, class RhsF>
-__device__ bool pcg_pipelined(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs, double rtol,
-                              int maxit, InnerCount& cnt, int& its) {
+template <class TM, class TV>
+__device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM* AV, const TV* DI, TV* x,
+                                           RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
+  Ctx<TM, TV> c(a);
   using Acc = typename Ctx<TM, TV>::Acc;
-  const SolveArgs& a = c.a;
   TV* r = c.vec(kVr);
   TV* u = c.vec(kVu);
   TV* w = c.vec(kVw);
@@ -387,7 +434,7 @@ __device__ bool pcg_pipelined(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* D
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
         const int s = s0 + uu, row = s * 32 + lane;
-        const TV rv = (TV)rhs(s, lane, row);
+        const TV rv = (TV)rhs(a, s, lane, row);
         x[row] = TV(0);
         r[row] = rv;
         u[row] = (TV)((Acc)DI[row] * (Acc)rv);
@@ -492,17 +539,11 @@ __device__ bool pcg_pipelined(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* D
   return true;
 }
 
-template <class TM, class TV, class RhsF>
-__device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x, RhsF rhs,
-                                    double rtol, int maxit, InnerCount& cnt, int& its) {
-  if (c.a.pcg_variant == 1) return pcg_pipelined(g, c, AV, DI, x, rhs, rtol, maxit, cnt, its);
-  return pcg_standard(g, c, AV, DI, x, rhs, rtol, maxit, cnt, its);
-}
-
-// One SELL row of a matrix with TM values times a TV vector, as Acc.
-template <class Acc, class TM, class TX>
-__device__ __forceinline__ Acc one_row(const SolveArgs& a, const TM* vals, const TX* x, int s, int lane) {
-  return sell_row_wide<Acc>(a.slice_ptr, a.cols, vals, x, s, lane);
+template <class TM, class TV>
+__device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x,
+                                    RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
+  if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, DI, x, rhs, rtol, maxit, cnt, its);
+  return pcg_standard<TM, TV>(g, c.a, AV, DI, x, rhs, rtol, maxit, cnt, its);
 }
 
 // z = P_CH^{-1} v for 3-field float64 vectors (n_pad per field).  Ends with a
@@ -519,22 +560,17 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
   const double rt = a.inner_rtol;
   const int mi = a.max_inner;
   int its;
+  using R = RhsSpec<TM, TV>;
   // (1) M y0 = v0
-  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVy0), [&](int, int, int row) { return v0[row]; }, rt, mi, cnt, its)) return false;
+  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVy0), R{v0, 1.0, nullptr, nullptr, 0.0}, rt, mi, cnt, its)) return false;
   // (2) (M + delta K) y1 = gamma v1 - tau_e K y0
-  if (!pcg(g, c, c.iMdK(), c.dMdK(), c.vec(kVy1),
-           [&](int s, int ln, int row) {
-             return a.gamma * v1[row] - a.tau_e * (double)one_row<Acc>(a, c.iK(), c.vec(kVy0), s, ln);
-           },
-           rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMdK(), c.dMdK(), c.vec(kVy1), R{v1, a.gamma, c.iK(), c.vec(kVy0), -a.tau_e}, rt, mi, cnt, its))
     return false;
   // (3.1) (M + sqrt(delta) K) w = M y1
-  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVwv), [&](int s, int ln, int) { return (double)one_row<Acc>(a, c.iM(), c.vec(kVy1), s, ln); },
-           rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVwv), R{nullptr, 0.0, c.iM(), c.vec(kVy1), 1.0}, rt, mi, cnt, its))
     return false;
   // (3.2) (M + sqrt(delta) K) x1 = M w
-  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVx1), [&](int s, int ln, int) { return (double)one_row<Acc>(a, c.iM(), c.vec(kVwv), s, ln); },
-           rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVx1), R{nullptr, 0.0, c.iM(), c.vec(kVwv), 1.0}, rt, mi, cnt, its))
     return false;
   // (4) x0 = y0 + (y1 - x1) / delta, and z = (x0, x1, .)
   FOR_MY_GROUPS(g, s0, nsl) {
@@ -549,10 +585,7 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
     }
   }
   // (5) M x2 = v2 - K x1
-  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVx2),
-           [&](int s, int ln, int row) { return v2[row] - (double)one_row<Acc>(a, c.iK(), c.vec(kVx1), s, ln); }, rt, mi, cnt,
-           its))
-    return false;
+  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVx2), R{v2, 1.0, c.iK(), c.vec(kVx1), -1.0}, rt, mi, cnt, its)) return false;
   FOR_MY_GROUPS(g, s0, nsl) {
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
@@ -769,7 +802,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
 }
 
 template <class TM, class TV>
-__global__ void __launch_bounds__(kThreads, 1) solve_kernel(const __grid_constant__ SolveArgs a) {
+__global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(const __grid_constant__ SolveArgs a) {
   Grid g;
   g.arrive = a.arrive;
   g.err = a.err;
@@ -799,7 +832,8 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const __grid_constan
     const TM* AV = a.which == 0 ? c.iM() : a.which == 1 ? c.iMdK() : c.iMsK();
     const TV* DI = a.which == 0 ? c.dM() : a.which == 1 ? c.dMdK() : c.dMsK();
     const double* b = a.b;
-    if (!pcg(g, c, AV, DI, c.vec(kVy0), [&](int, int, int row) { return b[row]; }, a.inner_rtol, a.max_inner, cnt, its))
+    if (!pcg(g, c, AV, DI, c.vec(kVy0), RhsSpec<TM, TV>{b, 1.0, nullptr, nullptr, 0.0}, a.inner_rtol, a.max_inner,
+             cnt, its))
       return;
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
