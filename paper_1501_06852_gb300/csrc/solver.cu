@@ -55,7 +55,7 @@ namespace {
 #define PFC_SOLVER_MINBLOCKS 2
 #endif
 #ifndef PFC_SPMV_WIDE
-#define PFC_SPMV_WIDE 0
+#define PFC_SPMV_WIDE 1
 #endif
 #ifndef PFC_GROUP
 #define PFC_GROUP 4
@@ -200,7 +200,7 @@ __device__ __forceinline__ Acc sell_row_wide_impl(const int* __restrict__ sp, co
 #ifdef PFC_WIDE_CH
   constexpr int CH = PFC_WIDE_CH;
 #else
-  constexpr int CH = sizeof(Acc) == 8 ? 10 : 20;
+  constexpr int CH = 10;
 #endif
   const int b = __ldg(sp + s);
   const int w = (__ldg(sp + s + 1) - b) >> 5;
