@@ -71,27 +71,31 @@ def tau_cap(w: synth.Workload) -> float:
 
 
 # ----------------------------------------------------------------------------- bytes
-def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30) -> float:
+def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, variant: int = 1) -> float:
     """Algorithmic HBM bytes of one persistent stage-solve launch, from its logged counts.
 
     Each array counted once per pass that needs it; gathered vectors once; int32
-    column indices; SELL padding not counted.  N = nnz of one block, n = dofs/field.
-      PCG iteration:        N (sM + 4) + 13 n sv      (SpMV; x, r, p, q, D passes)
-      P_CH application:     4 N (sM + 4) + 28 n sv + 48 n  (4 RHS SpMVs, 5 PCG set-ups, step (4), z writes)
-      outer iteration j:    28 N + 192 n + 96 j n      (A^R SpMV with 3 value streams, MGS, scaling)
-      restart cycle:        28 N + 96 n + 24 n (k + 2) (true residual, basis scaling, y update)
+    column indices; SELL padding not counted.  N = nnz of one block, n = dofs/field,
+    sM / sv = bytes of an inner matrix value / inner vector entry, S = N (sM + 4).
+      PCG iteration:       S + 13 n sv (textbook: SpMV; x, r, p, q, D passes)
+                           S + 19 n sv (pipelined: SpMV; 9 recurrences read and written, D)
+      PCG set-up (x5 per P_CH): 4 n sv (textbook) or S + 14 n sv (pipelined, incl. w = A u)
+      P_CH application:    4 (S + n sv) right-hand-side SpMVs + 24 n (v reads) + 4 n sv + 24 n (steps 4, 5)
+      outer iteration j:   28 N + 192 n + 96 j n  (A^R SpMV with 3 value streams, MGS, scaling)
+      restart cycle:       28 N + 96 n + 24 n (k + 2) (true residual, basis scaling, y update)
     """
     sM, sv = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 4)}[precision]
-    b = st.inner_its * (nnz * (sM + 4) + 13 * n * sv)
-    b += st.outer_its * (4 * nnz * (sM + 4) + 28 * n * sv + 48 * n)
+    S = nnz * (sM + 4)
+    it = S + (19 if variant == 1 else 13) * n * sv
+    setup = (S + 14 * n * sv) if variant == 1 else 4 * n * sv
+    b = st.inner_its * it
+    b += st.outer_its * (4 * (S + n * sv) + 24 * n + 4 * n * sv + 24 * n + 5 * setup)
     left = st.outer_its
-    cycles = 0
     while left > 0:
         k = min(restart, left)
         b += k * (28 * nnz + 192 * n) + 96 * n * k * (k - 1) / 2
         b += 28 * nnz + 96 * n + 24 * n * (k + 2)
         left -= k
-        cycles += 1
     b += 28 * nnz + 48 * n          # final true-residual check
     return float(b)
 

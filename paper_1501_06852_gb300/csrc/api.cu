@@ -366,16 +366,32 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (c->opt.blocks_per_sm > 0) bps = std::min(bps, c->opt.blocks_per_sm);
   if (bps < 1) return bail(fail(c, PFC_ERR_CUDA, "solver kernel does not fit on an SM"));
   c->G = std::max(1, std::min(sms * bps, c->nslices));
-  std::vector<int> blk(c->G + 1, 0);
+  // Slice ranges: blocks and, inside each block, warps get contiguous runs of
+  // slices of equal cost, cost(slice) = 32 * (width + 10) ~ bytes of one SpMV
+  // row plus the vector traffic of the inner iteration.
+  const int W = pfc::solve_threads() / 32;
+  std::vector<int> blk((size_t)c->G * W + 1, 0);
   {
-    const long long total = S.slice_ptr[S.nslices];
-    int s = 0;
-    for (int b = 1; b < c->G; ++b) {
-      const long long target = total * b / c->G;
-      while (s < S.nslices && S.slice_ptr[s] < target) ++s;
-      blk[b] = std::max(s, blk[b - 1]);
+    std::vector<long long> pre(S.nslices + 1, 0);
+    for (int s = 0; s < S.nslices; ++s) pre[s + 1] = pre[s] + (S.slice_ptr[s + 1] - S.slice_ptr[s]) + 320;
+    auto split = [&](int lo, int hi, int parts, int* out) {  // out[0..parts]
+      out[0] = lo;
+      int s = lo;
+      for (int k = 1; k < parts; ++k) {
+        const long long target = pre[lo] + (pre[hi] - pre[lo]) * k / parts;
+        while (s < hi && pre[s] < target) ++s;
+        out[k] = std::max(s, out[k - 1]);
+      }
+      out[parts] = hi;
+    };
+    std::vector<int> bb(c->G + 1);
+    split(0, S.nslices, c->G, bb.data());
+    for (int b = 0; b < c->G; ++b) {
+      std::vector<int> wb(W + 1);
+      split(bb[b], bb[b + 1], W, wb.data());
+      for (int w = 0; w < W; ++w) blk[(size_t)b * W + w] = wb[w];
     }
-    blk[c->G] = S.nslices;
+    blk[(size_t)c->G * W] = S.nslices;
   }
 
   // ---- device layout (one allocation) ----

@@ -35,7 +35,7 @@ struct SolveArgs {
   int n_pad;
   const int* slice_ptr;
   const int* cols;
-  const int* blk;          // gridDim.x + 1 slice boundaries (nnz balanced)
+  const int* blk;          // gridDim.x * warps + 1 slice boundaries, one range per warp
   const double* Mv;        // float64 M, K, A01 values (outer operator A^R)
   const double* Kv;
   const double* Av;

@@ -78,20 +78,21 @@ struct Grid {
   int expect;      // blocks that arrive at each barrier (G, or more in the timeout self-test)
   unsigned epoch;  // thread 0 only
   int ring;
-  int s_lo, s_hi;
+  int w_lo, w_hi;  // this warp's contiguous slice range (cost balanced on the host)
   bool prof;       // block 0, thread 0 (accumulators live in shared memory)
 };
 
 __shared__ unsigned long long s_t_last;
 __shared__ long long s_prof[8];
 
-// Warp-group iteration over this block's slices: groups of kGroup consecutive
-// slices, interleaved across warps.  Inside, rows (s0 + u) * 32 + lane, u < nsl.
-#define FOR_MY_GROUPS(g, s0, nsl)                                                                  \
-  for (int s0 = (g).s_lo + (int)(threadIdx.x >> 5) * kGroup; s0 < (g).s_hi; s0 += kWarps * kGroup) \
-    if (const int nsl = min(kGroup, (g).s_hi - s0); true)
+// Every warp owns a contiguous range of slices (the host splits each block's
+// range so that the warps carry equal SpMV-plus-vector cost).  Groups of kGroup
+// consecutive slices are staged together in vector phases: rows (s0 + u) * 32 + lane.
+#define FOR_MY_GROUPS(g, s0, nsl)                                     \
+  for (int s0 = (g).w_lo; s0 < (g).w_hi; s0 += kGroup) \
+    if (const int nsl = min(kGroup, (g).w_hi - s0); true)
 
-#define FOR_MY_SLICES(g, s) for (int s = (g).s_lo + (int)(threadIdx.x >> 5); s < (g).s_hi; s += kWarps)
+#define FOR_MY_SLICES(g, s) for (int s = (g).w_lo; s < (g).w_hi; ++s)
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -812,8 +813,11 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
   g.limit_ns = a.spin_limit_ns;
   g.epoch = 0;
   g.ring = 0;
-  g.s_lo = __ldg(a.blk + blockIdx.x);
-  g.s_hi = __ldg(a.blk + blockIdx.x + 1);
+  {
+    const int wi = blockIdx.x * kWarps + (int)(threadIdx.x >> 5);
+    g.w_lo = __ldg(a.blk + wi);
+    g.w_hi = __ldg(a.blk + wi + 1);
+  }
   g.prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) s_prof[k] = 0;

@@ -17,10 +17,13 @@ class _St:
 
 def test_stage_solve_bytes_counts_pcg_iterations():
     n, nnz = 1_050_625, 12_066_817
-    a = bench.stage_solve_bytes(_St(27, 2500), n, nnz, "fp32")
-    b = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32")
+    a = bench.stage_solve_bytes(_St(27, 2500), n, nnz, "fp32", variant=0)
+    b = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32", variant=0)
     # one more PCG iteration costs one SpMV (8 bytes per nonzero in fp32) plus 13 vector passes
     assert (b - a) / 100 == pytest.approx(8 * nnz + 13 * 4 * n)
+    c = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32", variant=1)
+    d = bench.stage_solve_bytes(_St(27, 2700), n, nnz, "fp32", variant=1)
+    assert (d - c) / 100 == pytest.approx(8 * nnz + 19 * 4 * n)
     f64 = bench.stage_solve_bytes(_St(27, 2500), n, nnz, "fp64")
     assert f64 > a
     assert bench.stage_solve_bytes(_St(0, 0), n, nnz, "fp32") == 28 * nnz + 48 * n
