@@ -201,7 +201,7 @@ def run_steps(s, state, tau, steps, cap, torch):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-    all_stats, accepted = [], 0
+    all_stats, accepted, traj = [], 0, []
     ev0.record(stream)
     marks[0].record(stream)
     for k in range(steps):
@@ -209,10 +209,13 @@ def run_steps(s, state, tau, steps, cap, torch):
         marks[k + 1].record(stream)
         all_stats.extend(st)
         accepted += int(acc)
+        traj.append([round(tau, 4), int(acc), round(err, 4), max(x.outer_its for x in st),
+                     round(sum(x.inner_its for x in st) / max(1, sum(x.outer_its for x in st)), 1)])
         tau = min(tau_next, cap)
     ev1.record(stream)
     torch.cuda.synchronize()
     per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(steps)]
+    run_steps.last_trajectory = traj
     return ev0.elapsed_time(ev1), per_step, all_stats, tau, accepted
 
 
@@ -302,6 +305,8 @@ def native(args, world, rank, local, pg):
         },
         "step_ms": {"p50": pct(per_step, 50), "p99": pct(per_step, 99), "mean": statistics.mean(per_step)},
         "accepted_steps": accepted,
+        "trajectory": {"columns": ["tau", "accepted", "err", "max_outer_its", "inner_its_per_outer"],
+                       "mixed": run_steps.last_trajectory},
         "solver": {
             "outer_its_mean": statistics.mean(st.outer_its for st in stats),
             "inner_its_per_outer": statistics.mean(st.inner_its / max(st.outer_its, 1) for st in stats),
@@ -332,6 +337,7 @@ def native(args, world, rank, local, pg):
         t64max = dist_max(pg, t64 / 1e3, dev)
         v64 = aggregate_value(solves, world, t64max)
         diff = float((mixed_state - st64).norm() / st64.norm())
+        out["trajectory"]["fp64"] = run_steps.last_trajectory
         out["fp64"] = {"value": v64, "ms_per_step": t64max * 1e3 / args.steps,
                        "step_ms": {"p50": pct(per64, 50), "p99": pct(per64, 99)},
                        "outer_its_mean": statistics.mean(x.outer_its for x in stats64),
