@@ -138,7 +138,8 @@ pfc_status pfc_stage_solve(pfc_ctx* ctx, const double* b, double* y,
  * e = sum (mhat_j - m_j) dpsi_j.  If err <= 1 the step is accepted and state
  * (3n, device, in/out) is overwritten with x^{k+1}; otherwise state is left
  * unchanged.  *tau (in/out) becomes tau * min(5, max(0.2, 0.9 err^(-1/3))),
- * capped at tau_max.  stats (may be NULL) receives 3 entries.  One host
+ * capped at tau_max; an accepted step that follows a rejected one (on this
+ * context) does not grow tau (Hairer-Wanner's rule after a rejection).  stats (may be NULL) receives 3 entries.  One host
  * synchronisation per call. */
 pfc_status pfc_step(pfc_ctx* ctx, double* state, double* tau, int* accepted,
                     double* err, pfc_solve_stats* stats);

@@ -33,7 +33,9 @@ Section 3.1): error vector e = xhat^{k+1} - x^{k+1} restricted to psi (the
 differential component, MM = diag(0, 1, 0)); err = RMS of
 e_j / (atol + rtol * max(|psi^k_j|, |psi^{k+1}_j|)) with atol = rtol = 1e-3;
 accept iff err <= 1; tau_new = tau * min(5, max(0.2, 0.9 err^{-1/3})) (embedded
-order 2).  Parity unpinned: this is a convention, not a result of the paper.
+order 2), except that an accepted step right after a rejected one may not grow
+the width (fac <= 1; Hairer & Wanner, Solving ODEs II, Section IV.8).  Parity
+unpinned: this is a convention, not a result of the paper.
 """
 from __future__ import annotations
 
@@ -207,10 +209,12 @@ class StepResult:
 
 
 def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = StepControl(),
-             tol: float = 1e-13, inner: str = "pcg", coef: Ros3Pw = ROS3PW) -> StepResult:
+             tol: float = 1e-13, inner: str = "pcg", coef: Ros3Pw = ROS3PW,
+             prev_rejected: bool = False) -> StepResult:
     """One attempted Ros3Pw step (Eq. 3.6, 3.7, 3.12) with the error estimate.
 
-    The matrix N(psi) is frozen at psi^k for all three stages (W-method)."""
+    The matrix N(psi) is frozen at psi^k for all three stages (W-method).
+    ``prev_rejected``: the previous attempt was rejected (no growth after it)."""
     n = prob.n
     psi_k = prob.split(x_k)[1]
     A = prob.stage_matrix(psi_k, tau, coef)
@@ -226,4 +230,7 @@ def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = S
     e = sum((coef.mhat[j] - coef.m[j]) * ys[j] for j in range(3))
     err = step_error(psi_k, x_new[n:2 * n], e[n:2 * n], ctl)
     accepted = err <= 1.0
-    return StepResult(x_new if accepted else x_k.copy(), accepted, err, next_tau(tau, err, ctl), ys, rhs, stats)
+    tau_next = next_tau(tau, err, ctl)
+    if accepted and prev_rejected:
+        tau_next = min(tau_next, tau)
+    return StepResult(x_new if accepted else x_k.copy(), accepted, err, tau_next, ys, rhs, stats)

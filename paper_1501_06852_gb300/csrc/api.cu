@@ -82,6 +82,7 @@ struct pfc_ctx {
   double* h_err = nullptr;
   int* h_errw = nullptr;
   bool assembled = false;
+  bool last_rejected = false;   // the previous pfc_step attempt was rejected
   double tau = 0.0, delta = 0.0;
   // accounting: kernels launched, persistent-solver launches and their event time
   long long launches = 0, solver_launches = 0;
@@ -655,6 +656,8 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   if (accepted) *accepted = acc ? 1 : 0;
   if (acc) LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
   double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
+  if (acc && c->last_rejected) fac = std::min(fac, 1.0);  // no growth right after a rejection
+  c->last_rejected = !acc;
   *tau = std::min(*tau * fac, c->opt.tau_max);
   if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
   return PFC_OK;

@@ -293,7 +293,9 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   TV* p = c.vec(kVp);
   TV* q = c.vec(kVq);
   const int lane = threadIdx.x & 31;
-  double pb = 0.0, pz = 0.0;
+  // per-thread partial sums stay in the inner type (fp64 work is scarce on this GPU);
+  // the warp, block and grid sums are float64
+  Acc pb = Acc(0), pz = Acc(0);
   FOR_MY_GROUPS(g, s0, nsl) {
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
@@ -304,13 +306,13 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         x[row] = TV(0);
         r[row] = rv;
         p[row] = zz;
-        pb += (double)rv * (double)rv;
-        pz += (double)rv * (double)zz;
+        pb = fma((Acc)rv, (Acc)rv, pb);
+        pz = fma((Acc)rv, (Acc)zz, pz);
       }
     }
   }
   double4 red;
-  if (!grid_sum(g, pb, pz, 0.0, red, kPhInit)) return false;
+  if (!grid_sum(g, (double)pb, (double)pz, 0.0, red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -322,14 +324,14 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   if (bb == 0.0) return true;
   const double thr = rtol * rtol * bb;
   for (int it = 1; it <= maxit; ++it) {
-    double ppq = 0.0;
+    Acc ppq = Acc(0);
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
       const TV qv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, p, s, lane);
       q[row] = qv;
-      ppq += (double)p[row] * (double)qv;
+      ppq = fma((Acc)p[row], (Acc)qv, ppq);
     }
-    if (!grid_sum(g, ppq, 0.0, 0.0, red, kPhSpmv)) return false;
+    if (!grid_sum(g, (double)ppq, 0.0, 0.0, red, kPhSpmv)) return false;
     const double pq = red.x;
     if (!isfinite(pq)) {
       flag(g, kErrNonfinite);
@@ -342,7 +344,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
       return true;
     }
     const Acc alpha = (Acc)(rz / pq);
-    double prr = 0.0, prz = 0.0;
+    Acc prr = Acc(0), prz = Acc(0);
     FOR_MY_GROUPS(g, s0, nsl) {
       TV xv[kGroup], pv[kGroup], qv[kGroup], rv[kGroup], dv[kGroup];
 #pragma unroll
@@ -365,12 +367,12 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
           x[row] = (TV)xn;
           r[row] = (TV)rn;
           const Acc zz = (Acc)dv[uu] * rn;
-          prr += (double)rn * (double)rn;
-          prz += (double)rn * (double)zz;
+          prr = fma(rn, rn, prr);
+          prz = fma(rn, zz, prz);
         }
       }
     }
-    if (!grid_sum(g, prr, prz, 0.0, red, kPhVec)) return false;
+    if (!grid_sum(g, (double)prr, (double)prz, 0.0, red, kPhVec)) return false;
     its = it;
     if (!isfinite(red.x)) {
       flag(g, kErrNonfinite);
@@ -428,8 +430,9 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   TV* mcur = c.vec(kVm0);
   TV* mnext = c.vec(kVm1);
   const int lane = threadIdx.x & 31;
-  // r = b, u = D r, x = 0; recurrences start at zero
-  double pb = 0.0;
+  // r = b, u = D r, x = 0; recurrences start at zero.  Per-thread partial sums
+  // stay in the inner type; the warp, block and grid sums are float64.
+  Acc pb = Acc(0);
   FOR_MY_GROUPS(g, s0, nsl) {
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
@@ -443,12 +446,12 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
         qv[row] = TV(0);
         sv[row] = TV(0);
         pv[row] = TV(0);
-        pb += (double)rv * (double)rv;
+        pb = fma((Acc)rv, (Acc)rv, pb);
       }
     }
   }
   double4 red;
-  if (!grid_sum(g, pb, 0.0, 0.0, red, kPhInit)) return false;
+  if (!grid_sum(g, (double)pb, 0.0, 0.0, red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -459,17 +462,17 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   if (bb == 0.0) return true;
   const double thr = rtol * rtol * bb;
   // w = A u, m = D w, partial (r, u), (w, u)
-  double pg = 0.0, pd = 0.0;
+  Acc pg = Acc(0), pd = Acc(0);
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
     const TV wvv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, u, s, lane);
     const TV uvv = u[row];
     w[row] = wvv;
     mcur[row] = (TV)((Acc)DI[row] * (Acc)wvv);
-    pg += (double)r[row] * (double)uvv;
-    pd += (double)wvv * (double)uvv;
+    pg = fma((Acc)r[row], (Acc)uvv, pg);
+    pd = fma((Acc)wvv, (Acc)uvv, pd);
   }
-  if (!grid_sum(g, pg, pd, 0.0, red, kPhSpmv)) return false;
+  if (!grid_sum(g, (double)pg, (double)pd, 0.0, red, kPhSpmv)) return false;
   double gamma = red.x, delta = red.y, gamma_old = 1.0, alpha_old = 1.0;
   for (int it = 0; it < maxit; ++it) {
     if (!isfinite(gamma) || !isfinite(delta)) {
@@ -491,7 +494,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       return true;
     }
     const Acc al = (Acc)alpha, be = (Acc)beta;
-    double prg = 0.0, pwd = 0.0, prr = 0.0;
+    Acc prg = Acc(0), pwd = Acc(0), prr = Acc(0);
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
       const Acc na = sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, mcur, s, lane);
@@ -513,11 +516,11 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       u[row] = (TV)u1;
       w[row] = (TV)w1;
       mnext[row] = (TV)((Acc)DI[row] * w1);
-      prg += (double)r1 * (double)u1;
-      pwd += (double)w1 * (double)u1;
-      prr += (double)r1 * (double)r1;
+      prg = fma(r1, u1, prg);
+      pwd = fma(w1, u1, pwd);
+      prr = fma(r1, r1, prr);
     }
-    if (!grid_sum(g, prg, pwd, prr, red, kPhSpmv)) return false;
+    if (!grid_sum(g, (double)prg, (double)pwd, (double)prr, red, kPhSpmv)) return false;
     its = it + 1;
     if (!isfinite(red.z)) {
       flag(g, kErrNonfinite);

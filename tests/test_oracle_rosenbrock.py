@@ -156,6 +156,11 @@ def test_step_control_rejects_and_shrinks(small_pfc):
     res = pfc_step(prob, x, 0.5, StepControl(atol=1e-9, rtol=1e-9))
     assert not res.accepted and res.err > 1.0 and res.tau_next < 0.5
     assert np.array_equal(res.x_new, x)
+    # an accepted step right after a rejection does not grow the width
+    ok = pfc_step(prob, x, res.tau_next, prev_rejected=True)
+    assert ok.accepted and ok.tau_next <= res.tau_next
+    free = pfc_step(prob, x, res.tau_next)
+    assert free.tau_next > res.tau_next
     ctl = StepControl()
     assert next_tau(1.0, 0.0, ctl) == 5.0
     assert next_tau(1.0, 1e6, ctl) == 0.2
