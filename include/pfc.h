@@ -69,7 +69,9 @@ typedef struct {
   int blocks_per_sm;  /* persistent-kernel residency; 0 = as many as fit */
   int pcg_variant;    /* inner CG form: 0 textbook Jacobi-PCG (3 grid barriers per
                          iteration), 1 pipelined Jacobi-PCG of Ghysels & Vanroose
-                         (same iterates in exact arithmetic, 1 barrier per iteration) */
+                         (same iterates in exact arithmetic, 1 barrier per iteration),
+                         2 automatic: pipelined with float64 inner solves, textbook with
+                         float32/float16 ones (the pipelined recurrences drift there) */
 } pfc_options;
 
 typedef struct {
@@ -87,7 +89,7 @@ typedef struct {
 
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
- * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 1. */
+ * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

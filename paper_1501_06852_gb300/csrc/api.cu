@@ -161,7 +161,9 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.stats = c->stats;
   a.spin_limit_ns = 2000000000ULL;
   a.barrier_extra = 0;
-  a.pcg_variant = c->opt.pcg_variant;
+  // 2 = automatic: the pipelined form in float64; the textbook form in float32/float16,
+  // where the pipelined recurrences drift and cost outer iterations
+  a.pcg_variant = c->opt.pcg_variant == 2 ? (prec == 0 ? 1 : 0) : c->opt.pcg_variant;
   a.prof = c->timing ? 1 : 0;
   return a;
 }
@@ -262,7 +264,7 @@ void pfc_default_options(pfc_options* o) {
   o->step_rtol = 1e-3;
   o->tau_max = 1e9;
   o->blocks_per_sm = 0;
-  o->pcg_variant = 1;
+  o->pcg_variant = 2;
 }
 
 const char* pfc_status_string(int s) {
@@ -323,7 +325,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (c->opt.restart < 1 || c->opt.restart > pfc::kMaxRestart)
     return bail(fail(c, PFC_ERR_INVALID, "restart must be in 1..40"));
   if (c->opt.precision < 0 || c->opt.precision > 2) return bail(fail(c, PFC_ERR_INVALID, "precision must be 0, 1 or 2"));
-  if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 1) return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0 or 1"));
+  if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 2) return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1 or 2"));
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
     return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
   c->stream = (cudaStream_t)cuda_stream;
@@ -366,7 +368,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   int bps = std::min(occ0, occ1);
   if (c->opt.blocks_per_sm > 0) bps = std::min(bps, c->opt.blocks_per_sm);
   if (bps < 1) return bail(fail(c, PFC_ERR_CUDA, "solver kernel does not fit on an SM"));
-  c->G = std::max(1, std::min(sms * bps, c->nslices));
+  c->G = std::max(1, std::min(std::min(sms * bps, c->nslices), pfc::solve_threads()));
   // Slice ranges: blocks and, inside each block, warps get contiguous runs of
   // slices of equal cost, cost(slice) = 32 * (width + 10) ~ bytes of one SpMV
   // row plus the vector traffic of the inner iteration.

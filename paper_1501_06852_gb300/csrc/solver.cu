@@ -79,6 +79,8 @@ struct Grid {
   unsigned epoch;  // thread 0 only
   int ring;
   int w_lo, w_hi;  // this warp's contiguous slice range (cost balanced on the host)
+  int sp_lane;     // slice_ptr[w_lo + lane] (valid when the range has at most 31 slices)
+  bool sp_reg;     // the slice pointers of this warp live in sp_lane
   bool prof;       // block 0, thread 0 (accumulators live in shared memory)
 };
 
@@ -93,6 +95,16 @@ __shared__ long long s_prof[8];
     if (const int nsl = min(kGroup, (g).w_hi - s0); true)
 
 #define FOR_MY_SLICES(g, s) for (int s = (g).w_lo; s < (g).w_hi; ++s)
+
+// First slot and end slot of slice s (one of this warp's slices).  Called by
+// all 32 lanes together.
+__device__ __forceinline__ int2 slice_bounds(const Grid& g, const int* __restrict__ sp, int s) {
+  if (g.sp_reg) {
+    const int k = s - g.w_lo;
+    return make_int2(__shfl_sync(0xffffffffu, g.sp_lane, k), __shfl_sync(0xffffffffu, g.sp_lane, k + 1));
+  }
+  return make_int2(__ldg(sp + s), __ldg(sp + s + 1));
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -146,6 +158,10 @@ __device__ bool grid_sync(Grid& g, int tag) {
 }
 
 // Sum of up to three values over all threads of the grid, identical in every block.
+// Each block publishes its partial (3 doubles in a 32-byte slot); after the
+// barrier every thread of a block loads at most one partial (the grid has at most
+// kThreads blocks), so the read-back is one memory round trip, and the partials
+// are summed in a fixed order.
 __device__ bool grid_sum(Grid& g, double a, double b, double c, double4& out, int tag) {
   __shared__ double4 s_w[kWarps];
   __shared__ double4 s_res;
@@ -169,19 +185,25 @@ __device__ bool grid_sum(Grid& g, double a, double b, double c, double4& out, in
     }
   }
   if (!grid_sync(g, tag)) return false;
+  double px = 0.0, py = 0.0, pz = 0.0;
+  if ((int)threadIdx.x < g.G) {
+    const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + threadIdx.x);
+    const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
+    px = t0.x;
+    py = t0.y;
+    pz = t1.x;
+  }
+  px = warp_sum(px);
+  py = warp_sum(py);
+  pz = warp_sum(pz);
+  if (l == 0) s_w[w] = make_double4(px, py, pz, 0.0);
+  __syncthreads();
   if (w == 0) {
-    double4 acc = make_double4(0.0, 0.0, 0.0, 0.0);
-    for (int i = l; i < g.G; i += 32) {
-      const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + i);
-      const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
-      acc.x += t0.x;
-      acc.y += t0.y;
-      acc.z += t1.x;
-    }
-    acc.x = warp_sum(acc.x);
-    acc.y = warp_sum(acc.y);
-    acc.z = warp_sum(acc.z);
-    if (l == 0) s_res = acc;
+    double4 t = l < kWarps ? s_w[l] : make_double4(0.0, 0.0, 0.0, 0.0);
+    t.x = warp_sum(t.x);
+    t.y = warp_sum(t.y);
+    t.z = warp_sum(t.z);
+    if (l == 0) s_res = t;
   }
   __syncthreads();
   out = s_res;
@@ -196,16 +218,15 @@ __device__ __forceinline__ void flag(Grid& g, int bit) {
 // values of the row before any of the CH gathers, so a row of up to CH
 // nonzeros costs two dependent memory round trips.
 template <class Acc, class TM, class TX>
-__device__ __forceinline__ Acc sell_row_wide_impl(const int* __restrict__ sp, const int* __restrict__ cols,
-                                             const TM* __restrict__ vals, const TX* x, int s, int lane) {
+__device__ __forceinline__ Acc sell_row_wide_impl(int2 se, const int* __restrict__ cols, const TM* __restrict__ vals,
+                                                  const TX* x, int lane) {
 #ifdef PFC_WIDE_CH
   constexpr int CH = PFC_WIDE_CH;
 #else
   constexpr int CH = 10;
 #endif
-  const int b = __ldg(sp + s);
-  const int w = (__ldg(sp + s + 1) - b) >> 5;
-  const int beg = b + lane;
+  const int w = (se.y - se.x) >> 5;
+  const int beg = se.x + lane;
   Acc acc = Acc(0);
   for (int j0 = 0; j0 < w; j0 += CH) {
     int cc[CH];
@@ -230,12 +251,15 @@ __device__ __forceinline__ Acc sell_row_wide_impl(const int* __restrict__ sp, co
 }
 
 template <class Acc, class TM, class TX>
-__device__ __forceinline__ Acc sell_row_wide(const int* __restrict__ sp, const int* __restrict__ cols,
-                                             const TM* __restrict__ vals, const TX* x, int s, int lane) {
+__device__ __forceinline__ Acc sell_row_wide(int2 se, const int* __restrict__ cols, const TM* __restrict__ vals,
+                                             const TX* x, int lane) {
 #if PFC_SPMV_WIDE
-  return sell_row_wide_impl<Acc>(sp, cols, vals, x, s, lane);
+  return sell_row_wide_impl<Acc>(se, cols, vals, x, lane);
 #else
-  return sell_row<Acc>(sp, cols, vals, x, s, lane);
+  Acc acc = Acc(0);
+#pragma unroll 4
+  for (int idx = se.x + lane; idx < se.y; idx += 32) acc = fma(ld_val<Acc>(vals + idx), (Acc)x[__ldg(cols + idx)], acc);
+  return acc;
 #endif
 }
 
@@ -274,10 +298,10 @@ struct RhsSpec {
   const TM* mat;
   const TV* vx;
   double beta;
-  __device__ __forceinline__ double operator()(const SolveArgs& a, int s, int lane, int row) const {
+  __device__ __forceinline__ double operator()(const Grid& g, const SolveArgs& a, int s, int lane, int row) const {
     using Acc = typename AccOf<TV>::type;
     double v = vin ? alpha * vin[row] : 0.0;
-    if (mat) v += beta * (double)sell_row_wide<Acc>(a.slice_ptr, a.cols, mat, vx, s, lane);
+    if (mat) v += beta * (double)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, mat, vx, lane);
     return v;
   }
 };
@@ -301,7 +325,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
         const int s = s0 + uu, row = s * 32 + lane;
-        const TV rv = (TV)rhs(a, s, lane, row);
+        const TV rv = (TV)rhs(g, a, s, lane, row);
         const TV zz = (TV)((Acc)DI[row] * (Acc)rv);
         x[row] = TV(0);
         r[row] = rv;
@@ -327,9 +351,10 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     Acc ppq = Acc(0);
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
-      const TV qv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, p, s, lane);
+      const Acc pr = (Acc)p[row];
+      const TV qv = (TV)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, p, lane);
       q[row] = qv;
-      ppq = fma((Acc)p[row], (Acc)qv, ppq);
+      ppq = fma(pr, (Acc)qv, ppq);
     }
     if (!grid_sum(g, (double)ppq, 0.0, 0.0, red, kPhSpmv)) return false;
     const double pq = red.x;
@@ -438,7 +463,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
         const int s = s0 + uu, row = s * 32 + lane;
-        const TV rv = (TV)rhs(a, s, lane, row);
+        const TV rv = (TV)rhs(g, a, s, lane, row);
         x[row] = TV(0);
         r[row] = rv;
         u[row] = (TV)((Acc)DI[row] * (Acc)rv);
@@ -465,11 +490,12 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   Acc pg = Acc(0), pd = Acc(0);
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
-    const TV wvv = (TV)sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, u, s, lane);
     const TV uvv = u[row];
+    const Acc rr0 = (Acc)r[row], dd0 = (Acc)DI[row];
+    const TV wvv = (TV)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, u, lane);
     w[row] = wvv;
-    mcur[row] = (TV)((Acc)DI[row] * (Acc)wvv);
-    pg = fma((Acc)r[row], (Acc)uvv, pg);
+    mcur[row] = (TV)(dd0 * (Acc)wvv);
+    pg = fma(rr0, (Acc)uvv, pg);
     pd = fma((Acc)wvv, (Acc)uvv, pd);
   }
   if (!grid_sum(g, (double)pg, (double)pd, 0.0, red, kPhSpmv)) return false;
@@ -497,16 +523,18 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     Acc prg = Acc(0), pwd = Acc(0), prr = Acc(0);
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
-      const Acc na = sell_row_wide<Acc>(a.slice_ptr, a.cols, AV, mcur, s, lane);
-      const Acc mv = (Acc)mcur[row];
-      const Acc z1 = na + be * (Acc)zv[row];
-      const Acc q1 = mv + be * (Acc)qv[row];
-      const Acc s1 = (Acc)w[row] + be * (Acc)sv[row];
-      const Acc p1 = (Acc)u[row] + be * (Acc)pv[row];
-      const Acc x1 = (Acc)x[row] + al * p1;
-      const Acc r1 = (Acc)r[row] - al * s1;
-      const Acc u1 = (Acc)u[row] - al * q1;
-      const Acc w1 = (Acc)w[row] - al * z1;
+      const Acc mv = (Acc)mcur[row], zo = (Acc)zv[row], qo = (Acc)qv[row], so = (Acc)sv[row];
+      const Acc po = (Acc)pv[row], xo = (Acc)x[row], ro = (Acc)r[row], uo = (Acc)u[row], wo = (Acc)w[row];
+      const Acc dd = (Acc)DI[row];
+      const Acc na = sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, mcur, lane);
+      const Acc z1 = na + be * zo;
+      const Acc q1 = mv + be * qo;
+      const Acc s1 = wo + be * so;
+      const Acc p1 = uo + be * po;
+      const Acc x1 = xo + al * p1;
+      const Acc r1 = ro - al * s1;
+      const Acc u1 = uo - al * q1;
+      const Acc w1 = wo - al * z1;
       zv[row] = (TV)z1;
       qv[row] = (TV)q1;
       sv[row] = (TV)s1;
@@ -515,7 +543,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       r[row] = (TV)r1;
       u[row] = (TV)u1;
       w[row] = (TV)w1;
-      mnext[row] = (TV)((Acc)DI[row] * w1);
+      mnext[row] = (TV)(dd * w1);
       prg = fma(r1, u1, prg);
       pwd = fma(w1, u1, pwd);
       prr = fma(r1, r1, prr);
@@ -820,6 +848,9 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
     const int wi = blockIdx.x * kWarps + (int)(threadIdx.x >> 5);
     g.w_lo = __ldg(a.blk + wi);
     g.w_hi = __ldg(a.blk + wi + 1);
+    g.sp_reg = (g.w_hi - g.w_lo) <= 31;
+    const int k = g.w_lo + (int)(threadIdx.x & 31);
+    g.sp_lane = (g.sp_reg && k <= g.w_hi) ? __ldg(a.slice_ptr + k) : 0;
   }
   g.prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) {
