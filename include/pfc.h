@@ -72,6 +72,12 @@ typedef struct {
                          (same iterates in exact arithmetic, 1 barrier per iteration),
                          2 automatic: pipelined with float64 inner solves, textbook with
                          float32/float16 ones (the pipelined recurrences drift there) */
+  int inner_operator; /* inner matrices M, K, M + delta K, M + sqrt(delta) K in the
+                         preconditioner: 0 assembled SELL-32 values with int32 column
+                         indices; 1 structured stencils - on this mesh every row whose
+                         elements all exist has the same entries as every other row of its
+                         dof type, so those rows read neither values nor indices (the
+                         other rows keep their assembled values) */
 } pfc_options;
 
 typedef struct {
@@ -89,7 +95,7 @@ typedef struct {
 
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
- * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2. */
+ * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

@@ -58,6 +58,11 @@ struct pfc_ctx {
   // pattern and maps
   int *slice_ptr = nullptr, *cols = nullptr, *diag = nullptr, *perm = nullptr, *elem = nullptr;
   int *cptr = nullptr, *cidx = nullptr, *dptr = nullptr, *didx = nullptr, *blk = nullptr;
+  // structured stencils (inner_operator == 1)
+  unsigned char* rowinfo = nullptr;
+  int *st_start = nullptr, *st_off = nullptr;
+  double *st_wM = nullptr, *st_wK = nullptr;
+  int st_types = 0;
   double *mass_tab = nullptr, *stiff_tab = nullptr;
   // float64 matrices
   double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
@@ -164,6 +169,19 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   // 2 = automatic: the pipelined form in float64; the textbook form in float32/float16,
   // where the pipelined recurrences drift and cost outer iterations
   a.pcg_variant = c->opt.pcg_variant == 2 ? (prec == 0 ? 1 : 0) : c->opt.pcg_variant;
+  a.stencil = c->opt.inner_operator == 1 ? 1 : 0;
+  a.rowinfo = c->rowinfo;
+  a.st_start = c->st_start;
+  a.st_off = c->st_off;
+  a.st_wM = c->st_wM;
+  a.st_wK = c->st_wK;
+  a.st_types = c->st_types;
+  const double cK[4] = {0.0, 1.0, c->delta, std::sqrt(c->delta)};
+  const double cM[4] = {1.0, 0.0, 1.0, 1.0};
+  for (int k = 0; k < 4; ++k) {
+    a.op_cK[k] = cK[k];
+    a.op_cM[k] = cM[k];
+  }
   a.prof = c->timing ? 1 : 0;
   return a;
 }
@@ -265,6 +283,7 @@ void pfc_default_options(pfc_options* o) {
   o->tau_max = 1e9;
   o->blocks_per_sm = 0;
   o->pcg_variant = 2;
+  o->inner_operator = 1;
 }
 
 const char* pfc_status_string(int s) {
@@ -326,6 +345,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "restart must be in 1..40"));
   if (c->opt.precision < 0 || c->opt.precision > 2) return bail(fail(c, PFC_ERR_INVALID, "precision must be 0, 1 or 2"));
   if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 2) return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1 or 2"));
+  if (c->opt.inner_operator < 0 || c->opt.inner_operator > 1)
+    return bail(fail(c, PFC_ERR_INVALID, "inner_operator must be 0 or 1"));
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
     return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
   c->stream = (cudaStream_t)cuda_stream;
@@ -340,7 +361,11 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
 
   pfc::HostSetup S;
   std::string err;
-  if (!pfc::build_setup(dim, side, length, S, err)) return bail(fail(c, PFC_ERR_INVALID, err));
+  const bool stencil = c->opt.inner_operator == 1;
+  if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma))
+    return bail(fail(c, PFC_ERR_INVALID, err));
+  if (stencil && ((int)S.st_off.size() > pfc::kMaxStencil || S.ntypes_dof > 8))
+    return bail(fail(c, PFC_ERR_INVALID, "structured stencil larger than the kernel's table"));
   c->n = S.n;
   c->n_pad = S.n_pad;
   c->nslices = S.nslices;
@@ -411,6 +436,11 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_dptr = L.take(sizeof(int) * S.dof_ptr.size());
   const size_t o_didx = L.take(sizeof(int) * std::max<size_t>(1, S.dof_idx.size()));
   const size_t o_blk = L.take(sizeof(int) * blk.size());
+  const size_t o_ri = L.take(S.rowinfo.size());
+  const size_t o_sts = L.take(sizeof(int) * std::max<size_t>(1, S.st_start.size()));
+  const size_t o_sto = L.take(sizeof(int) * std::max<size_t>(1, S.st_off.size()));
+  const size_t o_stm = L.take(sizeof(double) * std::max<size_t>(1, S.st_wM.size()));
+  const size_t o_stk = L.take(sizeof(double) * std::max<size_t>(1, S.st_wK.size()));
   const size_t o_mt = L.take(sizeof(double) * S.ref.mass.size());
   const size_t o_st = L.take(sizeof(double) * S.ref.stiff.size());
   const size_t vals = sizeof(double) * S.nnz_sell;
@@ -464,6 +494,12 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->dptr = (int*)(A + o_dptr);
   c->didx = (int*)(A + o_didx);
   c->blk = (int*)(A + o_blk);
+  c->rowinfo = (unsigned char*)(A + o_ri);
+  c->st_start = (int*)(A + o_sts);
+  c->st_off = (int*)(A + o_sto);
+  c->st_wM = (double*)(A + o_stm);
+  c->st_wK = (double*)(A + o_stk);
+  c->st_types = stencil ? S.ntypes_dof : 0;
   c->mass_tab = (double*)(A + o_mt);
   c->stiff_tab = (double*)(A + o_st);
   c->Mv = (double*)(A + o_M);
@@ -533,6 +569,13 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   UP(c->dptr, S.dof_ptr);
   if (!S.dof_idx.empty()) UP(c->didx, S.dof_idx);
   UP(c->blk, blk);
+  UP(c->rowinfo, S.rowinfo);
+  if (stencil) {
+    UP(c->st_start, S.st_start);
+    UP(c->st_off, S.st_off);
+    UP(c->st_wM, S.st_wM);
+    UP(c->st_wK, S.st_wK);
+  }
   UP(c->mass_tab, S.ref.mass);
   UP(c->stiff_tab, S.ref.stiff);
   {

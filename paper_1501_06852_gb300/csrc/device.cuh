@@ -64,7 +64,20 @@ struct SolveArgs {
   int barrier_extra;       // 0; > 0 only in the timeout self-test (waits cannot complete)
   int pcg_variant;         // 0 standard PCG (3 grid barriers per iteration), 1 pipelined PCG (1)
   int prof;                // 1: block 0 records per-phase work and wait times
+  // structured-stencil inner operators (lexicographic internal order only)
+  int stencil;             // 1: interior rows of M, K, M + delta K, M + sqrt(delta) K use the stencils
+  const unsigned char* rowinfo;  // bits 0-2 dof type, bit 3 interior
+  const int* st_start;     // ntypes + 1
+  const int* st_off;       // column offset of each stencil entry
+  const double* st_wM;     // M and K weights of each entry
+  const double* st_wK;
+  int st_types;
+  double op_cK[4];         // inner operator op = M, K, M + delta K, M + sqrt(delta) K:
+  double op_cM[4];         //   weights op_cM[op] * wM + op_cK[op] * wK
 };
+
+constexpr int kMaxStencil = 640;   // stencil entries over all dof types
+enum : int { kOpM = 0, kOpK = 1, kOpMdK = 2, kOpMsK = 3 };
 
 constexpr int kInnerVecs = 16;
 

@@ -31,7 +31,7 @@ namespace pfc {
 void element_path(int dim, int t, int verts[4][3]);
 void local_edge(int dim, int e, int& a, int& b);
 
-bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err) {
+bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma) {
   if (dim != 2 && dim != 3) {
     err = "dim must be 2 or 3";
     return false;
@@ -59,6 +59,7 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   S.n = (int)n64;
   S.ntypes = ntypes;
   S.nl = nl;
+  S.sigma = sigma < 1 ? 1 : sigma;
   if (!build_reference(dim, S.h, S.ref, err)) return false;
   const int n = S.n;
   const int E = (int)(cells64 * ntypes);
@@ -121,8 +122,8 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   // --- SELL-32-sigma ordering -------------------------------------------------
   S.perm.resize(n);
   std::iota(S.perm.begin(), S.perm.end(), 0);
-  for (int w0 = 0; w0 < n; w0 += kSellSigma) {
-    int w1 = std::min(n, w0 + kSellSigma);
+  for (int w0 = 0; w0 < n; w0 += S.sigma) {
+    int w1 = std::min(n, w0 + S.sigma);
     std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
   }
   S.iperm.resize(n);
@@ -227,6 +228,69 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   for (int p = 0; p < n; ++p) {
     int i = S.perm[p];
     std::copy(inc.begin() + inc_ptr[i], inc.begin() + inc_ptr[i + 1], S.dof_idx.begin() + S.dof_ptr[p]);
+  }
+
+  // --- structured stencils of M and K (lexicographic internal order only) ------
+  S.ntypes_dof = 1 << dim;
+  S.rowinfo.assign(S.n_pad, 0);
+  if (S.sigma == 1) {
+    auto dof_type = [&](int i) {
+      const int a = i % (int)lat, b = (int)((i / lat) % lat), c = dim == 3 ? (int)(i / (lat * lat)) : 0;
+      return (a & 1) | ((b & 1) << 1) | ((c & 1) << 2);
+    };
+    // rows whose incident-element count is the maximum of their type have all
+    // their elements, hence the interior stencil of the type
+    std::vector<int> maxinc(S.ntypes_dof, 0), rep(S.ntypes_dof, -1);
+    for (int i = 0; i < n; ++i) {
+      const int t = dof_type(i), k = inc_ptr[i + 1] - inc_ptr[i];
+      if (k > maxinc[t]) {
+        maxinc[t] = k;
+        rep[t] = i;
+      }
+    }
+    S.st_start.assign(S.ntypes_dof + 1, 0);
+    S.st_off.clear();
+    S.st_wM.clear();
+    S.st_wK.clear();
+    std::vector<int> buf;
+    for (int t = 0; t < S.ntypes_dof; ++t) {
+      const int i = rep[t];
+      if (i >= 0) {
+        row_cols(i, buf);  // internal == lexicographic here
+        const int s_ = i / kSellC, lane = i % kSellC, base = S.slice_ptr[s_] + lane;
+        for (int j = 0; j < (int)buf.size(); ++j) {
+          const int slot = base + j * kSellC;
+          double m = 0.0, k = 0.0;
+          for (int q = S.contrib_ptr[slot]; q < S.contrib_ptr[slot + 1]; ++q) {
+            const int idx = S.contrib_idx[q], pr = idx / E, e = idx - pr * E, et = e % ntypes;
+            m += R.mass[(size_t)et * R.npairs + pr];
+            k += R.stiff[(size_t)et * R.npairs + pr];
+          }
+          S.st_off.push_back(buf[j] - i);
+          S.st_wM.push_back(m);
+          S.st_wK.push_back(k);
+        }
+      }
+      S.st_start[t + 1] = (int)S.st_off.size();
+    }
+    // interior: same element count AND the same column offsets as the type's
+    // representative (translation invariance then gives the same values)
+#pragma omp parallel
+    {
+      std::vector<int> rb;
+#pragma omp for schedule(static)
+      for (int i = 0; i < n; ++i) {
+        const int t = dof_type(i);
+        bool interior = (inc_ptr[i + 1] - inc_ptr[i]) == maxinc[t];
+        if (interior) {
+          row_cols(i, rb);
+          const int k0 = S.st_start[t], len = S.st_start[t + 1] - k0;
+          interior = (int)rb.size() == len;
+          for (int j = 0; interior && j < len; ++j) interior = rb[j] - i == S.st_off[k0 + j];
+        }
+        S.rowinfo[i] = (unsigned char)(t | (interior ? 8 : 0));
+      }
+    }
   }
   return true;
 }

@@ -50,10 +50,21 @@ struct HostSetup {
   std::vector<int> dof_ptr;       // n_pad + 1
   std::vector<int> dof_idx;       // l * E + e for each element incident to a row
   RefTensors ref;
+  // Structured stencils of the constant matrices (only with sigma == 1, where the
+  // internal order is lexicographic): dof type t = lattice-coordinate parities;
+  // every row whose incident elements all exist ("interior") has the stencil of
+  // its type: M_i,i+off[k] = st_wM[k], K_i,i+off[k] = st_wK[k], k in
+  // [st_start[t], st_start[t+1]).
+  int sigma = kSellSigma;
+  int ntypes_dof = 0;
+  std::vector<int> st_start;      // ntypes_dof + 1
+  std::vector<int> st_off;
+  std::vector<double> st_wM, st_wK;
+  std::vector<unsigned char> rowinfo;  // n_pad: bits 0-2 dof type, bit 3 interior
 };
 
 bool build_reference(int dim, double h, RefTensors& out, std::string& err);
-bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err);
+bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err, int sigma = kSellSigma);
 
 // Bytes of device memory a context of this size holds (estimate used for admission).
 size_t footprint_estimate(int dim, int side, int restart, int precision);

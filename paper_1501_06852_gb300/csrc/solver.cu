@@ -86,6 +86,11 @@ struct Grid {
 
 __shared__ unsigned long long s_t_last;
 __shared__ long long s_prof[8];
+// structured-stencil tables, loaded once per block: entry offsets, the start of
+// each dof type, and the weights of the four inner operators in the inner type
+__shared__ int s_st_off[kMaxStencil];
+__shared__ int s_st_start[9];
+__shared__ __align__(16) unsigned char s_st_w_raw[4 * kMaxStencil * sizeof(double)];
 
 // Every warp owns a contiguous range of slices (the host splits each block's
 // range so that the warps carry equal SpMV-plus-vector cost).  Groups of kGroup
@@ -263,6 +268,29 @@ __device__ __forceinline__ Acc sell_row_wide(int2 se, const int* __restrict__ co
 #endif
 }
 
+// Row `row` (slice s, this lane) of inner operator op, whose assembled values are
+// vals: interior rows use the structured stencil from shared memory (no matrix
+// or index bytes), the others their SELL row.  Called by all 32 lanes together.
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int op, const TM* __restrict__ vals,
+                                         const TX* x, int s, int lane) {
+  const int2 se = slice_bounds(g, a.slice_ptr, s);
+  if (a.stencil) {
+    const int row = s * 32 + lane;
+    const unsigned info = __ldg(a.rowinfo + row);
+    if (info & 8u) {
+      const int t = info & 7u;
+      const int k0 = s_st_start[t], k1 = s_st_start[t + 1];
+      const Acc* w = reinterpret_cast<const Acc*>(s_st_w_raw) + op * kMaxStencil;
+      Acc acc = Acc(0);
+#pragma unroll 8
+      for (int k = k0; k < k1; ++k) acc = fma(w[k], (Acc)x[row + s_st_off[k]], acc);
+      return acc;
+    }
+  }
+  return sell_row_wide<Acc>(se, a.cols, vals, x, lane);
+}
+
 struct InnerCount {
   long long its = 0;
   int calls = 0;
@@ -296,12 +324,13 @@ struct RhsSpec {
   const double* vin;
   double alpha;
   const TM* mat;
+  int op;
   const TV* vx;
   double beta;
   __device__ __forceinline__ double operator()(const Grid& g, const SolveArgs& a, int s, int lane, int row) const {
     using Acc = typename AccOf<TV>::type;
     double v = vin ? alpha * vin[row] : 0.0;
-    if (mat) v += beta * (double)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, mat, vx, lane);
+    if (mat) v += beta * (double)inner_row<Acc>(g, a, op, mat, vx, s, lane);
     return v;
   }
 };
@@ -309,7 +338,7 @@ struct RhsSpec {
 // Textbook Jacobi-PCG for A x = rhs, x0 = 0, stop at ||r||_2 <= rtol ||rhs||_2.
 // The right-hand side is evaluated once per owned row in the first phase.
 template <class TM, class TV>
-__device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM* AV, const TV* DI, TV* x,
+__device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM* AV, int op, const TV* DI, TV* x,
                                           RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   Ctx<TM, TV> c(a);
   using Acc = typename Ctx<TM, TV>::Acc;
@@ -352,7 +381,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
       const Acc pr = (Acc)p[row];
-      const TV qv = (TV)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, p, lane);
+      const TV qv = (TV)inner_row<Acc>(g, a, op, AV, p, s, lane);
       q[row] = qv;
       ppq = fma(pr, (Acc)qv, ppq);
     }
@@ -441,7 +470,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
 //   x += a p, r -= a s, u -= a q, w -= a z, m' = D w
 // and the partial sums of (r, u), (w, u), (r, r); one barrier follows.
 template <class TM, class TV>
-__device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM* AV, const TV* DI, TV* x,
+__device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM* AV, int op, const TV* DI, TV* x,
                                            RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   Ctx<TM, TV> c(a);
   using Acc = typename Ctx<TM, TV>::Acc;
@@ -492,7 +521,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     const int row = s * 32 + lane;
     const TV uvv = u[row];
     const Acc rr0 = (Acc)r[row], dd0 = (Acc)DI[row];
-    const TV wvv = (TV)sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, u, lane);
+    const TV wvv = (TV)inner_row<Acc>(g, a, op, AV, u, s, lane);
     w[row] = wvv;
     mcur[row] = (TV)(dd0 * (Acc)wvv);
     pg = fma(rr0, (Acc)uvv, pg);
@@ -526,7 +555,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       const Acc mv = (Acc)mcur[row], zo = (Acc)zv[row], qo = (Acc)qv[row], so = (Acc)sv[row];
       const Acc po = (Acc)pv[row], xo = (Acc)x[row], ro = (Acc)r[row], uo = (Acc)u[row], wo = (Acc)w[row];
       const Acc dd = (Acc)DI[row];
-      const Acc na = sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s), a.cols, AV, mcur, lane);
+      const Acc na = inner_row<Acc>(g, a, op, AV, mcur, s, lane);
       const Acc z1 = na + be * zo;
       const Acc q1 = mv + be * qo;
       const Acc s1 = wo + be * so;
@@ -572,10 +601,10 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
 }
 
 template <class TM, class TV>
-__device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, const TV* DI, TV* x,
+__device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, int op, const TV* DI, TV* x,
                                     RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
-  if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, DI, x, rhs, rtol, maxit, cnt, its);
-  return pcg_standard<TM, TV>(g, c.a, AV, DI, x, rhs, rtol, maxit, cnt, its);
+  if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
+  return pcg_standard<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
 }
 
 // z = P_CH^{-1} v for 3-field float64 vectors (n_pad per field).  Ends with a
@@ -594,15 +623,19 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
   int its;
   using R = RhsSpec<TM, TV>;
   // (1) M y0 = v0
-  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVy0), R{v0, 1.0, nullptr, nullptr, 0.0}, rt, mi, cnt, its)) return false;
+  if (!pcg(g, c, c.iM(), kOpM, c.dM(), c.vec(kVy0), R{v0, 1.0, nullptr, 0, nullptr, 0.0}, rt, mi, cnt, its))
+    return false;
   // (2) (M + delta K) y1 = gamma v1 - tau_e K y0
-  if (!pcg(g, c, c.iMdK(), c.dMdK(), c.vec(kVy1), R{v1, a.gamma, c.iK(), c.vec(kVy0), -a.tau_e}, rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMdK(), kOpMdK, c.dMdK(), c.vec(kVy1), R{v1, a.gamma, c.iK(), kOpK, c.vec(kVy0), -a.tau_e}, rt,
+           mi, cnt, its))
     return false;
   // (3.1) (M + sqrt(delta) K) w = M y1
-  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVwv), R{nullptr, 0.0, c.iM(), c.vec(kVy1), 1.0}, rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVwv), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVy1), 1.0}, rt, mi,
+           cnt, its))
     return false;
   // (3.2) (M + sqrt(delta) K) x1 = M w
-  if (!pcg(g, c, c.iMsK(), c.dMsK(), c.vec(kVx1), R{nullptr, 0.0, c.iM(), c.vec(kVwv), 1.0}, rt, mi, cnt, its))
+  if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVx1), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVwv), 1.0}, rt, mi,
+           cnt, its))
     return false;
   // (4) x0 = y0 + (y1 - x1) / delta, and z = (x0, x1, .)
   FOR_MY_GROUPS(g, s0, nsl) {
@@ -617,7 +650,8 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
     }
   }
   // (5) M x2 = v2 - K x1
-  if (!pcg(g, c, c.iM(), c.dM(), c.vec(kVx2), R{v2, 1.0, c.iK(), c.vec(kVx1), -1.0}, rt, mi, cnt, its)) return false;
+  if (!pcg(g, c, c.iM(), kOpM, c.dM(), c.vec(kVx2), R{v2, 1.0, c.iK(), kOpK, c.vec(kVx1), -1.0}, rt, mi, cnt, its))
+    return false;
   FOR_MY_GROUPS(g, s0, nsl) {
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
@@ -857,6 +891,19 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
     for (int k = 0; k < 8; ++k) s_prof[k] = 0;
     s_t_last = global_ns();
   }
+  if (a.stencil) {
+    using Acc = typename AccOf<TV>::type;
+    const int ns = __ldg(a.st_start + a.st_types);
+    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+      s_st_off[k] = __ldg(a.st_off + k);
+      const double wm = __ldg(a.st_wM + k), wk = __ldg(a.st_wK + k);
+      Acc* w = reinterpret_cast<Acc*>(s_st_w_raw);
+#pragma unroll
+      for (int op = 0; op < 4; ++op) w[op * kMaxStencil + k] = (Acc)(a.op_cM[op] * wm + a.op_cK[op] * wk);
+    }
+    if ((int)threadIdx.x <= a.st_types) s_st_start[threadIdx.x] = __ldg(a.st_start + threadIdx.x);
+    __syncthreads();
+  }
   Ctx<TM, TV> c(a);
   const int lane = threadIdx.x & 31;
   if (a.mode == 0) {
@@ -868,10 +915,11 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
     InnerCount cnt;
     int its = 0;
     const TM* AV = a.which == 0 ? c.iM() : a.which == 1 ? c.iMdK() : c.iMsK();
+    const int op = a.which == 0 ? kOpM : a.which == 1 ? kOpMdK : kOpMsK;
     const TV* DI = a.which == 0 ? c.dM() : a.which == 1 ? c.dMdK() : c.dMsK();
     const double* b = a.b;
-    if (!pcg(g, c, AV, DI, c.vec(kVy0), RhsSpec<TM, TV>{b, 1.0, nullptr, nullptr, 0.0}, a.inner_rtol, a.max_inner,
-             cnt, its))
+    if (!pcg(g, c, AV, op, DI, c.vec(kVy0), RhsSpec<TM, TV>{b, 1.0, nullptr, 0, nullptr, 0.0}, a.inner_rtol,
+             a.max_inner, cnt, its))
       return;
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;

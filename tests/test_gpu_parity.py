@@ -112,9 +112,10 @@ def test_stage_rhs_matches_oracle(case):
             assert_close_scaled(got, want, np.concatenate([s0, s1, s2]))
 
 
+@pytest.mark.parametrize("inner_op", [0, 1], ids=["sell", "stencil"])
 @pytest.mark.parametrize("variant", [0, 1], ids=["pcg", "pipelined"])
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
-def test_pcg_matches_oracle(case, variant):
+def test_pcg_matches_oracle(case, variant, inner_op):
     dim, side, L, r, pm, amp = case
     prob = problem(dim, side, L, r)
     x = state_for(prob, dim, side, pm, amp)
@@ -122,7 +123,7 @@ def test_pcg_matches_oracle(case, variant):
     delta = math.sqrt(ROS3PW.gamma * tau)
     mats = [prob.M, (prob.M + delta * prob.K).tocsr(), (prob.M + math.sqrt(delta) * prob.K).tocsr()]
     b = synth.random_vector(prob.n, 8)
-    with pfc.PFCSolver(dim, side, L, r=r, pcg_variant=variant) as s:
+    with pfc.PFCSolver(dim, side, L, r=r, pcg_variant=variant, inner_operator=inner_op) as s:
         s.assemble(cuda(x), tau)
         for which, A in enumerate(mats):
             for rtol in (1e-3, 1e-10):
@@ -156,15 +157,16 @@ def test_mixed_precision_pcg_meets_tolerance(precision):
         assert its < 200
 
 
+@pytest.mark.parametrize("inner_op", [0, 1], ids=["sell", "stencil"])
 @pytest.mark.parametrize("case", CASES[:3], ids=IDS[:3])
-def test_preconditioner_matches_oracle(case):
+def test_preconditioner_matches_oracle(case, inner_op):
     dim, side, L, r, pm, amp = case
     prob = problem(dim, side, L, r)
     x = state_for(prob, dim, side, pm, amp)
     tau = 0.25
     v = synth.random_vector(3 * prob.n, 9)
     ref = PCH(prob.M, prob.K, tau, ROS3PW.gamma, inner="exact").apply(v)
-    with pfc.PFCSolver(dim, side, L, r=r, inner_rtol=1e-13) as s:
+    with pfc.PFCSolver(dim, side, L, r=r, inner_rtol=1e-13, inner_operator=inner_op) as s:
         s.assemble(cuda(x), tau)
         got = host(s.apply(pfc.OP_PCH, cuda(v)))
     assert np.linalg.norm(got - ref) <= 1e-9 * np.linalg.norm(ref)
@@ -187,14 +189,16 @@ def oracle_stage(case, tau, stage_seed=1):
     return _ref_solutions[key]
 
 
+@pytest.mark.parametrize("inner_op", [0, 1], ids=["sell", "stencil"])
 @pytest.mark.parametrize("variant", [0, 1], ids=["pcg", "pipelined"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_stage_solve_parity(case, precision, variant):
+def test_stage_solve_parity(case, precision, variant, inner_op):
     dim, side, L, r, pm, amp = case
     tau = 0.1
     x, b, yref = oracle_stage(case, tau)
-    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11, pcg_variant=variant) as s:
+    with pfc.PFCSolver(dim, side, L, r=r, precision=precision, outer_tol=1e-11, pcg_variant=variant,
+                       inner_operator=inner_op) as s:
         s.assemble(cuda(x), tau)
         y, st = s.stage_solve(cuda(b))
         y = host(y)
