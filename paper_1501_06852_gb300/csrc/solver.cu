@@ -99,12 +99,6 @@ __shared__ __align__(16) unsigned char s_st_w_raw[4 * kMaxStencil * sizeof(doubl
   for (int s0 = (g).w_lo; s0 < (g).w_hi; s0 += kGroup) \
     if (const int nsl = min(kGroup, (g).w_hi - s0); true)
 
-// Staged vector phases: GR slices per warp have all their loads in flight at once
-// (8 for 4-byte inner vectors, kGroup for 8-byte ones).
-#define FOR_MY_GROUPS_N(g, s0, nsl, GR)                    \
-  for (int s0 = (g).w_lo; s0 < (g).w_hi; s0 += (GR)) \
-    if (const int nsl = min((GR), (g).w_hi - s0); true)
-
 #define FOR_MY_SLICES(g, s) for (int s = (g).w_lo; s < (g).w_hi; ++s)
 
 // First slot and end slot of slice s (one of this warp's slices).  Called by
@@ -285,19 +279,12 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
     const int row = s * 32 + lane;
     const unsigned info = __ldg(a.rowinfo + row);
     if (info & 8u) {
-      constexpr int CH = sizeof(Acc) == 8 ? 10 : 20;
       const int t = info & 7u;
       const int k0 = s_st_start[t], k1 = s_st_start[t + 1];
       const Acc* w = reinterpret_cast<const Acc*>(s_st_w_raw) + op * kMaxStencil;
       Acc acc = Acc(0);
-      for (int kb = k0; kb < k1; kb += CH) {
-        Acc xv[CH];
-#pragma unroll
-        for (int kk = 0; kk < CH; ++kk) xv[kk] = (kb + kk < k1) ? (Acc)x[row + s_st_off[kb + kk]] : Acc(0);
-#pragma unroll
-        for (int kk = 0; kk < CH; ++kk)
-          if (kb + kk < k1) acc = fma(w[kb + kk], xv[kk], acc);
-      }
+#pragma unroll 8
+      for (int k = k0; k < k1; ++k) acc = fma(w[k], (Acc)x[row + s_st_off[k]], acc);
       return acc;
     }
   }
@@ -412,11 +399,10 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     }
     const Acc alpha = (Acc)(rz / pq);
     Acc prr = Acc(0), prz = Acc(0);
-    constexpr int GR = sizeof(TV) == 4 ? 8 : kGroup;
-    FOR_MY_GROUPS_N(g, s0, nsl, GR) {
-      TV xv[GR], pv[GR], qv[GR], rv[GR], dv[GR];
+    FOR_MY_GROUPS(g, s0, nsl) {
+      TV xv[kGroup], pv[kGroup], qv[kGroup], rv[kGroup], dv[kGroup];
 #pragma unroll
-      for (int uu = 0; uu < GR; ++uu) {
+      for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
           const int row = (s0 + uu) * 32 + lane;
           xv[uu] = x[row];
@@ -427,7 +413,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         }
       }
 #pragma unroll
-      for (int uu = 0; uu < GR; ++uu) {
+      for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
           const int row = (s0 + uu) * 32 + lane;
           const Acc xn = (Acc)xv[uu] + alpha * (Acc)pv[uu];
@@ -452,11 +438,10 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     }
     const Acc beta = (Acc)(red.y / rz);
     rz = red.y;
-    constexpr int GRC = sizeof(TV) == 4 ? 8 : kGroup;
-    FOR_MY_GROUPS_N(g, s0, nsl, GRC) {
-      TV dv[GRC], rv[GRC], pv[GRC];
+    FOR_MY_GROUPS(g, s0, nsl) {
+      TV dv[kGroup], rv[kGroup], pv[kGroup];
 #pragma unroll
-      for (int uu = 0; uu < GRC; ++uu) {
+      for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
           const int row = (s0 + uu) * 32 + lane;
           dv[uu] = DI[row];
@@ -465,7 +450,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         }
       }
 #pragma unroll
-      for (int uu = 0; uu < GRC; ++uu) {
+      for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
           const int row = (s0 + uu) * 32 + lane;
           p[row] = (TV)((Acc)dv[uu] * (Acc)rv[uu] + beta * (Acc)pv[uu]);
