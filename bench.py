@@ -71,12 +71,16 @@ def tau_cap(w: synth.Workload) -> float:
 
 
 # ----------------------------------------------------------------------------- bytes
-def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, variant: int = 1) -> float:
+def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, variant: int = 1,
+                      inner_nnz: int | None = None) -> float:
     """Algorithmic HBM bytes of one persistent stage-solve launch, from its logged counts.
 
     Each array counted once per pass that needs it; gathered vectors once; int32
     column indices; SELL padding not counted.  N = nnz of one block, n = dofs/field,
-    sM / sv = bytes of an inner matrix value / inner vector entry, S = N (sM + 4).
+    sM / sv = bytes of an inner matrix value / inner vector entry, S = N_in (sM + 4)
+    with N_in the nonzeros an inner SpMV reads from memory: N with assembled inner
+    matrices, only the boundary rows' nonzeros with the structured stencils
+    (interior rows read no matrix data).
       PCG iteration:       S + 13 n sv (textbook: SpMV; x, r, p, q, D passes)
                            S + 19 n sv (pipelined: SpMV; 9 recurrences read and written, D)
       PCG set-up (x5 per P_CH): 4 n sv (textbook) or S + 14 n sv (pipelined, incl. w = A u)
@@ -85,7 +89,7 @@ def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, v
       restart cycle:       28 N + 96 n + 24 n (k + 2) (true residual, basis scaling, y update)
     """
     sM, sv = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 4)}[precision]
-    S = nnz * (sM + 4)
+    S = (nnz if inner_nnz is None else inner_nnz) * (sM + 4)
     it = S + (19 if variant == 1 else 13) * n * sv
     setup = (S + 14 * n * sv) if variant == 1 else 4 * n * sv
     b = st.inner_its * it
@@ -257,6 +261,8 @@ def native(args, world, rank, local, pg):
     s = make(args.precision)
     n = s.n
     nnz = pfc.host_pattern(w.dim, w.side, w.length)["nnz"]
+    inner_nnz = pfc.host_stencil(w.dim, w.side, w.length)["boundary_nnz"]   # stencil inner operators
+    variant = 1 if args.precision == "fp64" else 0                           # automatic PCG form
     state0 = s.init_state(psi0)
     state = state0.clone()
     tau = w.tau0
@@ -279,7 +285,8 @@ def native(args, world, rank, local, pg):
     launches = c1["kernel_launches"] - c0["kernel_launches"]
     nsolver = c1["solver_launches"] - c0["solver_launches"]
     solver_ms = (c1["solver_ms"] - c0["solver_ms"]) / max(nsolver, 1)
-    bytes_per = statistics.mean(stage_solve_bytes(st, n, nnz, args.precision) for st in stats)
+    bytes_per = statistics.mean(stage_solve_bytes(st, n, nnz, args.precision, variant=variant, inner_nnz=inner_nnz)
+                                for st in stats)
     achieved = bytes_per / (solver_ms / 1e3) / 1e9
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
@@ -298,7 +305,8 @@ def native(args, world, rank, local, pg):
             "workload": f"{w.name}: {w.dim}D [0,{w.length:g}]^{w.dim}, side {w.side}, P2, {n} dofs/field, "
                         f"{3 * n} unknowns, r={w.r}, psi={w.psi_mean}+{w.amp}U(-1,1) seed {w.seed}, "
                         f"tau0={w.tau0}, adaptive Ros3Pw (Lemma-3 guard tau<={cap:.3g})",
-            "precision": f"{args.precision} inner PCG, fp64 outer FGMRES(30)/Arnoldi/step control",
+            "precision": f"{args.precision} inner PCG (textbook form), fp64 outer FGMRES(30)/Arnoldi/step control",
+            "inner_operator": "structured stencils for M, K, M+dK, M+sqrt(d)K (boundary rows assembled SELL-32)",
             "outer_tol": args.outer_tol, "inner_rtol": 1e-3,
             "l2": "inputs larger than L2: matrices + Krylov bases ~3 GB per instance vs 129 MB L2",
             "parallelism": f"{world} independent replica(s), one per GPU",

@@ -193,6 +193,11 @@ pfc_status pfc_counters(const pfc_ctx* ctx, long long* kernel_launches, long lon
  * out4 = {n, nnz of one block, stored SELL slots, elements}. */
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
 
+/* Host-only inspection of the structured stencils (no GPU needed):
+ * out3 = {rows that use the stencil, nonzeros of the rows that keep their
+ * assembled values, stencil entries over all dof types}. */
+pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3);
+
 /* Text of the most recent error of ctx ("" if none; static text for NULL). */
 const char* pfc_last_error(const pfc_ctx* ctx);
 

@@ -65,6 +65,7 @@ def _load():
         "pfc_pcg": (I, [P, I, P, P, D, ctypes.POINTER(I)]),
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_set_timing": (I, [P, I]),
         "pfc_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(D)]),
@@ -128,6 +129,15 @@ def host_pattern(dim: int, side: int, length: float = 1.0) -> dict:
     if st != 0:
         raise PFCError(st, "host_pattern")
     return {"n": out[0], "nnz": out[1], "nnz_sell": out[2], "elements": out[3]}
+
+
+def host_stencil(dim: int, side: int, length: float = 1.0) -> dict:
+    """Stencil sizes from the host builder (no GPU needed)."""
+    out = (ctypes.c_int64 * 3)()
+    st = lib.pfc_host_stencil(dim, side, float(length), out)
+    if st != 0:
+        raise PFCError(st, "host_stencil")
+    return {"interior_rows": out[0], "boundary_nnz": out[1], "stencil_entries": out[2]}
 
 
 class PFCSolver:

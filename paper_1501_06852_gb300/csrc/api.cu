@@ -845,6 +845,33 @@ pfc_status pfc_counters(const pfc_ctx* c, long long* launches, long long* solver
   return PFC_OK;
 }
 
+pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3) {
+  if (!out3) return PFC_ERR_INVALID;
+  pfc::HostSetup S;
+  std::string err;
+  if (!pfc::build_setup(dim, side, length, S, err, 1)) return PFC_ERR_INVALID;
+  int64_t interior = 0, bnnz = 0;
+  for (int p = 0; p < S.n; ++p) {
+    if (S.rowinfo[p] & 8) {
+      ++interior;
+    } else {
+      bnnz += 0;  // counted below from the row's stored slots
+    }
+  }
+  // nonzeros of the rows that keep their assembled values (true row lengths)
+  for (int p = 0; p < S.n; ++p) {
+    if (S.rowinfo[p] & 8) continue;
+    const int s = p / pfc::kSellC, lane = p % pfc::kSellC, base = S.slice_ptr[s] + lane;
+    const int w = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / pfc::kSellC;
+    for (int j = 0; j < w; ++j)
+      if (S.cols[base + j * pfc::kSellC] != p || S.diag_pos[p] == base + j * pfc::kSellC) ++bnnz;
+  }
+  out3[0] = interior;
+  out3[1] = bnnz;
+  out3[2] = (int64_t)S.st_off.size();
+  return PFC_OK;
+}
+
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4) {
   if (!out4) return PFC_ERR_INVALID;
   pfc::HostSetup S;

@@ -91,7 +91,8 @@ template <class A> __device__ __forceinline__ A ld_val(const __half* p) { return
 template <class T> __device__ __forceinline__ T from_acc(double v) { return (T)v; }
 template <class T> __device__ __forceinline__ T from_acc(float v) { return (T)v; }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

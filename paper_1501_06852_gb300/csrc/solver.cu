@@ -88,9 +88,13 @@ __shared__ unsigned long long s_t_last;
 __shared__ long long s_prof[8];
 // structured-stencil tables, loaded once per block: entry offsets, the start of
 // each dof type, and the weights of the four inner operators in the inner type
-__shared__ int s_st_off[kMaxStencil];
 __shared__ int s_st_start[9];
-__shared__ __align__(16) unsigned char s_st_w_raw[4 * kMaxStencil * sizeof(double)];
+__shared__ __align__(16) unsigned char s_st_raw[4 * kMaxStencil * 16];
+
+// one stencil entry: column offset and weight, read with a single shared load
+template <class Acc> struct StEntry;
+template <> struct __align__(8) StEntry<float> { int off; float w; };
+template <> struct __align__(16) StEntry<double> { int off; int pad; double w; };
 
 // Every warp owns a contiguous range of slices (the host splits each block's
 // range so that the warps carry equal SpMV-plus-vector cost).  Groups of kGroup
@@ -167,48 +171,67 @@ __device__ bool grid_sync(Grid& g, int tag) {
 // barrier every thread of a block loads at most one partial (the grid has at most
 // kThreads blocks), so the read-back is one memory round trip, and the partials
 // are summed in a fixed order.
-__device__ bool grid_sum(Grid& g, double a, double b, double c, double4& out, int tag) {
+template <class T>
+__device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
+  // T is the arithmetic of every stage of the tree: float for the float32 inner
+  // solves (float64 throughput is scarce on this GPU), double everywhere else
   __shared__ double4 s_w[kWarps];
   __shared__ double4 s_res;
   a = warp_sum(a);
   b = warp_sum(b);
   c = warp_sum(c);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) s_w[w] = make_double4(a, b, c, 0.0);
+  if (l == 0) s_w[w] = make_double4((double)a, (double)b, (double)c, 0.0);
   __syncthreads();
   const int slot = g.ring;
   g.ring = (g.ring + 1) % kRing;
   if (w == 0) {
-    double4 t = l < kWarps ? s_w[l] : make_double4(0.0, 0.0, 0.0, 0.0);
-    t.x = warp_sum(t.x);
-    t.y = warp_sum(t.y);
-    t.z = warp_sum(t.z);
+    T tx = T(0), ty = T(0), tz = T(0);
+    if (l < kWarps) {
+      const double4 t = s_w[l];
+      tx = (T)t.x;
+      ty = (T)t.y;
+      tz = (T)t.z;
+    }
+    tx = warp_sum(tx);
+    ty = warp_sum(ty);
+    tz = warp_sum(tz);
     if (l == 0) {
       double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + blockIdx.x);
-      __stcg(dst, make_double2(t.x, t.y));
-      __stcg(dst + 1, make_double2(t.z, 0.0));
+      __stcg(dst, make_double2((double)tx, (double)ty));
+      __stcg(dst + 1, make_double2((double)tz, 0.0));
     }
   }
   if (!grid_sync(g, tag)) return false;
-  double px = 0.0, py = 0.0, pz = 0.0;
-  if ((int)threadIdx.x < g.G) {
-    const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + threadIdx.x);
-    const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
-    px = t0.x;
-    py = t0.y;
-    pz = t1.x;
+  // one partial per thread of the first ceil(G / 32) warps, summed in a fixed order
+  if (w * 32 < g.G) {
+    T px = T(0), py = T(0), pz = T(0);
+    if ((int)threadIdx.x < g.G) {
+      const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + threadIdx.x);
+      const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
+      px = (T)t0.x;
+      py = (T)t0.y;
+      pz = (T)t1.x;
+    }
+    px = warp_sum(px);
+    py = warp_sum(py);
+    pz = warp_sum(pz);
+    if (l == 0) s_w[w] = make_double4((double)px, (double)py, (double)pz, 0.0);
   }
-  px = warp_sum(px);
-  py = warp_sum(py);
-  pz = warp_sum(pz);
-  if (l == 0) s_w[w] = make_double4(px, py, pz, 0.0);
   __syncthreads();
   if (w == 0) {
-    double4 t = l < kWarps ? s_w[l] : make_double4(0.0, 0.0, 0.0, 0.0);
-    t.x = warp_sum(t.x);
-    t.y = warp_sum(t.y);
-    t.z = warp_sum(t.z);
-    if (l == 0) s_res = t;
+    const int nw = (g.G + 31) >> 5;
+    T tx = T(0), ty = T(0), tz = T(0);
+    if (l < nw) {
+      const double4 t = s_w[l];
+      tx = (T)t.x;
+      ty = (T)t.y;
+      tz = (T)t.z;
+    }
+    tx = warp_sum(tx);
+    ty = warp_sum(ty);
+    tz = warp_sum(tz);
+    if (l == 0) s_res = make_double4((double)tx, (double)ty, (double)tz, 0.0);
   }
   __syncthreads();
   out = s_res;
@@ -281,10 +304,13 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
     if (info & 8u) {
       const int t = info & 7u;
       const int k0 = s_st_start[t], k1 = s_st_start[t + 1];
-      const Acc* w = reinterpret_cast<const Acc*>(s_st_w_raw) + op * kMaxStencil;
+      const StEntry<Acc>* tab = reinterpret_cast<const StEntry<Acc>*>(s_st_raw) + op * kMaxStencil;
       Acc acc = Acc(0);
 #pragma unroll 8
-      for (int k = k0; k < k1; ++k) acc = fma(w[k], (Acc)x[row + s_st_off[k]], acc);
+      for (int k = k0; k < k1; ++k) {
+        const StEntry<Acc> e = tab[k];
+        acc = fma(e.w, (Acc)x[row + e.off], acc);
+      }
       return acc;
     }
   }
@@ -365,11 +391,11 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     }
   }
   double4 red;
-  if (!grid_sum(g, (double)pb, (double)pz, 0.0, red, kPhInit)) return false;
+  if (!grid_sum<Acc>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
-  double rz = red.y;
+  Acc rz = (Acc)red.y;
   if (!isfinite(bb)) {
     flag(g, kErrNonfinite);
     return false;
@@ -385,19 +411,19 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
       q[row] = qv;
       ppq = fma(pr, (Acc)qv, ppq);
     }
-    if (!grid_sum(g, (double)ppq, 0.0, 0.0, red, kPhSpmv)) return false;
-    const double pq = red.x;
+    if (!grid_sum<Acc>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
+    const Acc pq = (Acc)red.x;
     if (!isfinite(pq)) {
       flag(g, kErrNonfinite);
       return false;
     }
-    if (!(pq > 0.0)) {
+    if (!(pq > Acc(0))) {
       flag(g, kErrBreakdown);
       its = it;
       cnt.its += it;
       return true;
     }
-    const Acc alpha = (Acc)(rz / pq);
+    const Acc alpha = rz / pq;
     Acc prr = Acc(0), prz = Acc(0);
     FOR_MY_GROUPS(g, s0, nsl) {
       TV xv[kGroup], pv[kGroup], qv[kGroup], rv[kGroup], dv[kGroup];
@@ -426,7 +452,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         }
       }
     }
-    if (!grid_sum(g, (double)prr, (double)prz, 0.0, red, kPhVec)) return false;
+    if (!grid_sum<Acc>(g, prr, prz, Acc(0), red, kPhVec)) return false;
     its = it;
     if (!isfinite(red.x)) {
       flag(g, kErrNonfinite);
@@ -436,8 +462,9 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
       cnt.its += it;
       return true;
     }
-    const Acc beta = (Acc)(red.y / rz);
-    rz = red.y;
+    const Acc rz_new = (Acc)red.y;
+    const Acc beta = rz_new / rz;
+    rz = rz_new;
     FOR_MY_GROUPS(g, s0, nsl) {
       TV dv[kGroup], rv[kGroup], pv[kGroup];
 #pragma unroll
@@ -505,7 +532,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     }
   }
   double4 red;
-  if (!grid_sum(g, (double)pb, 0.0, 0.0, red, kPhInit)) return false;
+  if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -527,7 +554,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     pg = fma(rr0, (Acc)uvv, pg);
     pd = fma((Acc)wvv, (Acc)uvv, pd);
   }
-  if (!grid_sum(g, (double)pg, (double)pd, 0.0, red, kPhSpmv)) return false;
+  if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   double gamma = red.x, delta = red.y, gamma_old = 1.0, alpha_old = 1.0;
   for (int it = 0; it < maxit; ++it) {
     if (!isfinite(gamma) || !isfinite(delta)) {
@@ -577,7 +604,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       pwd = fma(w1, u1, pwd);
       prr = fma(r1, r1, prr);
     }
-    if (!grid_sum(g, (double)prg, (double)pwd, (double)prr, red, kPhSpmv)) return false;
+    if (!grid_sum<Acc>(g, prg, pwd, prr, red, kPhSpmv)) return false;
     its = it + 1;
     if (!isfinite(red.z)) {
       flag(g, kErrNonfinite);
@@ -727,7 +754,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       a.y[f * np + row] = 0.0;
     }
   }
-  if (!grid_sum(g, pb, 0.0, 0.0, red, kPhOuter)) return;
+  if (!grid_sum<double>(g, pb, 0.0, 0.0, red, kPhOuter)) return;
   const double bnorm = sqrt(red.x);
   if (!isfinite(bnorm)) {
     flag(g, kErrNonfinite);
@@ -753,7 +780,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       V0[2 * np + row] = r2;
       pr += r0 * r0 + r1 * r1 + r2 * r2;
     }
-    if (!grid_sum(g, pr, 0.0, 0.0, red, kPhOuter)) return;
+    if (!grid_sum<double>(g, pr, 0.0, 0.0, red, kPhOuter)) return;
     const double beta = sqrt(red.x);
     if (!isfinite(beta)) {
       flag(g, kErrNonfinite);
@@ -792,7 +819,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
         w[2 * np + row] = w2;
         ph += w0 * V0[row] + w1 * V0[np + row] + w2 * V0[2 * np + row];
       }
-      if (!grid_sum(g, ph, 0.0, 0.0, red, kPhOuter)) return;
+      if (!grid_sum<double>(g, ph, 0.0, 0.0, red, kPhOuter)) return;
       double hij = red.x;
       for (int i = 0; i <= j; ++i) {
         if (threadIdx.x == 0) H[i + j * ld] = hij;
@@ -808,7 +835,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
             pn += wv * (vn ? vn[f * np + row] : wv);
           }
         }
-        if (!grid_sum(g, pn, 0.0, 0.0, red, kPhOuter)) return;
+        if (!grid_sum<double>(g, pn, 0.0, 0.0, red, kPhOuter)) return;
         hij = red.x;
       }
       const double hnext = sqrt(hij);
@@ -895,11 +922,16 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
     using Acc = typename AccOf<TV>::type;
     const int ns = __ldg(a.st_start + a.st_types);
     for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      s_st_off[k] = __ldg(a.st_off + k);
+      const int off = __ldg(a.st_off + k);
       const double wm = __ldg(a.st_wM + k), wk = __ldg(a.st_wK + k);
-      Acc* w = reinterpret_cast<Acc*>(s_st_w_raw);
+      StEntry<Acc>* tab = reinterpret_cast<StEntry<Acc>*>(s_st_raw);
 #pragma unroll
-      for (int op = 0; op < 4; ++op) w[op * kMaxStencil + k] = (Acc)(a.op_cM[op] * wm + a.op_cK[op] * wk);
+      for (int op = 0; op < 4; ++op) {
+        StEntry<Acc> e{};
+        e.off = off;
+        e.w = (Acc)(a.op_cM[op] * wm + a.op_cK[op] * wk);
+        tab[op * kMaxStencil + k] = e;
+      }
     }
     if ((int)threadIdx.x <= a.st_types) s_st_start[threadIdx.x] = __ldg(a.st_start + threadIdx.x);
     __syncthreads();

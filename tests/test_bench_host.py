@@ -27,6 +27,10 @@ def test_stage_solve_bytes_counts_pcg_iterations():
     f64 = bench.stage_solve_bytes(_St(27, 2500), n, nnz, "fp64")
     assert f64 > a
     assert bench.stage_solve_bytes(_St(0, 0), n, nnz, "fp32") == 28 * nnz + 48 * n
+    # with structured stencils only the boundary rows' nonzeros are read by inner SpMVs
+    e = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32", variant=0, inner_nnz=36846)
+    f = bench.stage_solve_bytes(_St(27, 2700), n, nnz, "fp32", variant=0, inner_nnz=36846)
+    assert (f - e) / 100 == pytest.approx(8 * 36846 + 13 * 4 * n)
 
 
 def test_aggregate_value_is_whole_job():
