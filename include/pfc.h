@@ -67,11 +67,13 @@ typedef struct {
   double step_rtol;
   double tau_max;     /* upper bound for the next time-step width */
   int blocks_per_sm;  /* persistent-kernel residency; 0 = as many as fit */
-  int pcg_variant;    /* inner CG form: 0 textbook Jacobi-PCG (3 grid barriers per
-                         iteration), 1 pipelined Jacobi-PCG of Ghysels & Vanroose
-                         (same iterates in exact arithmetic, 1 barrier per iteration),
-                         2 automatic: pipelined with float64 inner solves, textbook with
-                         float32/float16 ones (the pipelined recurrences drift there) */
+  int pcg_variant;    /* inner CG form (all give the same iterates in exact arithmetic):
+                         0 textbook Jacobi-PCG (3 grid barriers per iteration),
+                         1 pipelined Jacobi-PCG of Ghysels & Vanroose (1 barrier),
+                         3 Chronopoulos-Gear Jacobi-PCG (2 barriers),
+                         2 automatic: pipelined with float64 inner solves,
+                         Chronopoulos-Gear with float32/float16 ones (the pipelined
+                         recurrences drift there and cost outer iterations) */
   int inner_operator; /* inner matrices M, K, M + delta K, M + sqrt(delta) K in the
                          preconditioner: 0 assembled SELL-32 values with int32 column
                          indices; 1 structured stencils - on this mesh every row whose

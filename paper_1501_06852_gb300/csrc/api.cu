@@ -166,9 +166,9 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.stats = c->stats;
   a.spin_limit_ns = 2000000000ULL;
   a.barrier_extra = 0;
-  // 2 = automatic: the pipelined form in float64; the textbook form in float32/float16,
-  // where the pipelined recurrences drift and cost outer iterations
-  a.pcg_variant = c->opt.pcg_variant == 2 ? (prec == 0 ? 1 : 0) : c->opt.pcg_variant;
+  // 2 = automatic: the pipelined form in float64; the Chronopoulos-Gear form in
+  // float32/float16, where the pipelined recurrences drift and cost outer iterations
+  a.pcg_variant = c->opt.pcg_variant == 2 ? (prec == 0 ? 1 : 3) : c->opt.pcg_variant;
   a.stencil = c->opt.inner_operator == 1 ? 1 : 0;
   a.rowinfo = c->rowinfo;
   a.st_start = c->st_start;
@@ -344,7 +344,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (c->opt.restart < 1 || c->opt.restart > pfc::kMaxRestart)
     return bail(fail(c, PFC_ERR_INVALID, "restart must be in 1..40"));
   if (c->opt.precision < 0 || c->opt.precision > 2) return bail(fail(c, PFC_ERR_INVALID, "precision must be 0, 1 or 2"));
-  if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 2) return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1 or 2"));
+  if (c->opt.pcg_variant < 0 || c->opt.pcg_variant > 3)
+    return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1, 2 or 3"));
   if (c->opt.inner_operator < 0 || c->opt.inner_operator > 1)
     return bail(fail(c, PFC_ERR_INVALID, "inner_operator must be 0 or 1"));
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)

@@ -30,12 +30,13 @@
 // vector z_j, the iterate y) is only read after a barrier; everything else is
 // touched by its owner only.
 //
-// The inner CG comes in two arithmetically equivalent forms: the textbook
+// The inner CG comes in three arithmetically equivalent forms: the textbook
 // Jacobi-PCG (three barriers per iteration: after q = A p with p.q, after the
-// x/r update with r.z, after the p update), and the pipelined PCG of Ghysels and
-// Vanroose (Parallel Computing 40, 2014), which carries w = A u and m = D w as
-// extra recurrences so that one pass does the SpMV, every vector update and all
-// partial dot products, leaving one barrier per iteration.
+// x/r update with r.z, after the p update); the Chronopoulos-Gear form (two:
+// vector recurrences with r.r, then w = A u with both inner products); and the
+// pipelined PCG of Ghysels and Vanroose (Parallel Computing 40, 2014), which
+// carries w = A u and m = D w as extra recurrences so that one pass does the
+// SpMV, every vector update and all partial dot products (one barrier).
 #include <cuda_fp16.h>
 
 #include "device.cuh"
@@ -627,10 +628,145 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   return true;
 }
 
+// Chronopoulos-Gear Jacobi-PCG (Chronopoulos & Gear, J. Comput. Appl. Math. 25,
+// 1989): the same iterates as pcg_standard in exact arithmetic with two phases
+// per iteration.  It carries w = A u (u = D r) and s = A p as recurrences:
+//   phase 1: p = u + b p, s = w + b s, x += a p, r -= a s, u = D r, partial (r, r)
+//   phase 2: w = A u, partials (r, u), (w, u);  b = g'/g, a = g' / (d - b g'/a)
+template <class TM, class TV>
+__device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, int op, const TV* DI, TV* x,
+                                    RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
+  Ctx<TM, TV> c(a);
+  using Acc = typename Ctx<TM, TV>::Acc;
+  TV* r = c.vec(kVr);
+  TV* u = c.vec(kVu);
+  TV* w = c.vec(kVw);
+  TV* sv = c.vec(kVs);
+  TV* pv = c.vec(kVp);
+  const int lane = threadIdx.x & 31;
+  // r = b, u = D r, x = p = s = 0
+  Acc pb = Acc(0);
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int s = s0 + uu, row = s * 32 + lane;
+        const TV rv = (TV)rhs(g, a, s, lane, row);
+        x[row] = TV(0);
+        r[row] = rv;
+        u[row] = (TV)((Acc)DI[row] * (Acc)rv);
+        sv[row] = TV(0);
+        pv[row] = TV(0);
+        pb = fma((Acc)rv, (Acc)rv, pb);
+      }
+    }
+  }
+  double4 red;
+  if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
+  its = 0;
+  cnt.calls += 1;
+  const double bb = red.x;
+  if (!isfinite(bb)) {
+    flag(g, kErrNonfinite);
+    return false;
+  }
+  if (bb == 0.0) return true;
+  const Acc thr = (Acc)(rtol * rtol * bb);
+  // w = A u, partials (r, u), (w, u)
+  Acc pg = Acc(0), pd = Acc(0);
+  FOR_MY_SLICES(g, s) {
+    const int row = s * 32 + lane;
+    const Acc uo = (Acc)u[row], ro = (Acc)r[row];
+    const Acc wv = inner_row<Acc>(g, a, op, AV, u, s, lane);
+    w[row] = (TV)wv;
+    pg = fma(ro, uo, pg);
+    pd = fma(wv, uo, pd);
+  }
+  if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
+  Acc gam = (Acc)red.x, del = (Acc)red.y;
+  if (!(del > Acc(0))) {
+    flag(g, kErrBreakdown);
+    return true;
+  }
+  Acc alpha = gam / del, beta = Acc(0);
+  for (int it = 1; it <= maxit; ++it) {
+    // phase 1: recurrences and the new residual
+    Acc prr = Acc(0);
+    FOR_MY_GROUPS(g, s0, nsl) {
+      TV uv[kGroup], pvv[kGroup], wv[kGroup], svv[kGroup], xv[kGroup], rv[kGroup], dv[kGroup];
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          uv[uu] = u[row];
+          pvv[uu] = pv[row];
+          wv[uu] = w[row];
+          svv[uu] = sv[row];
+          xv[uu] = x[row];
+          rv[uu] = r[row];
+          dv[uu] = DI[row];
+        }
+      }
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc p1 = (Acc)uv[uu] + beta * (Acc)pvv[uu];
+          const Acc s1 = (Acc)wv[uu] + beta * (Acc)svv[uu];
+          const Acc x1 = (Acc)xv[uu] + alpha * p1;
+          const Acc r1 = (Acc)rv[uu] - alpha * s1;
+          pv[row] = (TV)p1;
+          sv[row] = (TV)s1;
+          x[row] = (TV)x1;
+          r[row] = (TV)r1;
+          u[row] = (TV)((Acc)dv[uu] * r1);
+          prr = fma(r1, r1, prr);
+        }
+      }
+    }
+    if (!grid_sum<Acc>(g, prr, Acc(0), Acc(0), red, kPhVec)) return false;
+    its = it;
+    if (!isfinite(red.x)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    if ((Acc)red.x <= thr) {
+      cnt.its += it;
+      return true;
+    }
+    // phase 2: w = A u and the two inner products
+    pg = Acc(0);
+    pd = Acc(0);
+    FOR_MY_SLICES(g, s) {
+      const int row = s * 32 + lane;
+      const Acc uo = (Acc)u[row], ro = (Acc)r[row];
+      const Acc wv = inner_row<Acc>(g, a, op, AV, u, s, lane);
+      w[row] = (TV)wv;
+      pg = fma(ro, uo, pg);
+      pd = fma(wv, uo, pd);
+    }
+    if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
+    const Acc gnew = (Acc)red.x, dnew = (Acc)red.y;
+    beta = gnew / gam;
+    const Acc den = dnew - beta * gnew / alpha;
+    if (!(den > Acc(0)) || !isfinite((double)den)) {
+      flag(g, kErrBreakdown);
+      cnt.its += it;
+      return true;
+    }
+    alpha = gnew / den;
+    gam = gnew;
+  }
+  cnt.its += maxit;
+  cnt.capped += 1;
+  return true;
+}
+
 template <class TM, class TV>
 __device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, int op, const TV* DI, TV* x,
                                     RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
+  if (c.a.pcg_variant == 3) return pcg_cg<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
   return pcg_standard<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
 }
 
