@@ -55,6 +55,9 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-outer", type=int, default=2, help="FGMRES iterations in the CPU baseline sample")
+    p.add_argument("--profile-case", action="store_true",
+                   help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
+                        "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
     return p.parse_args(argv)
 
 
@@ -288,12 +291,15 @@ def native(args, world, rank, local, pg):
     bytes_per = statistics.mean(stage_solve_bytes(st, n, nnz, args.precision, variant=variant, inner_nnz=inner_nnz)
                                 for st in stats)
     achieved = bytes_per / (solver_ms / 1e3) / 1e9
+    # DRAM traffic of this kernel from an ncu capture of the same kernel source,
+    # scaled to a full launch by its PCG iterations; null when the kernel changed since
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         try:
             tr = json.load(open(TRAFFIC_FILE))
-            if tr.get("precision") == args.precision and tr.get("workload") == w.name and tr.get("current"):
-                traffic = tr.get("bytes_per_launch")
+            if (tr.get("precision") == args.precision and tr.get("workload") == w.name
+                    and tr.get("kernel_source_sha256") == kernel_source_sha()):
+                traffic = tr["dram_bytes_per_inner_iteration"] * statistics.mean(st.inner_its for st in stats)
         except Exception:
             traffic = None
     out.update({
@@ -490,8 +496,35 @@ def reference(args, world, rank):
 OUTER_ITS_PER_SOLVE = {"2d-s512-L256": 30.0, "2d-s32-L32": 30.0, "3d-s64-L64": 30.0}
 
 
+def profile_case(args):
+    import torch
+
+    import paper_1501_06852_gb300 as pfc
+
+    w = workload(args.workload)
+    psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
+    s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol, max_outer=1)
+    x = s.init_state(psi0)
+    s.assemble(x, w.tau0)
+    b = s.stage_rhs(0, x)
+    y, st = s.stage_solve(b, check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": w.name, "precision": args.precision, "outer_its": st.outer_its,
+                      "inner_its": st.inner_its, "status": st.status}))
+    s.close()
+    return 0
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_1501_06852_gb300", "csrc", "solver.cu"), "rb").read()).hexdigest()
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_case:
+        return profile_case(args)
     world, rank, local, pg = dist_setup()
     if args.impl == "reference":
         res = reference(args, world, rank)
