@@ -200,6 +200,31 @@ pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
  * assembled values, stencil entries over all dof types}. */
 pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3);
 
+/* Step combination and embedded error estimate for callers that cannot
+ * allocate device memory: code inside a CUDA stream capture, a loop that must not
+ * touch the allocator once running, or a guest whose host application owns all
+ * device memory cannot create a context, but can combine stage increments it
+ * already holds.  (The paper has no counterpart: this is a packaging of the
+ * step combination of pfc_step.)
+ *   state_new = state + sum_j m_j y_j          (3n doubles, device, written)
+ *   *err      = RMS over the psi block [n, 2n) of e / (atol + rtol max(|psi|, |psi_new|)),
+ *               e = sum_j (mhat_j - m_j) y_j   (1 double, device, written)
+ * state: 3n doubles [mu | psi | omega]; y: the three stage increments back to
+ * back (3 x 3n doubles); all device pointers; m, mhat from Table 1.  Work is
+ * enqueued on cuda_stream (NULL = legacy default stream); nothing synchronises.
+ * Allocates nothing: the only working memory is an 8 KiB array of per-block
+ * partial sums in static device memory of the library, which every GPU that loads
+ * the library keeps until the process exits.  The first call on a device looks
+ * up that array's device address (with the device current); make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents; each call overwrites the partials it reads, so nothing needs
+ * clearing, but two calls whose kernels overlap on the GPU (different streams, or
+ * several host threads) race on it and must be serialised by the caller.
+ * Returns PFC_ERR_INVALID for n < 1, n > (2^31 - 1) / 3, null pointers or bad
+ * tolerances, PFC_ERR_CUDA if a launch fails. */
+pfc_status pfc_step_combine_static(int64_t n, const double* state, const double* y, double atol, double rtol,
+                                   double* state_new, double* err, void* cuda_stream);
+
 /* Text of the most recent error of ctx ("" if none; static text for NULL). */
 const char* pfc_last_error(const pfc_ctx* ctx);
 

@@ -67,6 +67,7 @@ def _load():
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_set_timing": (I, [P, I]),
+        "pfc_step_combine_static": (I, [ctypes.c_int64, P, P, D, D, P, P, P]),
         "pfc_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(D)]),
         "pfc_last_error": (ctypes.c_char_p, [P]),

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpfc.so")
-SOURCES = ["api.cu", "solver.cu", "kernels.cu", "host_mesh.cpp", "refelem.cpp"]
+SOURCES = ["api.cu", "solver.cu", "kernels.cu", "noalloc.cu", "host_mesh.cpp", "refelem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
