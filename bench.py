@@ -50,7 +50,12 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--precision", choices=["fp32", "fp16"], default="fp32", help="inner precision of the mixed form")
     p.add_argument("--outer-tol", type=float, default=1e-11)
-    p.add_argument("--workload", choices=["c2", "c1", "c3"], default="c2")
+    p.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
+                   help="c2 (default) the 2D 512^2 metric; c1/c3 other single instances; c4 256 batched "
+                        "instances; c5 the serving stream")
+    p.add_argument("--requests", type=int, default=2000, help="c5: number of requests")
+    p.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
+    p.add_argument("--instances", type=int, default=256, help="c4: number of instances")
     p.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,6 +68,75 @@ def parse_args(argv=None):
 
 def workload(name: str) -> synth.Workload:
     return {"c1": synth.C1_2D_SMALL, "c2": synth.C2_2D_LARGE, "c3": synth.C3_3D}[name]
+
+
+def batched(args):
+    """c4: independent 2D instances of uneven size advanced by batched steps."""
+    import torch
+
+    import paper_1501_06852_gb300 as pfc
+
+    wls = synth.batched_instances(args.instances)
+    t0 = time.perf_counter()
+    solvers, states, taus = [], [], []
+    for w in wls:
+        cap = tau_cap(w)
+        s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol,
+                          tau_max=cap)
+        solvers.append(s)
+        states.append(s.init_state(torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp,
+                                                                      w.seed)).cuda()))
+        taus.append(min(w.tau0, cap))
+    setup_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        _, _, taus, _ = pfc.batch_step(solvers, states, taus)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = []
+    ev0.record()
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        acc, errs, taus, stats = pfc.batch_step(solvers, states, taus)
+        per.append(1e3 * (time.perf_counter() - t))
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    rows = sum(s.n for s in solvers)
+    for s in solvers:
+        s.close()
+    return {"metric": "PFC stage solves/s, batched independent instances", "value": 3 * len(wls) * args.steps / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"{len(wls)} 2D instances, side log-uniform [16,256] (h=1), r~U(-0.5,-0.2), "
+                                   f"psi_mean~U(-0.4,-0.2), amp 0.1, seeds 1000+b; {rows} dofs/field in total",
+                       "launch": "one persistent cooperative launch per stage for all instances (segmented grid)"},
+            "step_ms": {"p50": pct(per, 50), "p99": pct(per, 99)}, "setup_s": setup_s}
+
+
+def serve(args):
+    """c5: Poisson stream of time-step requests through the continuous-batching server."""
+    import torch
+
+    from paper_1501_06852_gb300 import serving
+
+    reqs = synth.serving_stream(args.requests, args.rate)
+    free, total = torch.cuda.mem_get_info()
+    srv = serving.Server(budget_bytes=int(0.6 * free), precision=args.precision, outer_tol=1e-10,
+                         initial_psi=lambda w: synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed))
+    try:
+        rep = srv.run(reqs)
+    finally:
+        srv.close()
+    sm = rep.summary()
+    return {"metric": "PFC serving: p50/p99 step latency (ms) and stage solves/s", "value": sm["p99_ms"],
+            "unit": "ms (p99 step latency)", "n_gpus": 1, "steps": sm["requests"], "warmup": 0,
+            "ms_per_step": sm["mean_ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"{args.requests} requests, Poisson rate {args.rate}/s over 64 simulations "
+                                   f"(80% 2D side 32-512, 20% 3D side 16-48, log-uniform; h=1)",
+                       "budget_bytes": int(0.6 * free)},
+            "serving": sm}
 
 
 def tau_cap(w: synth.Workload) -> float:
@@ -525,6 +599,10 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_case:
         return profile_case(args)
+    if args.workload in ("c4", "c5"):
+        out = batched(args) if args.workload == "c4" else serve(args)
+        print(json.dumps(out), flush=True)
+        return 0
     world, rank, local, pg = dist_setup()
     if args.impl == "reference":
         res = reference(args, world, rank)

@@ -174,6 +174,30 @@ pfc_status pfc_apply(pfc_ctx* ctx, int op, const double* x, double* y);
 pfc_status pfc_pcg(pfc_ctx* ctx, int which, const double* b, double* x, double rtol,
                    int* iterations);
 
+/* Batched solves of independent instances (not in the paper: many simulations
+ * advanced together).  All contexts must live on the same device, share the same
+ * CUDA stream and inner precision, and appear once.  One cooperative launch (or
+ * one per wave, when there are more instances than co-resident blocks) runs every
+ * instance's FGMRES stage solve at once: the grid is split into segments, one per
+ * instance, sized by its rows, and each segment runs the solver of
+ * pfc_stage_solve with its own barriers and reductions, so an instance's result
+ * matches its single-instance solve to the solver tolerance (the block partition,
+ * hence the summation order, differs).
+ *
+ * pfc_batch_stage_solve: y[k] = (A^R_k)^{-1} b[k] for the last pfc_assemble of
+ * each context (device pointers, 3n_k doubles each); stats (may be NULL) gets
+ * count entries.  Synchronises once.
+ *
+ * pfc_batch_step: one pfc_step for every instance (states[k]: 3n_k doubles on
+ * the device, in/out; taus[k] in/out; accepted, errs (may be NULL) and stats
+ * (3 x count, may be NULL) out).  The three stages of all instances are solved by
+ * three batched launches; one host synchronisation per call.  The worst status of
+ * the instances is returned; every instance's outputs are filled. */
+pfc_status pfc_batch_stage_solve(pfc_ctx* const* ctxs, int count, const double* const* b, double* const* y,
+                                 pfc_solve_stats* stats);
+pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states, double* taus, int* accepted,
+                          double* errs, pfc_solve_stats* stats);
+
 /* Failure-detection self-test: launches a PCG whose grid barriers wait for one
  * block more than the grid holds, so every wait runs out after limit_seconds
  * (0 < limit <= 10).  The kernel sets its timeout bit and returns; the context

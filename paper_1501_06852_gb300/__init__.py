@@ -21,6 +21,7 @@ from . import build as _build
 from .build import LIB as _LIB_PATH
 
 __all__ = ["PFCSolver", "PFCError", "SolveStats", "lib", "critical_tau", "ROS3PW_GAMMA",
+           "batch_stage_solve", "batch_step",
            "OP_M", "OP_K", "OP_A01", "OP_AR", "OP_PCH", "PRECISIONS"]
 
 OP_M, OP_K, OP_A01, OP_AR, OP_PCH = 0, 1, 2, 3, 4
@@ -66,6 +67,10 @@ def _load():
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_batch_stage_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                      ctypes.POINTER(_Stats)]),
+        "pfc_batch_step": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(D), ctypes.POINTER(I),
+                               ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
         "pfc_set_timing": (I, [P, I]),
         "pfc_step_combine_static": (I, [ctypes.c_int64, P, P, D, D, P, P, P]),
         "pfc_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -130,6 +135,45 @@ def host_pattern(dim: int, side: int, length: float = 1.0) -> dict:
     if st != 0:
         raise PFCError(st, "host_pattern")
     return {"n": out[0], "nnz": out[1], "nnz_sell": out[2], "elements": out[3]}
+
+
+def _handles(solvers):
+    arr = (ctypes.c_void_p * len(solvers))()
+    for k, s in enumerate(solvers):
+        arr[k] = s._h.value
+    return arr
+
+
+def batch_stage_solve(solvers, bs):
+    """One batched launch solving A^R_k y_k = b_k for every solver (see pfc_batch_stage_solve)."""
+    if len(solvers) != len(bs) or not solvers:
+        raise ValueError("one right-hand side per solver")
+    ys = [s._new(3 * s.n) for s in solvers]
+    bp = (ctypes.c_void_p * len(bs))(*[s._vec(b, 3 * s.n, "b").value for s, b in zip(solvers, bs)])
+    yp = (ctypes.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+    stats = (_Stats * len(solvers))()
+    st = lib.pfc_batch_stage_solve(_handles(solvers), len(solvers), bp, yp, stats)
+    if st != 0:
+        raise PFCError(st, lib.pfc_last_error(solvers[0]._h).decode())
+    return ys, [SolveStats._from(x) for x in stats]
+
+
+def batch_step(solvers, states, taus, check: bool = True):
+    """One Ros3Pw step attempt for every solver in one batch (see pfc_batch_step).
+    states are updated in place where accepted.  Returns (accepted, errs, taus_next, stats[k][3])."""
+    k = len(solvers)
+    if len(states) != k or len(taus) != k or k == 0:
+        raise ValueError("one state and one tau per solver")
+    sp = (ctypes.c_void_p * k)(*[s._vec(x, 3 * s.n, "state").value for s, x in zip(solvers, states)])
+    tt = (ctypes.c_double * k)(*[float(t) for t in taus])
+    acc = (ctypes.c_int * k)()
+    errs = (ctypes.c_double * k)()
+    stats = (_Stats * (3 * k))()
+    st = lib.pfc_batch_step(_handles(solvers), k, sp, tt, acc, errs, stats)
+    if check and st != 0:
+        raise PFCError(st, lib.pfc_last_error(solvers[0]._h).decode())
+    out = [[SolveStats._from(stats[3 * i + j]) for j in range(3)] for i in range(k)]
+    return [bool(a) for a in acc], list(errs), list(tt), out
 
 
 def host_stencil(dim: int, side: int, length: float = 1.0) -> dict:

@@ -89,6 +89,11 @@ struct pfc_ctx {
   bool assembled = false;
   bool last_rejected = false;   // the previous pfc_step attempt was rejected
   double tau = 0.0, delta = 0.0;
+  // batched launches: this instance's warp slice ranges for a segment of blk_b_G blocks
+  std::vector<long long> slice_cost_prefix;   // host, nslices + 1
+  int* blk_b = nullptr;                       // device, G * W + 1
+  int* h_blk_b = nullptr;                     // pinned staging
+  int blk_b_G = 0;
   // accounting: kernels launched, persistent-solver launches and their event time
   long long launches = 0, solver_launches = 0;
   double solver_ms = 0.0;
@@ -265,6 +270,183 @@ pfc_status check_ctx(pfc_ctx* c) {
   return PFC_OK;
 }
 
+// ---------------------------------------------------------------- batches
+// Device and pinned staging buffers of batched launches (per device, grown on demand).
+struct BatchSpace {
+  char* dev = nullptr;
+  char* host = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_batch_mutex;
+BatchSpace g_batch[64];
+
+pfc_status batch_space(pfc_ctx* c, size_t need, BatchSpace*& out) {
+  BatchSpace& b = g_batch[c->device];
+  if (b.bytes < need) {
+    if (b.dev) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(b.dev);
+      cudaFreeHost(b.host);
+      b = BatchSpace{};
+    }
+    size_t bytes = std::max<size_t>(need, 1 << 16);
+    if (cudaMalloc((void**)&b.dev, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, PFC_ERR_OOM, "batch workspace allocation failed");
+    }
+    if (cudaMallocHost((void**)&b.host, bytes) != cudaSuccess) {
+      cudaFree(b.dev);
+      b = BatchSpace{};
+      return fail(c, PFC_ERR_OOM, "batch staging allocation failed");
+    }
+    b.bytes = bytes;
+  }
+  out = &b;
+  return PFC_OK;
+}
+
+// Warp slice ranges of instance c for a segment of G blocks (cost balanced as at set-up).
+pfc_status prepare_segment(pfc_ctx* c, int G) {
+  if (c->blk_b_G == G) return PFC_OK;
+  const int W = pfc::solve_threads() / 32;
+  const std::vector<long long>& pre = c->slice_cost_prefix;
+  auto split = [&](int lo, int hi, int parts, int* out) {
+    out[0] = lo;
+    int s = lo;
+    for (int k = 1; k < parts; ++k) {
+      const long long target = pre[lo] + (pre[hi] - pre[lo]) * k / parts;
+      while (s < hi && pre[s] < target) ++s;
+      out[k] = std::max(s, out[k - 1]);
+    }
+    out[parts] = hi;
+  };
+  // the staging buffer may still feed an earlier copy: wait for the stream first
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<int> bb(G + 1), wb(W + 1);
+  split(0, c->nslices, G, bb.data());
+  for (int b = 0; b < G; ++b) {
+    split(bb[b], bb[b + 1], W, wb.data());
+    for (int w = 0; w < W; ++w) c->h_blk_b[(size_t)b * W + w] = wb[w];
+  }
+  c->h_blk_b[(size_t)G * W] = c->nslices;
+  CK(cudaMemcpyAsync(c->blk_b, c->h_blk_b, sizeof(int) * ((size_t)G * W + 1), cudaMemcpyHostToDevice, c->stream));
+  c->blk_b_G = G;
+  return PFC_OK;
+}
+
+// Splits `count` instances into waves that fit one co-resident grid and gives each
+// instance a segment proportional to its rows (at least one block, at most its
+// own grid).  Returns the waves as [first, last) instance ranges with block counts.
+void plan_segments(pfc_ctx* const* ctxs, int count, int max_blocks, std::vector<int>& Gs,
+                   std::vector<std::pair<int, int>>& waves) {
+  Gs.assign(count, 1);
+  waves.clear();
+  for (int lo = 0; lo < count; lo += max_blocks) {
+    const int hi = std::min(count, lo + max_blocks);
+    long long rows = 0;
+    for (int k = lo; k < hi; ++k) rows += ctxs[k]->n_pad;
+    int spare = max_blocks - (hi - lo);
+    // proportional shares, capped by each instance's own grid, in a few rounds
+    for (int round = 0; round < 4 && spare > 0; ++round) {
+      long long w = 0;
+      for (int k = lo; k < hi; ++k)
+        if (Gs[k] < ctxs[k]->G) w += ctxs[k]->n_pad;
+      if (w == 0) break;
+      int given = 0;
+      for (int k = lo; k < hi; ++k) {
+        if (Gs[k] >= ctxs[k]->G) continue;
+        int add = (int)((long long)spare * ctxs[k]->n_pad / w);
+        add = std::min(add, ctxs[k]->G - Gs[k]);
+        Gs[k] += add;
+        given += add;
+      }
+      spare -= given;
+      if (given == 0) break;
+    }
+    (void)rows;
+    waves.emplace_back(lo, hi);
+  }
+}
+
+// Enqueues the batched FGMRES solves of stage `slot` for every instance: b = ctx->bv,
+// y = ys + slot * 3 n_pad (or tmp3 for slot 3), stats and error word in `slot`.
+pfc_status run_batch(pfc_ctx* const* ctxs, int count, int slot, bool to_tmp, BatchSpace* space, size_t region) {
+  pfc_ctx* c0 = ctxs[0];
+  pfc_ctx* c = c0;
+  int occ = 0;
+  CK(pfc::batch_occupancy(c0->prec, &occ));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+  int bps = occ;
+  if (c0->opt.blocks_per_sm > 0) bps = std::min(bps, c0->opt.blocks_per_sm);
+  const int max_blocks = std::min(sms * bps, pfc::solve_threads());
+  if (max_blocks < 1) return fail(c0, PFC_ERR_CUDA, "batched solver does not fit on an SM");
+  std::vector<int> Gs;
+  std::vector<std::pair<int, int>> waves;
+  plan_segments(ctxs, count, max_blocks, Gs, waves);
+  for (int k = 0; k < count; ++k) {
+    pfc_status st = prepare_segment(ctxs[k], Gs[k]);
+    if (st != PFC_OK) return st;
+  }
+  char* hbase = space->host + region;
+  char* dbase = space->dev + region;
+  size_t off = 0;
+  for (const auto& wv : waves) {
+    const int n = wv.second - wv.first;
+    pfc::SolveArgs* hargs = (pfc::SolveArgs*)(hbase + off);
+    int* hseg = (int*)(hbase + off + sizeof(pfc::SolveArgs) * n);
+    hseg[0] = 0;
+    for (int i = 0; i < n; ++i) {
+      pfc_ctx* ck = ctxs[wv.first + i];
+      c = ck;
+      pfc::SolveArgs a = base_args(ck, ck->prec);
+      a.mode = 0;
+      a.b = ck->bv;
+      a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)slot * 3 * ck->n_pad;
+      a.blk = ck->blk_b;
+      a.stats = ck->stats + slot;
+      a.err = ck->errw + slot;
+      hargs[i] = a;
+      hseg[i + 1] = hseg[i] + Gs[wv.first + i];
+      CK(cudaMemsetAsync(ck->arrive, 0, sizeof(unsigned), ck->stream));
+      CK(cudaMemsetAsync(ck->errw + slot, 0, sizeof(int), ck->stream));
+      CK(cudaMemsetAsync(ck->stats + slot, 0, sizeof(pfc::DevStats), ck->stream));
+    }
+    c = c0;
+    const size_t bytes = sizeof(pfc::SolveArgs) * n + sizeof(int) * (n + 1);
+    CK(cudaMemcpyAsync(dbase + off, hbase + off, bytes, cudaMemcpyHostToDevice, c0->stream));
+    pfc::BatchArgs ba;
+    ba.inst = (const pfc::SolveArgs*)(dbase + off);
+    ba.seg = (const int*)(dbase + off + sizeof(pfc::SolveArgs) * n);
+    ba.count = n;
+    CK(pfc::launch_solve_batch(c0->prec, hseg[n], ba, c0->stream));
+    c0->launches += 1;
+    c0->solver_launches += 1;
+    off += (bytes + 255) & ~size_t(255);
+  }
+  return PFC_OK;
+}
+
+size_t batch_region_bytes(int count) {
+  return ((sizeof(pfc::SolveArgs) + sizeof(int)) * (size_t)count + 256 * ((size_t)count + 2) + 255) & ~size_t(255);
+}
+
+pfc_status check_batch(pfc_ctx* const* ctxs, int count) {
+  if (!ctxs || count < 1) return PFC_ERR_INVALID;
+  for (int k = 0; k < count; ++k)
+    if (!ctxs[k]) return PFC_ERR_INVALID;
+  pfc_ctx* c = ctxs[0];
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  for (int k = 1; k < count; ++k) {
+    if (ctxs[k]->device != c->device || ctxs[k]->stream != c->stream || ctxs[k]->prec != c->prec)
+      return fail(c, PFC_ERR_INVALID, "batched contexts must share device, stream and precision");
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(c, PFC_ERR_INVALID, "a context appears twice in a batch");
+  }
+  return PFC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -413,6 +595,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
       }
       out[parts] = hi;
     };
+    c->slice_cost_prefix = pre;
     std::vector<int> bb(c->G + 1);
     split(0, S.nslices, c->G, bb.data());
     for (int b = 0; b < c->G; ++b) {
@@ -437,6 +620,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_dptr = L.take(sizeof(int) * S.dof_ptr.size());
   const size_t o_didx = L.take(sizeof(int) * std::max<size_t>(1, S.dof_idx.size()));
   const size_t o_blk = L.take(sizeof(int) * blk.size());
+  const size_t o_blkb = L.take(sizeof(int) * blk.size());
   const size_t o_ri = L.take(S.rowinfo.size());
   const size_t o_sts = L.take(sizeof(int) * std::max<size_t>(1, S.st_start.size()));
   const size_t o_sto = L.take(sizeof(int) * std::max<size_t>(1, S.st_off.size()));
@@ -495,6 +679,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->dptr = (int*)(A + o_dptr);
   c->didx = (int*)(A + o_didx);
   c->blk = (int*)(A + o_blk);
+  c->blk_b = (int*)(A + o_blkb);
   c->rowinfo = (unsigned char*)(A + o_ri);
   c->st_start = (int*)(A + o_sts);
   c->st_off = (int*)(A + o_sto);
@@ -540,10 +725,12 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);
   {
-    cudaError_t e = cudaMallocHost((void**)&c->h_stats, sizeof(pfc::DevStats) * 4 + sizeof(double) * 2 + sizeof(int) * 8);
+    cudaError_t e = cudaMallocHost((void**)&c->h_stats, sizeof(pfc::DevStats) * 4 + sizeof(double) * 2 + sizeof(int) * 8 +
+                                                         sizeof(int) * blk.size());
     if (e != cudaSuccess) return bail(fail(c, PFC_ERR_OOM, "cudaMallocHost failed"));
     c->h_err = (double*)(c->h_stats + 4);
     c->h_errw = (int*)(c->h_err + 2);
+    c->h_blk_b = c->h_errw + 8;
   }
 
   for (int k = 0; k < 4; ++k)
@@ -829,6 +1016,127 @@ pfc_status pfc_selftest_barrier_timeout(pfc_ctx* c, double limit_seconds) {
   CK(cudaStreamSynchronize(c->stream));
   harvest(c);
   return status_from_err(c->h_errw[0]);
+}
+
+pfc_status pfc_batch_stage_solve(pfc_ctx* const* ctxs, int count, const double* const* b, double* const* y,
+                                 pfc_solve_stats* stats) {
+  pfc_status st = check_batch(ctxs, count);
+  if (st != PFC_OK) return st;
+  pfc_ctx* c = ctxs[0];
+  if (!b || !y) return fail(c, PFC_ERR_INVALID, "null vector array");
+  for (int k = 0; k < count; ++k) {
+    if (!ctxs[k]->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first for every context");
+    if (!b[k] || !y[k]) return fail(c, PFC_ERR_INVALID, "null vector");
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  BatchSpace* space = nullptr;
+  st = batch_space(c, batch_region_bytes(count), space);
+  if (st != PFC_OK) return st;
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    LAUNCH(pfc::launch_gather_in(ck->n, ck->n_pad, 3, ck->perm, b[k], ck->bv, ck->stream));
+  }
+  st = run_batch(ctxs, count, 0, true, space, 0);
+  if (st != PFC_OK) return st;
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    LAUNCH(pfc::launch_scatter_out(ck->n, ck->n_pad, 3, ck->perm, ck->tmp3, y[k], ck->stream));
+    CK(cudaMemcpyAsync(ck->h_stats, ck->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, ck->stream));
+    CK(cudaMemcpyAsync(ck->h_errw, ck->errw, sizeof(int), cudaMemcpyDeviceToHost, ck->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  pfc_status worst = PFC_OK;
+  for (int k = 0; k < count; ++k) {
+    fill_stats(ctxs[k]->h_stats[0], ctxs[k]->h_errw[0], stats ? stats + k : nullptr);
+    pfc_status sk = status_from_err(ctxs[k]->h_errw[0]);
+    if (sk != PFC_OK && worst == PFC_OK) worst = sk;
+  }
+  if (worst != PFC_OK) return fail(c, worst, "a batched stage solve failed");
+  return PFC_OK;
+}
+
+pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states, double* taus, int* accepted,
+                          double* errs, pfc_solve_stats* stats) {
+  pfc_status st = check_batch(ctxs, count);
+  if (st != PFC_OK) return st;
+  pfc_ctx* c = ctxs[0];
+  if (!states || !taus) return fail(c, PFC_ERR_INVALID, "null argument");
+  for (int k = 0; k < count; ++k)
+    if (!states[k] || !(taus[k] > 0.0) || !std::isfinite(taus[k])) return fail(c, PFC_ERR_INVALID, "bad step arguments");
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  BatchSpace* space = nullptr;
+  const size_t region = batch_region_bytes(count);
+  st = batch_space(c, 3 * region, space);
+  if (st != PFC_OK) return st;
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    c = ck;
+    LAUNCH(pfc::launch_gather_in(ck->n, ck->n_pad, 3, ck->perm, states[k], ck->xk, ck->stream));
+    st = assemble_internal(ck, taus[k]);
+    if (st != PFC_OK) return st;
+  }
+  c = ctxs[0];
+  for (int i = 0; i < 3; ++i) {
+    for (int k = 0; k < count; ++k) {
+      pfc_ctx* ck = ctxs[k];
+      c = ck;
+      const int np = ck->n_pad;
+      const size_t np3 = 3 * (size_t)np;
+      LAUNCH(pfc::launch_stage_combine(np, ck->xk, ck->ys, ck->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1],
+                                       ck->xi, ck->dvec, ck->stream));
+      LAUNCH(pfc::launch_elem_load(ck->dim, ck->E, ck->elem, ck->xi + np, ck->vol, ck->ebuf, ck->stream));
+      LAUNCH(pfc::launch_rhs(ck->nslices, ck->slice_ptr, ck->cols, ck->Mv, ck->Kv, ck->dptr, ck->didx, ck->ebuf, ck->xi,
+                             i > 0 ? ck->dvec : nullptr, ck->opt.r, ck->tau, ck->bv, ck->stream));
+    }
+    c = ctxs[0];
+    st = run_batch(ctxs, count, i, false, space, (size_t)i * region);
+    if (st != PFC_OK) return st;
+  }
+  double e[3];
+  for (int j = 0; j < 3; ++j) e[j] = kMhat[j] - kM[j];
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    c = ck;
+    const int np = ck->n_pad;
+    const size_t np3 = 3 * (size_t)np;
+    LAUNCH(pfc::launch_step_combine(np, ck->xk, ck->ys, ck->ys + np3, ck->ys + 2 * np3, kM, e, ck->opt.step_atol,
+                                    ck->opt.step_rtol, ck->xnew, ck->step_part, pfc::step_partials(), ck->stream));
+    LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), ck->step_part, 1.0 / ck->n, ck->err_scalar, ck->stream));
+    CK(cudaMemcpyAsync(ck->h_stats, ck->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, ck->stream));
+    CK(cudaMemcpyAsync(ck->h_errw, ck->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, ck->stream));
+    CK(cudaMemcpyAsync(ck->h_err, ck->err_scalar, sizeof(double), cudaMemcpyDeviceToHost, ck->stream));
+  }
+  c = ctxs[0];
+  CK(cudaStreamSynchronize(c->stream));
+  pfc_status worst = PFC_OK;
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    c = ck;
+    int werr = 0;
+    for (int i = 0; i < 3; ++i) {
+      fill_stats(ck->h_stats[i], ck->h_errw[i], stats ? stats + 3 * k + i : nullptr);
+      werr |= ck->h_errw[i];
+    }
+    const double ev = ck->h_err[0];
+    if (errs) errs[k] = ev;
+    pfc_status sk = status_from_err(werr);
+    if (sk == PFC_ERR_TIMEOUT || sk == PFC_ERR_NONFINITE || !std::isfinite(ev)) {
+      if (accepted) accepted[k] = 0;
+      if (worst == PFC_OK) worst = sk == PFC_OK ? PFC_ERR_NONFINITE : sk;
+      continue;
+    }
+    const bool acc = ev <= 1.0 && sk == PFC_OK;
+    if (accepted) accepted[k] = acc ? 1 : 0;
+    if (acc) LAUNCH(pfc::launch_scatter_out(ck->n, ck->n_pad, 3, ck->perm, ck->xnew, states[k], ck->stream));
+    double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
+    if (acc && ck->last_rejected) fac = std::min(fac, 1.0);
+    ck->last_rejected = !acc;
+    taus[k] = std::min(taus[k] * fac, ck->opt.tau_max);
+    if (sk != PFC_OK && worst == PFC_OK) worst = sk;
+  }
+  c = ctxs[0];
+  if (worst != PFC_OK) return fail(c, worst, "a batched step failed");
+  return PFC_OK;
 }
 
 pfc_status pfc_set_timing(pfc_ctx* c, int enable) {

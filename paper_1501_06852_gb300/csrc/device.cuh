@@ -76,6 +76,14 @@ struct SolveArgs {
   double op_cM[4];         //   weights op_cM[op] * wM + op_cK[op] * wK
 };
 
+// A batched launch: instance k (arguments inst[k], in device memory) owns the
+// blocks seg[k] .. seg[k+1]-1 of the grid.
+struct BatchArgs {
+  const SolveArgs* inst;
+  const int* seg;
+  int count;
+};
+
 constexpr int kMaxStencil = 640;   // stencil entries over all dof types
 enum : int { kOpM = 0, kOpK = 1, kOpMdK = 2, kOpMsK = 3 };
 

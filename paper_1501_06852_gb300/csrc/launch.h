@@ -12,6 +12,8 @@ int solve_threads();
 int solve_ring();
 cudaError_t solve_occupancy(int prec, int* blocks_per_sm);
 cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t stream);
+cudaError_t batch_occupancy(int prec, int* blocks_per_sm);
+cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream);
 
 // element and vector kernels (kernels.cu)
 cudaError_t upload_quartic(int dim, const double* unit_quartic, int npairs);

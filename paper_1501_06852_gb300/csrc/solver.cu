@@ -79,6 +79,7 @@ struct Grid {
   int expect;      // blocks that arrive at each barrier (G, or more in the timeout self-test)
   unsigned epoch;  // thread 0 only
   int ring;
+  int bid;         // block index inside this solve's grid (its segment in a batched launch)
   int w_lo, w_hi;  // this warp's contiguous slice range (cost balanced on the host)
   int sp_lane;     // slice_ptr[w_lo + lane] (valid when the range has at most 31 slices)
   bool sp_reg;     // the slice pointers of this warp live in sp_lane
@@ -198,7 +199,7 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
     ty = warp_sum(ty);
     tz = warp_sum(tz);
     if (l == 0) {
-      double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + blockIdx.x);
+      double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + g.bid);
       __stcg(dst, make_double2((double)tx, (double)ty));
       __stcg(dst + 1, make_double2((double)tz, 0.0));
     }
@@ -240,7 +241,7 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
 }
 
 __device__ __forceinline__ void flag(Grid& g, int bit) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(g.err, bit);
+  if (threadIdx.x == 0 && g.bid == 0) atomicOr(g.err, bit);
 }
 
 // One SELL-32 row (lane = row of slice s) times x, loading CH column indices and
@@ -854,7 +855,7 @@ __device__ __forceinline__ void block_row(const SolveArgs& a, const double* z, i
 
 __device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts, const InnerCount& cnt, double rel,
                             double bnorm, int last_its) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g.bid == 0 && threadIdx.x == 0) {
     DevStats st;
     st.outer_its = outer;
     st.restarts = restarts;
@@ -1030,26 +1031,29 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   }
 }
 
+// One solve (FGMRES stage solve, one P_CH application or one PCG solve) run by
+// the G blocks bid = 0..G-1 of a grid or of a segment of a batched grid.
 template <class TM, class TV>
-__global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(const __grid_constant__ SolveArgs a) {
+__device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
   Grid g;
   g.arrive = a.arrive;
   g.err = a.err;
   g.part = a.part;
-  g.G = gridDim.x;
-  g.expect = gridDim.x + a.barrier_extra;
+  g.bid = bid;
+  g.G = G;
+  g.expect = G + a.barrier_extra;
   g.limit_ns = a.spin_limit_ns;
   g.epoch = 0;
   g.ring = 0;
   {
-    const int wi = blockIdx.x * kWarps + (int)(threadIdx.x >> 5);
+    const int wi = bid * kWarps + (int)(threadIdx.x >> 5);
     g.w_lo = __ldg(a.blk + wi);
     g.w_hi = __ldg(a.blk + wi + 1);
     g.sp_reg = (g.w_hi - g.w_lo) <= 31;
     const int k = g.w_lo + (int)(threadIdx.x & 31);
     g.sp_lane = (g.sp_reg && k <= g.w_hi) ? __ldg(a.slice_ptr + k) : 0;
   }
-  g.prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
+  g.prof = a.prof && bid == 0 && threadIdx.x == 0;
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) s_prof[k] = 0;
     s_t_last = global_ns();
@@ -1098,14 +1102,34 @@ __global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(c
 }
 
 template <class TM, class TV>
-const void* kernel_ptr() {
-  return (const void*)solve_kernel<TM, TV>;
+__global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_kernel(const __grid_constant__ SolveArgs a) {
+  solve_body<TM, TV>(a, blockIdx.x, gridDim.x);
 }
 
-const void* kernel_for(int prec) {
-  if (prec == 0) return kernel_ptr<double, double>();
-  if (prec == 1) return kernel_ptr<float, float>();
-  return kernel_ptr<__half, float>();
+// Batched launch: instance k owns the blocks seg[k] .. seg[k+1]-1 of the grid and
+// solves its own stage system with them (its own barrier counter, partial sums,
+// error word and statistics).  Segments never wait for one another.
+template <class TM, class TV>
+__global__ void __launch_bounds__(kThreads, PFC_SOLVER_MINBLOCKS) solve_batch_kernel(const __grid_constant__ BatchArgs b) {
+  int lo = 0, hi = b.count;  // find k with seg[k] <= blockIdx.x < seg[k+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(b.seg + mid) <= (int)blockIdx.x) lo = mid;
+    else hi = mid;
+  }
+  const int s0 = __ldg(b.seg + lo), s1 = __ldg(b.seg + lo + 1);
+  solve_body<TM, TV>(b.inst[lo], (int)blockIdx.x - s0, s1 - s0);
+}
+
+template <class TM, class TV>
+const void* kernel_ptr(bool batch) {
+  return batch ? (const void*)solve_batch_kernel<TM, TV> : (const void*)solve_kernel<TM, TV>;
+}
+
+const void* kernel_for(int prec, bool batch = false) {
+  if (prec == 0) return kernel_ptr<double, double>(batch);
+  if (prec == 1) return kernel_ptr<float, float>(batch);
+  return kernel_ptr<__half, float>(batch);
 }
 
 }  // namespace
@@ -1121,6 +1145,16 @@ cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t
   SolveArgs local = args;
   void* params[] = {&local};
   return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, 0, stream);
+}
+
+cudaError_t batch_occupancy(int prec, int* blocks_per_sm) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(prec, true), kThreads, 0);
+}
+
+cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream) {
+  BatchArgs local = args;
+  void* params[] = {&local};
+  return cudaLaunchCooperativeKernel(kernel_for(prec, true), dim3(grid), dim3(kThreads), params, 0, stream);
 }
 
 }  // namespace pfc
