@@ -53,8 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5"], default="c2",
                    help="c2 (default) the 2D 512^2 metric; c1/c3 other single instances; c4 256 batched "
                         "instances; c5 the serving stream")
-    p.add_argument("--requests", type=int, default=2000, help="c5: number of requests")
-    p.add_argument("--rate", type=float, default=20.0, help="c5: Poisson arrival rate (requests/s)")
+    p.add_argument("--requests", type=int, default=300, help="c5: number of requests")
+    p.add_argument("--rate", type=float, default=3.0, help="c5: Poisson arrival rate (requests/s)")
     p.add_argument("--instances", type=int, default=256, help="c4: number of instances")
     p.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     p.add_argument("--no-e2e", action="store_true")
