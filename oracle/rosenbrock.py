@@ -234,3 +234,29 @@ def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = S
     if accepted and prev_rejected:
         tau_next = min(tau_next, tau)
     return StepResult(x_new if accepted else x_k.copy(), accepted, err, tau_next, ys, rhs, stats)
+
+
+# --- linearised semi-implicit Euler (Section 3, Eq. 3.3-3.4) -----------------------
+def euler_matrix(prob: PFCProblem, psi_k: np.ndarray, tau: float) -> sp.csr_matrix:
+    """A of the linearised semi-implicit Euler step for PFC2 (K_+ = K):
+    [[M, -(1+r) M + N(psi_k) + 2 K, K], [tau K, M, 0], [0, K, M]]."""
+    M, K = prob.M, prob.K
+    return sp.bmat([[M, prob.a01(psi_k), K], [tau * K, M, None], [None, K, M]], format="csr")
+
+
+def euler_rhs(prob: PFCProblem, psi_k: np.ndarray) -> np.ndarray:
+    """b0 = (-2 psi_k^3, phi), b1 = M psi_k, b2 = 0."""
+    n = prob.n
+    return np.concatenate([-2.0 * assembly.load_cubed(prob.mesh, psi_k, prob.ref), prob.M @ psi_k, np.zeros(n)])
+
+
+def euler_step(prob: PFCProblem, x_k: np.ndarray, tau: float, tol: float = 1e-13, inner: str = "pcg",
+               restart: int = 30, max_outer: int = 2000):
+    """x_{k+1} = A^{-1} b by FGMRES(restart) with P_CH built for gamma = 1 (Section 4)."""
+    psi_k = prob.split(x_k)[1]
+    A = euler_matrix(prob, psi_k, tau)
+    b = euler_rhs(prob, psi_k)
+    pc = PCH(prob.M, prob.K, tau, 1.0, inner=inner)
+    x, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
+    st.inner = pc.log
+    return x, st
