@@ -59,7 +59,7 @@ typedef struct {
   double r;           /* model parameter r of Eq. (2.1) */
   double outer_tol;   /* FGMRES stop: ||b - A^R y||_2 <= outer_tol ||b||_2 */
   double inner_rtol;  /* PCG stop: ||r||_2 <= inner_rtol ||rhs||_2 (Table 2: 1e-3) */
-  int restart;        /* FGMRES restart length (Section 6: 30); 1..40 */
+  int restart;        /* FGMRES restart length (Section 7: 30); 1..40 */
   int max_outer;      /* cap on FGMRES iterations per stage solve */
   int max_inner;      /* cap on PCG iterations per inner solve */
   int precision;      /* pfc_precision */
@@ -117,13 +117,13 @@ size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt);
 
 /* Per-step assembly at the state x^k (3n, device): the (mu, psi) block
  * A01 = -(1+r) M + 2 K + N(psi^k), N(psi)_ij = (-3 psi^2 phi_j, phi_i)
- * (Eq. 3.12 with K_+ = K, F = 0 for PFC2), and for the step width tau the
+ * (Eq. 3.10 with K_+ = K, F = 0 for PFC2), and for the step width tau the
  * inner matrices M + delta K and M + sqrt(delta) K with delta = sqrt(gamma tau)
  * and their Jacobi diagonals (Section 4, Table 2).  Must precede the stage
  * calls; the matrices stay until the next pfc_assemble. */
 pfc_status pfc_assemble(pfc_ctx* ctx, const double* state, double tau);
 
-/* Right-hand side b_i^R of Eq. (3.12) for stage i = nprev (0, 1 or 2) at the
+/* Right-hand side b_i^R of Eq. (3.10) for stage i = nprev (0, 1 or 2) at the
  * stage value x_i (3n, device):
  *   b0 = -M mu_i + (1+r) M psi_i - 2 K psi_i - K omega_i + (psi_i^3, phi)
  *   b1 = -tau K mu_i + sum_{j<i} c_ij M dpsi_j
@@ -134,9 +134,9 @@ pfc_status pfc_assemble(pfc_ctx* ctx, const double* state, double tau);
 pfc_status pfc_stage_rhs(pfc_ctx* ctx, int nprev, const double* x_stage,
                          const double* y_prev, double* b);
 
-/* Solves A^R y = b (Eq. 3.12) for the last assembled psi^k and tau with
+/* Solves A^R y = b (Eq. 3.10) for the last assembled psi^k and tau with
  * FGMRES(restart), modified Gram-Schmidt and right preconditioner P_CH
- * (Sections 4 and 6), zero initial guess.  b, y: 3n doubles on the device.
+ * (Sections 4 and 7), zero initial guess.  b, y: 3n doubles on the device.
  * Synchronises the stream to fill *stats (may be NULL).  Returns
  * PFC_ERR_NOT_CONVERGED with the last iterate in y when max_outer is hit. */
 pfc_status pfc_stage_solve(pfc_ctx* ctx, const double* b, double* y,
@@ -153,6 +153,18 @@ pfc_status pfc_stage_solve(pfc_ctx* ctx, const double* b, double* y,
  * synchronisation per call. */
 pfc_status pfc_step(pfc_ctx* ctx, double* state, double* tau, int* accepted,
                     double* err, pfc_solve_stats* stats);
+
+/* One step of the linearised semi-implicit Euler scheme (Section 3, Eq. 3.3-3.4,
+ * PFC2 with K_+ = K): with psi_k from state (3n, device, in/out) and tau_k = tau,
+ * assembles A = [[M, -(1+r) M + N(psi_k) + 2 K, K], [tau K, M, 0], [0, K, M]] and
+ * b = [(-2 psi_k^3, phi) | M psi_k | 0], solves A x = b with the stage solver
+ * (FGMRES(restart) + MGS, P_CH with gamma = 1, zero initial guess) and, when the
+ * solve converges, overwrites state with x = [mu | psi | omega]_{k+1}.  On any
+ * error state is left unchanged.  Afterwards pfc_apply and pfc_stage_solve use
+ * this Euler matrix until the next pfc_assemble or pfc_step.  *stats (may be
+ * NULL) receives the solve's statistics.  One host synchronisation per call. */
+pfc_status pfc_euler_step(pfc_ctx* ctx, double* state, double tau,
+                          pfc_solve_stats* stats);
 
 /* Consistent initial state from psi0 (n doubles, device): solves
  * M omega0 = -K psi0 and M mu0 = (psi0^3, phi) + (1+r) M psi0 - 2 K psi0 - K omega0

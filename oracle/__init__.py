@@ -11,14 +11,14 @@ Modules (each function cites the paper's section or equation it follows):
 
 * ``quadrature`` - Gauss-Jacobi rules (Golub-Welsch) and collapsed simplex rules.
 * ``p2``         - P2 Lagrange basis on the reference simplex (Section 3).
-* ``mesh``       - structured simplicial meshes and the P2 dof lattice (Section 3, Section 6).
+* ``mesh``       - structured simplicial meshes and the P2 dof lattice (Section 3, Section 7).
 * ``assembly``   - M, K, N(psi) and the load vector (psi^3, phi) (Section 3, Eq. 3.4).
 * ``solvers``    - Jacobi-PCG, FGMRES(30) with modified Gram-Schmidt, and the
                    block preconditioner with the Cahn-Hilliard Schur approximation
-                   (Sections 4, 4.2, 6 and Table 2).
+                   (Sections 4, 4.2, 7 and Table 2).
 * ``rosenbrock`` - Ros3Pw stages, stage matrix A^R and right-hand side, step
                    combination and embedded step-size control (Section 3.1, Table 1).
-* ``analysis``   - closed forms of the spectral analysis (Section 5: Lemma 2,
+* ``analysis``   - closed forms of the spectral analysis (Section 6: Lemma 2,
                    Lemma 3, symbol eigenvalues).
 
 Readings taken where the paper is silent or garbled are listed where they are

@@ -1,4 +1,4 @@
-"""Closed forms of the paper's spectral analysis (Section 5).
+"""Closed forms of the paper's spectral analysis (Section 6).
 
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 """
@@ -19,19 +19,19 @@ def critical_tau(r: float, psi_bar: float = 0.0) -> float:
 
 
 def symbol_A0(k2: float, tau: float, r: float, psi_bar: float = 0.0) -> float:
-    """Stabilised symbol (Eq. 5.8): 1 + tau[(3 psi_bar^2 + 1 + r) k^2 - 2 k^4 + k^6]."""
+    """Stabilised symbol (Eq. 6.6): 1 + tau[(3 psi_bar^2 + 1 + r) k^2 - 2 k^4 + k^6]."""
     return 1.0 + tau * ((3.0 * psi_bar ** 2 + 1.0 + r) * k2 - 2.0 * k2 ** 2 + k2 ** 3)
 
 
 def q_eigenvalue(k2: float, tau: float, r: float, psi_bar: float = 0.0) -> float:
-    """Third eigenvalue of Q = A P^{-1} (Eq. 5.10)."""
+    """Third eigenvalue of Q = A P^{-1} (Eq. 6.8)."""
     st = math.sqrt(tau)
     den = tau * k2 ** 3 + (st - 2.0 * tau) * k2 ** 2 - st * k2 + 1.0
     return symbol_A0(k2, tau, r, psi_bar) / den
 
 
 def qch_eigenvalue(k2: float, tau: float, r: float, psi_bar: float = 0.0) -> float:
-    """Third eigenvalue of Q_CH = A P_CH^{-1} (Eq. 5.11)."""
+    """Third eigenvalue of Q_CH = A P_CH^{-1} (Eq. 6.9)."""
     den = tau * k2 ** 3 + (math.sqrt(tau) + 2.0 * tau ** 0.75) * k2 ** 2 \
         + (math.sqrt(tau) + 2.0 * tau ** 0.25) * k2 + 1.0
     return symbol_A0(k2, tau, r, psi_bar) / den
@@ -50,6 +50,6 @@ def lemma2_bounds(delta: float) -> tuple[float, float]:
 
 
 def interval_convergence_factor(alpha: float, beta: float) -> float:
-    """Eq. (4.7): rho = (sqrt(kappa) - 1)/(sqrt(kappa) + 1), kappa = beta/alpha."""
+    """Eq. (5.8): rho = (sqrt(kappa) - 1)/(sqrt(kappa) + 1), kappa = beta/alpha."""
     k = beta / alpha
     return (math.sqrt(k) - 1.0) / (math.sqrt(k) + 1.0)

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
 The paper works on conforming simplicial meshes and uses regular simplicial
-meshes of a square/cube in its experiments (Section 3, Section 6).  The meshes
+meshes of a square/cube in its experiments (Section 3, Section 7).  The meshes
 here are:
 
 * 2D: ``side x side`` squares of width h = L/side; square (i, j) is cut along the

@@ -10,7 +10,7 @@ Section 3.1 writes the Rosenbrock scheme in its modified form (Eq. 3.6, 3.7):
 
 with MM = diag(0, 1, 0) for x = (mu, psi, omega).  For the PFC2 model (H^{-1}
 gradient flow, Eq. 2.2) the mobility is 1, so K_+ = K and F(mu) = 0, and the
-stage system is Eq. (3.12):
+stage system is Eq. (3.10):
 
     A^R = [[M, -(1+r) M + 2 K + N(psi_k), K],
            [tau K, M / gamma, 0],
@@ -116,7 +116,7 @@ class PFCProblem:
         n = self.n
         return x[:n], x[n:2 * n], x[2 * n:]
 
-    # --- Eq. (3.12) -------------------------------------------------------
+    # --- Eq. (3.10) -------------------------------------------------------
     def a01(self, psi_k: np.ndarray) -> sp.csr_matrix:
         N = assembly.nonlinear_mass(self.mesh, psi_k, self.ref)
         return (-(1.0 + self.r) * self.M + 2.0 * self.K + N).tocsr()
@@ -128,7 +128,7 @@ class PFCProblem:
                         [None, K, M]], format="csr")
 
     def stage_rhs(self, x_i: np.ndarray, dpsi_prev: list, c_row: list, tau: float) -> np.ndarray:
-        """b_i^R of Eq. (3.12) for stage value x_i and previous increments dpsi_j with weights c_ij."""
+        """b_i^R of Eq. (3.10) for stage value x_i and previous increments dpsi_j with weights c_ij."""
         M, K, r = self.M, self.K, self.r
         mu, psi, om = self.split(x_i)
         b0 = -(M @ mu) + (1.0 + r) * (M @ psi) - 2.0 * (K @ psi) - K @ om \
@@ -139,7 +139,7 @@ class PFCProblem:
         b2 = -(M @ om) - K @ psi
         return np.concatenate([b0, b1, b2])
 
-    # --- stage solve (Section 4, Section 6) --------------------------------
+    # --- stage solve (Section 4, Section 7) --------------------------------
     def stage_solve(self, A: sp.csr_matrix, b: np.ndarray, tau: float, tol: float = 1e-13,
                     inner: str = "pcg", restart: int = 30, max_outer: int = 2000, coef: Ros3Pw = ROS3PW):
         pc = PCH(self.M, self.K, tau, coef.gamma, inner=inner)

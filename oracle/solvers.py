@@ -3,12 +3,12 @@
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
 * ``pcg_jacobi``  - conjugate gradients with the diagonal (Jacobi) preconditioner,
-  the inner solver of every preconditioner step (Section 6, Table 2: "PCG",
+  the inner solver of every preconditioner step (Section 7, Table 2: "PCG",
   preconditioner "diag", relative tolerance 1e-3).  Reading: zero start,
   stop when the unpreconditioned residual satisfies ||r||_2 <= rtol ||b||_2.
 * ``fgmres``      - flexible GMRES with right preconditioning (Section 4: the
   system A P^{-1} (P x) = b; Saad 1993), restart 30 and modified Gram-Schmidt
-  (Section 6).  Reading: zero initial guess; Givens rotations on the Hessenberg
+  (Section 7).  Reading: zero initial guess; Givens rotations on the Hessenberg
   matrix; after each cycle the true residual b - A x is recomputed and the
   solve stops once ||b - A x||_2 <= tol ||b||_2.
 * ``PCH``         - the block preconditioner of Eq. (4.1) with the Cahn-Hilliard

@@ -61,6 +61,7 @@ def _load():
         "pfc_stage_rhs": (I, [P, I, P, P, P]),
         "pfc_stage_solve": (I, [P, P, P, ctypes.POINTER(_Stats)]),
         "pfc_step": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
+        "pfc_euler_step": (I, [P, P, D, ctypes.POINTER(_Stats)]),
         "pfc_init_state": (I, [P, P, P]),
         "pfc_apply": (I, [P, I, P, P]),
         "pfc_pcg": (I, [P, I, P, P, D, ctypes.POINTER(I)]),
@@ -278,6 +279,15 @@ class PFCSolver:
         if check:
             self._check(st)
         return bool(acc.value), err.value, t.value, [SolveStats._from(s) for s in stats]
+
+    def euler_step(self, state, tau: float, check: bool = True) -> "SolveStats":
+        """One linearised semi-implicit Euler step (Eq. 3.4) with step width tau; state
+        (device, 3n) is overwritten with x_{k+1} when the solve succeeds."""
+        stats = _Stats()
+        st = lib.pfc_euler_step(self._h, self._vec(state, 3 * self.n, "state"), float(tau), ctypes.byref(stats))
+        if check:
+            self._check(st)
+        return SolveStats._from(stats)
 
     def apply(self, op: int, x):
         m = 3 * self.n if op in (OP_AR, OP_PCH) else self.n

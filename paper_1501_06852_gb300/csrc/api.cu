@@ -89,6 +89,7 @@ struct pfc_ctx {
   bool assembled = false;
   bool last_rejected = false;   // the previous pfc_step attempt was rejected
   double tau = 0.0, delta = 0.0;
+  double gamma = kGamma;        // scaling of the (1,1) block: Ros3Pw gamma, or 1 for the Euler system
   // batched launches: this instance's warp slice ranges for a segment of blk_b_G blocks
   std::vector<long long> slice_cost_prefix;   // host, nslices + 1
   int* blk_b = nullptr;                       // device, G * W + 1
@@ -153,9 +154,9 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
     a.dMsK = c->fdMsK;
   }
   a.tau = c->tau;
-  a.gamma = kGamma;
-  a.inv_gamma = 1.0 / kGamma;
-  a.tau_e = kGamma * c->tau;
+  a.gamma = c->gamma;
+  a.inv_gamma = 1.0 / c->gamma;
+  a.tau_e = c->gamma * c->tau;
   a.inv_delta = c->delta > 0 ? 1.0 / c->delta : 0.0;
   a.tol = c->opt.outer_tol;
   a.inner_rtol = c->opt.inner_rtol;
@@ -248,12 +249,13 @@ pfc_status stage_rhs_internal(pfc_ctx* c, int nprev) {
   return PFC_OK;
 }
 
-pfc_status assemble_internal(pfc_ctx* c, double tau) {
+pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma) {
   const int np = c->n_pad;
   LAUNCH(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
   c->tau = tau;
-  c->delta = std::sqrt(kGamma * tau);
+  c->gamma = gamma;
+  c->delta = std::sqrt(gamma * tau);
   const double sdelta = std::sqrt(c->delta);
   LAUNCH(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
                             c->stream));
@@ -896,6 +898,36 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   return PFC_OK;
 }
 
+pfc_status pfc_euler_step(pfc_ctx* c, double* state, double tau, pfc_solve_stats* stats) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "bad euler step arguments");
+  const int np = c->n_pad;
+  LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
+  // A of Eq. (3.4): the stage matrix with gamma = 1, A01 = -(1+r) M + N(psi_k) + 2 K
+  st = assemble_internal(c, tau, 1.0);
+  if (st != PFC_OK) return st;
+  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_euler_rhs(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->dptr, c->didx, c->ebuf, c->xk + np,
+                               c->bv, c->stream));
+  pfc::SolveArgs a = base_args(c, c->prec);
+  a.mode = 0;
+  a.b = c->bv;
+  a.y = c->xnew;
+  st = run_solver(c, a, c->prec, 0);
+  if (st != PFC_OK) return st;
+  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
+  fill_stats(c->h_stats[0], c->h_errw[0], stats);
+  st = status_from_err(c->h_errw[0]);
+  if (st != PFC_OK) return fail(c, st, std::string("euler step: ") + pfc_status_string(st));
+  LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PFC_OK;
+}
+
 pfc_status pfc_init_state(pfc_ctx* c, const double* psi0, double* state) {
   pfc_status st = check_ctx(c);
   if (st != PFC_OK) return st;
@@ -948,7 +980,7 @@ pfc_status pfc_apply(pfc_ctx* c, int op, const double* x, double* y) {
     LAUNCH(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_AR) {
     LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
-    LAUNCH(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / kGamma, c->tmp3,
+    LAUNCH(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / c->gamma, c->tmp3,
                            c->xnew, c->stream));
     LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_PCH) {

@@ -1,7 +1,7 @@
 // Structured simplicial mesh, P2 dof lattice, SELL-C-sigma pattern and the
 // gather maps of the assembly kernels (host side, once per instance).
 //
-// Mesh (Section 3 and Section 6 use regular simplicial meshes): side^dim cells of
+// Mesh (Section 3 and Section 7 use regular simplicial meshes): side^dim cells of
 // width h = length / side; cell c splits into the simplices whose vertices follow
 // a monotone lattice path from the cell's low corner to its high corner (2 in 2D,
 // the 6 Kuhn tetrahedra in 3D).  P2 dofs are the half-spacing lattice points,

@@ -181,7 +181,7 @@ __global__ void k_diag_inv(int n_pad, const int* __restrict__ diag, const double
   }
 }
 
-// Stage right-hand side of Eq. (3.12) for one SELL-32 slice per warp:
+// Stage right-hand side of Eq. (3.10) for one SELL-32 slice per warp:
 //   b0 = -M mu + (1+r) M psi - 2 K psi - K omega + l,  b1 = -tau K mu + M d,  b2 = -M omega - K psi
 __global__ void k_rhs(int nslices, int n_pad, const int* __restrict__ sp, const int* __restrict__ cols,
                       const double* __restrict__ Mv, const double* __restrict__ Kv, const int* __restrict__ dptr,
@@ -213,6 +213,26 @@ __global__ void k_rhs(int nslices, int n_pad, const int* __restrict__ sp, const 
   b[row] = -m_mu + (1.0 + r) * m_psi - 2.0 * k_psi - k_om + l;
   b[n_pad + row] = -tau * k_mu + m_d;
   b[2 * n_pad + row] = -m_om - k_psi;
+}
+
+// Right-hand side of the linearised semi-implicit Euler system (Eq. 3.4):
+// b0 = (-2 psi_k^3, phi) from the per-element loads, b1 = M psi_k, b2 = 0.
+__global__ void k_euler_rhs(int nslices, int n_pad, const int* __restrict__ sp, const int* __restrict__ cols,
+                            const double* __restrict__ Mv, const int* __restrict__ dptr,
+                            const int* __restrict__ didx, const double* __restrict__ lbuf,
+                            const double* __restrict__ psi, double* b) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= nslices) return;
+  const int row = s * 32 + lane;
+  double m_psi = 0.0;
+  const int end = sp[s + 1];
+  for (int idx = sp[s] + lane; idx < end; idx += 32) m_psi = fma(Mv[idx], psi[cols[idx]], m_psi);
+  double l = 0.0;
+  for (int q = dptr[row]; q < dptr[row + 1]; ++q) l += lbuf[didx[q]];
+  b[row] = -2.0 * l;
+  b[n_pad + row] = m_psi;
+  b[2 * n_pad + row] = 0.0;
 }
 
 __global__ void k_dof_gather(int n_pad, const int* __restrict__ dptr, const int* __restrict__ didx,
@@ -443,6 +463,13 @@ cudaError_t launch_rhs(int nslices, const int* sp, const int* cols, const double
   const int n_pad = nslices * 32;
   k_rhs<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, n_pad, sp, cols, Mv, Kv, dptr, didx,
                                                                        lbuf, x, d, r, tau, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_euler_rhs(int nslices, int n_pad, const int* sp, const int* cols, const double* Mv, const int* dptr,
+                             const int* didx, const double* lbuf, const double* psi, double* b, cudaStream_t st) {
+  k_euler_rhs<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, n_pad, sp, cols, Mv, dptr, didx,
+                                                                             lbuf, psi, b);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,9 @@ cudaError_t launch_diag_inv(int n_pad, const int* diag_pos, const double* A, dou
 cudaError_t launch_rhs(int nslices, const int* slice_ptr, const int* cols, const double* Mv, const double* Kv,
                        const int* dptr, const int* didx, const double* lbuf, const double* x, const double* d,
                        double r, double tau, double* b, cudaStream_t st);
+cudaError_t launch_euler_rhs(int nslices, int n_pad, const int* slice_ptr, const int* cols, const double* Mv,
+                             const int* dptr, const int* didx, const double* lbuf, const double* psi, double* b,
+                             cudaStream_t st);
 cudaError_t launch_dof_gather(int n_pad, const int* dptr, const int* didx, const double* lbuf, double* out,
                               cudaStream_t st);
 cudaError_t launch_spmv_combo(int nslices, const int* slice_ptr, const int* cols, const double* Mv,

@@ -1,8 +1,8 @@
 // Persistent cooperative kernel for one Rosenbrock stage solve.
 //
 // One launch runs the whole right-preconditioned FGMRES(restart) with modified
-// Gram-Schmidt (Section 4 and Section 6 of Praetorius & Voigt) on
-//     A^R = [[M, A01, K], [tau K, M / gamma, 0], [0, K, M]]      (Eq. 3.12, PFC2)
+// Gram-Schmidt (Section 4 and Section 7 of Praetorius & Voigt) on
+//     A^R = [[M, A01, K], [tau K, M / gamma, 0], [0, K, M]]      (Eq. 3.10, PFC2)
 // with the block preconditioner P_CH applied in the steps of Section 4 / 4.2:
 //     (1)   M y0 = v0
 //     (2)   (M + delta K) y1 = gamma v1 - tau_e K y0

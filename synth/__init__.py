@@ -11,8 +11,8 @@ generator seeded with ``seed`` is ``mix64(seed + (j + 1) * 0x9E3779B97F4A7C15)``
 (all arithmetic mod 2**64), which is the sequence of successive ``next()`` calls
 of the published generator.  Uniforms in [0, 1) take the top 53 bits.
 
-Initial states follow the crystallisation set-up of the paper (Section 6: a
-state "far from stationary", noise around a mean density psi_bar):
+Initial states follow the crystallisation set-up of the paper (Section 7: a
+start well away from equilibrium, noise around a mean density psi_bar):
 ``psi0_j = psi_bar + amp * (2 u_j - 1)`` with ``j`` the lexicographic P2 dof index.
 """
 from __future__ import annotations
@@ -85,10 +85,21 @@ class Workload:
 
 
 # Workload recipes.  Sizes and parameters follow the paper's 2D/3D crystallisation
-# settings (Section 6) scaled to structured square/cube grids.
+# settings (Section 7) scaled to structured square/cube grids.
 C1_2D_SMALL = Workload("2d-s32-L32", 2, 32, 32.0, -0.4, -0.3, 0.1, 1, 0.1, 1, 1e-10)
 C2_2D_LARGE = Workload("2d-s512-L256", 2, 512, 256.0, -0.4, -0.3, 0.1, 2, 0.1, 20, 1e-10)
 C3_3D = Workload("3d-s64-L64", 3, 64, 64.0, -0.3, -0.35, 0.05, 3, 0.1, 5, 1e-10)
+
+# Lattice spacing d = 4 pi / sqrt(3) of the one-mode crystal approximation the
+# paper sizes its domains by (Section 7: Omega = [N d]^dim, P2 dof spacing about pi/4).
+LATTICE_D = 4.0 * math.pi / math.sqrt(3.0)
+# The ~66,000-unknown comparison problems of the paper's solver tables (Section 7,
+# Tables 3-5), linearised Euler steps at tau = 0.1: 2D [16 d]^2 with 74^2 squares
+# (3 x 149^2 = 66,603 unknowns; r = psi_bar = -0.35) and 3D [3 d]^3 with 14^3 cubes
+# (3 x 29^3 = 73,167 unknowns; r = -0.3, psi_bar = -0.34), both with dof spacing
+# within 1.5 % of pi/4.
+C0_2D_EULER = Workload("2d-s74-L16d", 2, 74, 16 * LATTICE_D, -0.35, -0.35, 0.1, 6, 0.1, 20, 1e-8)
+C0_3D_EULER = Workload("3d-s14-L3d", 3, 14, 3 * LATTICE_D, -0.3, -0.34, 0.05, 7, 0.1, 20, 1e-8)
 
 
 def batched_instances(count: int = 256, seed: int = 4, lo: int = 16, hi: int = 256) -> list[Workload]:

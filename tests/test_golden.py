@@ -36,11 +36,11 @@ def test_lemma3_no_critical_width_in_liquid_phase():
 
 
 def test_critical_tau_for_p_is_one():
-    # tau_natural = 1 for P (Section 5.1): its q-denominator vanishes at k^2 = 1, tau = 1
+    # tau_natural = 1 for P (Section 6.1): its q-denominator vanishes at k^2 = 1, tau = 1
     den = lambda k2, tau: tau * k2 ** 3 + (math.sqrt(tau) - 2 * tau) * k2 ** 2 - math.sqrt(tau) * k2 + 1
     assert abs(den(1.0, 1.0)) < 1e-15
     assert min(den(0.01 * i, 0.99) for i in range(1, 400)) > 0
-    # P_CH's denominator stays positive for every tau (Section 5.1)
+    # P_CH's denominator stays positive for every tau (Section 6.1)
     for tau in (0.01, 1.0, 10.0, 100.0):
         assert min(analysis.qch_eigenvalue(0.05 * i, tau, -0.35) for i in range(1, 200)) > 0 or True
 

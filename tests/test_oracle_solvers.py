@@ -3,7 +3,7 @@
 * Jacobi-PCG and FGMRES against direct solves (library LU).
 * The full stage solve (FGMRES(30) + P_CH + PCG inner) against a dense LU of A^R
   on tiny meshes, to 1e-12.
-* The discrete form of the spectral statement of Section 5 (Eq. 5.11): for a
+* The discrete form of the spectral statement of Section 6 (Eq. 6.9): for a
   constant psi_bar and exact inner solves the preconditioned stage operator has
   the eigenvalue 1 (2n times) and q_CH(mu_j) for the generalised eigenvalues mu_j
   of (K, M), with tau replaced by tau_e = gamma tau.
