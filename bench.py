@@ -60,6 +60,9 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-outer", type=int, default=2, help="FGMRES iterations in the CPU baseline sample")
+    p.add_argument("--pcg-sweep", action="store_true",
+                   help="per-iteration time of fixed-length inner PCG solves (M + sqrt(delta) K) against "
+                        "problem size, PCG form and blocks per SM; one JSON line per configuration")
     p.add_argument("--profile-case", action="store_true",
                    help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
                         "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
@@ -213,6 +216,37 @@ def oracle_euler_sample(w: synth.Workload):
     return {"value": 1e3 * t, "unit": "ms/solve", "cores": 1, "kind": "oracle",
             "sample": f"oracle (numpy/scipy, 1 thread): assembly and one Euler solve of {w.name} at tau 0.1, "
                       f"{st.outer_iterations} outer iterations"}
+
+
+def pcg_sweep(args):
+    """Per-iteration cost of the inner Jacobi-PCG against size: 60-iteration solves with
+    M + sqrt(delta) K (tau = 1) through pfc_pcg, timed by the library's CUDA events."""
+    import torch
+
+    import paper_1501_06852_gb300 as pfc
+
+    cases = [(2, s) for s in (32, 64, 128, 256, 512, 1024)] + [(3, s) for s in (8, 16, 32, 64)]
+    for dim, side in cases:
+        n = (2 * side + 1) ** dim
+        psi0 = torch.from_numpy(synth.initial_psi(dim, side, -0.3, 0.1, 7)).cuda()
+        rhs = torch.from_numpy(synth.random_vector(n, 8)).cuda()
+        for precision, variants in (("fp32", (0, 3)), ("fp64", (0, 1))):
+            for variant in variants:
+                for bps in (1, 2):
+                    with pfc.PFCSolver(dim, side, float(side), r=-0.4, precision=precision, max_inner=60,
+                                       pcg_variant=variant, blocks_per_sm=bps) as s:
+                        s.assemble(s.init_state(psi0), 1.0)
+                        s.pcg(2, rhs, 1e-30)
+                        s.set_timing(True)
+                        best = float("inf")
+                        for _ in range(3):
+                            m0 = s.counters()["solver_ms"]
+                            _, its = s.pcg(2, rhs, 1e-30)
+                            best = min(best, 1e3 * (s.counters()["solver_ms"] - m0) / max(its, 1))
+                    print(json.dumps({"dim": dim, "side": side, "rows": n, "precision": precision,
+                                      "pcg_variant": variant, "blocks_per_sm": bps, "us_per_iteration": best}),
+                          flush=True)
+    return 0
 
 
 def tau_cap(w: synth.Workload) -> float:
@@ -461,7 +495,7 @@ def native(args, world, rank, local, pg):
             "workload": f"{w.name}: {w.dim}D [0,{w.length:g}]^{w.dim}, side {w.side}, P2, {n} dofs/field, "
                         f"{3 * n} unknowns, r={w.r}, psi={w.psi_mean}+{w.amp}U(-1,1) seed {w.seed}, "
                         f"tau0={w.tau0}, adaptive Ros3Pw (Lemma-3 guard tau<={cap:.3g})",
-            "precision": f"{args.precision} inner PCG (textbook form), fp64 outer FGMRES(30)/Arnoldi/step control",
+            "precision": f"{args.precision} inner Jacobi-PCG (Chronopoulos-Gear form), fp64 outer FGMRES(30)/Arnoldi/step control",
             "inner_operator": "structured stencils for M, K, M+dK, M+sqrt(d)K (boundary rows assembled SELL-32)",
             "outer_tol": args.outer_tol, "inner_rtol": 1e-3,
             "l2": "inputs larger than L2: matrices + Krylov bases ~3 GB per instance vs 129 MB L2",
@@ -675,6 +709,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_case:
         return profile_case(args)
+    if args.pcg_sweep:
+        return pcg_sweep(args)
     if args.workload in ("c4", "c5", "c0"):
         out = {"c4": batched, "c5": serve, "c0": euler_tables}[args.workload](args)
         print(json.dumps(out), flush=True)
