@@ -549,8 +549,15 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const bool stencil = c->opt.inner_operator == 1;
   if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma))
     return bail(fail(c, PFC_ERR_INVALID, err));
-  if (stencil && ((int)S.st_off.size() > pfc::kMaxStencil || S.ntypes_dof > 8))
-    return bail(fail(c, PFC_ERR_INVALID, "structured stencil larger than the kernel's table"));
+  if (stencil) {
+    // the kernel pads every type to the longest stencil (rounded up to 4) and adds
+    // one all-padding type
+    int longest = 0;
+    for (int t = 0; t < S.ntypes_dof; ++t) longest = std::max(longest, S.st_start[t + 1] - S.st_start[t]);
+    const int stride = (longest + 3) & ~3;
+    if (S.ntypes_dof > 8 || (S.ntypes_dof + 1) * stride > pfc::kMaxStencil)
+      return bail(fail(c, PFC_ERR_INVALID, "structured stencil larger than the kernel's table"));
+  }
   c->n = S.n;
   c->n_pad = S.n_pad;
   c->nslices = S.nslices;

@@ -59,8 +59,13 @@ namespace {
 #define PFC_SPMV_WIDE 1
 #endif
 #ifndef PFC_GROUP
-#define PFC_GROUP 4
+#define PFC_GROUP 1
 #endif
+#ifndef PFC_ST_UNROLL
+#define PFC_ST_UNROLL 4
+#endif
+// the stencil tables are padded to a multiple of 4 entries per type
+static_assert(4 % PFC_ST_UNROLL == 0, "PFC_ST_UNROLL must divide 4");
 
 constexpr int kThreads = PFC_SOLVER_THREADS;
 constexpr int kWarps = kThreads / 32;
@@ -90,7 +95,8 @@ __shared__ unsigned long long s_t_last;
 __shared__ long long s_prof[8];
 // structured-stencil tables, loaded once per block: entry offsets, the start of
 // each dof type, and the weights of the four inner operators in the inner type
-__shared__ int s_st_start[9];
+__shared__ int s_st_start[9];   // first table entry of each dof type (type * stride)
+__shared__ int s_st_cnt[9];     // entries of each dof type; the last type is all padding
 __shared__ __align__(16) unsigned char s_st_raw[4 * kMaxStencil * 16];
 
 // one stencil entry: column offset and weight, read with a single shared load
@@ -305,7 +311,7 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
     const unsigned info = __ldg(a.rowinfo + row);
     if (info & 8u) {
       const int t = info & 7u;
-      const int k0 = s_st_start[t], k1 = s_st_start[t + 1];
+      const int k0 = s_st_start[t], k1 = k0 + s_st_cnt[t];
       const StEntry<Acc>* tab = reinterpret_cast<const StEntry<Acc>*>(s_st_raw) + op * kMaxStencil;
       Acc acc = Acc(0);
 #pragma unroll 8
@@ -317,6 +323,70 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
     }
   }
   return sell_row_wide<Acc>(se, a.cols, vals, x, lane);
+}
+
+// Rows (s0 + u) * 32 + lane, u < nsl, of inner operator op applied to x: the
+// group form of inner_row for the SpMV phases.  Each row of the group has its own
+// dof type; all lanes loop up to the longest stencil among the warp's rows and
+// predicate per row, so lanes of different types (they alternate along x) do not
+// serialise, and the loads of all rows of the group are in flight together.  Each
+// row accumulates its entries in the same order as inner_row, so the results are
+// the same bits.  Rows with a missing element take their SELL row.  Called by all
+// 32 lanes together.
+template <class Acc, class TM, class TX>
+__device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, int op, const TM* __restrict__ vals,
+                                           const TX* x, int s0, int nsl, int lane, Acc (&out)[kGroup]) {
+  if (!a.stencil) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu)
+      if (uu < nsl) out[uu] = sell_row_wide<Acc>(slice_bounds(g, a.slice_ptr, s0 + uu), a.cols, vals, x, lane);
+    return;
+  }
+  const StEntry<Acc>* tab = reinterpret_cast<const StEntry<Acc>*>(s_st_raw) + op * kMaxStencil;
+  // every type's entries are padded with (offset 0, weight 0) up to the table
+  // stride, and the extra type a.st_types is padding only: rows past the group's
+  // end and rows with a missing element run the loop on it, reading x at a valid row
+  int base[kGroup], rowc[kGroup];
+  bool interior[kGroup];
+  int nmax = 0;
+#pragma unroll
+  for (int uu = 0; uu < kGroup; ++uu) {
+    base[uu] = s_st_start[a.st_types];
+    rowc[uu] = s0 * 32 + lane;
+    interior[uu] = true;
+    if (uu < nsl) {
+      rowc[uu] = (s0 + uu) * 32 + lane;
+      const unsigned info = __ldg(a.rowinfo + rowc[uu]);
+      interior[uu] = (info & 8u) != 0;
+      if (interior[uu]) {
+        const int t = info & 7u;
+        base[uu] = s_st_start[t];
+        nmax = max(nmax, s_st_cnt[t]);
+      }
+    }
+  }
+  nmax = __reduce_max_sync(0xffffffffu, nmax);
+  Acc acc[kGroup];
+#pragma unroll
+  for (int uu = 0; uu < kGroup; ++uu) acc[uu] = Acc(0);
+  for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
+#pragma unroll
+    for (int j = 0; j < PFC_ST_UNROLL; ++j) {
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        const StEntry<Acc> e = tab[base[uu] + k + j];
+        acc[uu] = fma(e.w, (Acc)x[rowc[uu] + e.off], acc[uu]);
+      }
+    }
+  }
+#pragma unroll
+  for (int uu = 0; uu < kGroup; ++uu) {
+    if (uu < nsl) {
+      const int2 se = slice_bounds(g, a.slice_ptr, s0 + uu);
+      if (!interior[uu]) acc[uu] = sell_row_wide<Acc>(se, a.cols, vals, x, lane);
+      out[uu] = acc[uu];
+    }
+  }
 }
 
 struct InnerCount {
@@ -406,12 +476,19 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   const double thr = rtol * rtol * bb;
   for (int it = 1; it <= maxit; ++it) {
     Acc ppq = Acc(0);
-    FOR_MY_SLICES(g, s) {
-      const int row = s * 32 + lane;
-      const Acc pr = (Acc)p[row];
-      const TV qv = (TV)inner_row<Acc>(g, a, op, AV, p, s, lane);
-      q[row] = qv;
-      ppq = fma(pr, (Acc)qv, ppq);
+    FOR_MY_GROUPS(g, s0, nsl) {
+      Acc qa[kGroup];
+      inner_rows<Acc>(g, a, op, AV, p, s0, nsl, lane, qa);
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc pr = (Acc)p[row];
+          const TV qv = (TV)qa[uu];
+          q[row] = qv;
+          ppq = fma(pr, (Acc)qv, ppq);
+        }
+      }
     }
     if (!grid_sum<Acc>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
     const Acc pq = (Acc)red.x;
@@ -546,15 +623,22 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   const double thr = rtol * rtol * bb;
   // w = A u, m = D w, partial (r, u), (w, u)
   Acc pg = Acc(0), pd = Acc(0);
-  FOR_MY_SLICES(g, s) {
-    const int row = s * 32 + lane;
-    const TV uvv = u[row];
-    const Acc rr0 = (Acc)r[row], dd0 = (Acc)DI[row];
-    const TV wvv = (TV)inner_row<Acc>(g, a, op, AV, u, s, lane);
-    w[row] = wvv;
-    mcur[row] = (TV)(dd0 * (Acc)wvv);
-    pg = fma(rr0, (Acc)uvv, pg);
-    pd = fma((Acc)wvv, (Acc)uvv, pd);
+  FOR_MY_GROUPS(g, s0, nsl) {
+    Acc wa[kGroup];
+    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int row = (s0 + uu) * 32 + lane;
+        const TV uvv = u[row];
+        const Acc rr0 = (Acc)r[row], dd0 = (Acc)DI[row];
+        const TV wvv = (TV)wa[uu];
+        w[row] = wvv;
+        mcur[row] = (TV)(dd0 * (Acc)wvv);
+        pg = fma(rr0, (Acc)uvv, pg);
+        pd = fma((Acc)wvv, (Acc)uvv, pd);
+      }
+    }
   }
   if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   double gamma = red.x, delta = red.y, gamma_old = 1.0, alpha_old = 1.0;
@@ -579,12 +663,17 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     }
     const Acc al = (Acc)alpha, be = (Acc)beta;
     Acc prg = Acc(0), pwd = Acc(0), prr = Acc(0);
-    FOR_MY_SLICES(g, s) {
-      const int row = s * 32 + lane;
+    FOR_MY_GROUPS(g, s0, nsl) {
+      Acc nav[kGroup];
+      inner_rows<Acc>(g, a, op, AV, mcur, s0, nsl, lane, nav);
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu >= nsl) break;
+      const int row = (s0 + uu) * 32 + lane;
       const Acc mv = (Acc)mcur[row], zo = (Acc)zv[row], qo = (Acc)qv[row], so = (Acc)sv[row];
       const Acc po = (Acc)pv[row], xo = (Acc)x[row], ro = (Acc)r[row], uo = (Acc)u[row], wo = (Acc)w[row];
       const Acc dd = (Acc)DI[row];
-      const Acc na = inner_row<Acc>(g, a, op, AV, mcur, s, lane);
+      const Acc na = nav[uu];
       const Acc z1 = na + be * zo;
       const Acc q1 = mv + be * qo;
       const Acc s1 = wo + be * so;
@@ -605,6 +694,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       prg = fma(r1, u1, prg);
       pwd = fma(w1, u1, pwd);
       prr = fma(r1, r1, prr);
+      }
     }
     if (!grid_sum<Acc>(g, prg, pwd, prr, red, kPhSpmv)) return false;
     its = it + 1;
@@ -675,13 +765,19 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
   const Acc thr = (Acc)(rtol * rtol * bb);
   // w = A u, partials (r, u), (w, u)
   Acc pg = Acc(0), pd = Acc(0);
-  FOR_MY_SLICES(g, s) {
-    const int row = s * 32 + lane;
-    const Acc uo = (Acc)u[row], ro = (Acc)r[row];
-    const Acc wv = inner_row<Acc>(g, a, op, AV, u, s, lane);
-    w[row] = (TV)wv;
-    pg = fma(ro, uo, pg);
-    pd = fma(wv, uo, pd);
+  FOR_MY_GROUPS(g, s0, nsl) {
+    Acc wa[kGroup];
+    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int row = (s0 + uu) * 32 + lane;
+        const Acc uo = (Acc)u[row], ro = (Acc)r[row];
+        w[row] = (TV)wa[uu];
+        pg = fma(ro, uo, pg);
+        pd = fma(wa[uu], uo, pd);
+      }
+    }
   }
   if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   Acc gam = (Acc)red.x, del = (Acc)red.y;
@@ -738,13 +834,19 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
     // phase 2: w = A u and the two inner products
     pg = Acc(0);
     pd = Acc(0);
-    FOR_MY_SLICES(g, s) {
-      const int row = s * 32 + lane;
-      const Acc uo = (Acc)u[row], ro = (Acc)r[row];
-      const Acc wv = inner_row<Acc>(g, a, op, AV, u, s, lane);
-      w[row] = (TV)wv;
-      pg = fma(ro, uo, pg);
-      pd = fma(wv, uo, pd);
+    FOR_MY_GROUPS(g, s0, nsl) {
+      Acc wa[kGroup];
+      inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc uo = (Acc)u[row], ro = (Acc)r[row];
+          w[row] = (TV)wa[uu];
+          pg = fma(ro, uo, pg);
+          pd = fma(wa[uu], uo, pd);
+        }
+      }
     }
     if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
     const Acc gnew = (Acc)red.x, dnew = (Acc)red.y;
@@ -1060,11 +1162,25 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
   }
   if (a.stencil) {
     using Acc = typename AccOf<TV>::type;
-    const int ns = __ldg(a.st_start + a.st_types);
-    for (int k = threadIdx.x; k < ns; k += blockDim.x) {
-      const int off = __ldg(a.st_off + k);
-      const double wm = __ldg(a.st_wM + k), wk = __ldg(a.st_wK + k);
-      StEntry<Acc>* tab = reinterpret_cast<StEntry<Acc>*>(s_st_raw);
+    // table stride: the longest type stencil rounded up to a multiple of 4 (the
+    // host checks (types + 1) * stride <= kMaxStencil); entries past a type's
+    // length and the whole extra type a.st_types are (offset 0, weight 0)
+    int L = 0;
+    for (int t = 0; t < a.st_types; ++t) L = max(L, __ldg(a.st_start + t + 1) - __ldg(a.st_start + t));
+    L = (L + 3) & ~3;
+    const int total = (a.st_types + 1) * L;
+    StEntry<Acc>* tab = reinterpret_cast<StEntry<Acc>*>(s_st_raw);
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+      const int t = k / L, j = k - t * L;
+      const int len = t < a.st_types ? __ldg(a.st_start + t + 1) - __ldg(a.st_start + t) : 0;
+      int off = 0;
+      double wm = 0.0, wk = 0.0;
+      if (j < len) {
+        const int src = __ldg(a.st_start + t) + j;
+        off = __ldg(a.st_off + src);
+        wm = __ldg(a.st_wM + src);
+        wk = __ldg(a.st_wK + src);
+      }
 #pragma unroll
       for (int op = 0; op < 4; ++op) {
         StEntry<Acc> e{};
@@ -1073,7 +1189,11 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
         tab[op * kMaxStencil + k] = e;
       }
     }
-    if ((int)threadIdx.x <= a.st_types) s_st_start[threadIdx.x] = __ldg(a.st_start + threadIdx.x);
+    if ((int)threadIdx.x <= a.st_types) {
+      const int t = threadIdx.x;
+      s_st_start[t] = t * L;
+      s_st_cnt[t] = t < a.st_types ? __ldg(a.st_start + t + 1) - __ldg(a.st_start + t) : 0;
+    }
     __syncthreads();
   }
   Ctx<TM, TV> c(a);
