@@ -80,6 +80,12 @@ typedef struct {
                          elements all exist has the same entries as every other row of its
                          dof type, so those rows read neither values nor indices (the
                          other rows keep their assembled values) */
+  int smem_window;    /* 1: with structured stencils and float32/float16 inner solves, each
+                         block of the persistent kernel copies the rows of the SpMV source
+                         vector its rows reach (its own rows plus the stencil reach on both
+                         sides) into shared memory once per product, when that window fits
+                         without lowering the grid's residency; 0: stencil reads go to
+                         global memory.  Same results bit for bit either way. */
 } pfc_options;
 
 typedef struct {
@@ -97,7 +103,8 @@ typedef struct {
 
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
- * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1. */
+ * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
+ * smem_window = 1. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

@@ -36,7 +36,8 @@ class _Options(ctypes.Structure):
                 ("restart", ctypes.c_int), ("max_outer", ctypes.c_int), ("max_inner", ctypes.c_int),
                 ("precision", ctypes.c_int), ("step_atol", ctypes.c_double), ("step_rtol", ctypes.c_double),
                 ("tau_max", ctypes.c_double), ("blocks_per_sm", ctypes.c_int), ("pcg_variant", ctypes.c_int),
-                ("inner_operator", ctypes.c_int)]
+                ("inner_operator", ctypes.c_int),
+                ("smem_window", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -197,7 +198,7 @@ class PFCSolver:
                  outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
-                 inner_operator: int = 1, stream=None):
+                 inner_operator: int = 1, smem_window: int = 1, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -213,6 +214,7 @@ class PFCSolver:
         o.step_atol, o.step_rtol, o.tau_max, o.blocks_per_sm = step_atol, step_rtol, tau_max, blocks_per_sm
         o.pcg_variant = pcg_variant
         o.inner_operator = inner_operator
+        o.smem_window = smem_window
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -63,6 +63,8 @@ struct pfc_ctx {
   int *st_start = nullptr, *st_off = nullptr;
   double *st_wM = nullptr, *st_wK = nullptr;
   int st_types = 0;
+  int st_halo = 0;              // largest |stencil offset|
+  int win_cap = 0;              // floats of the shared-memory SpMV window (0: off)
   double *mass_tab = nullptr, *stiff_tab = nullptr;
   // float64 matrices
   double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
@@ -78,7 +80,7 @@ struct pfc_ctx {
   // control
   unsigned* arrive = nullptr;
   int* errw = nullptr;
-  double4* part = nullptr;
+  double4_32a* part = nullptr;
   pfc::DevStats* stats = nullptr;   // 4 slots
   double* step_part = nullptr;
   double* err_scalar = nullptr;
@@ -182,6 +184,8 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.st_wM = c->st_wM;
   a.st_wK = c->st_wK;
   a.st_types = c->st_types;
+  a.st_halo = c->st_halo;
+  a.win_cap = c->win_cap;
   const double cK[4] = {0.0, 1.0, c->delta, std::sqrt(c->delta)};
   const double cM[4] = {1.0, 0.0, 1.0, 1.0};
   for (int k = 0; k < 4; ++k) {
@@ -402,6 +406,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs, int count, int slot, bool to_tmp, Bat
       pfc_ctx* ck = ctxs[wv.first + i];
       c = ck;
       pfc::SolveArgs a = base_args(ck, ck->prec);
+      a.win_cap = 0;  // segments of different instances: no shared-memory window
       a.mode = 0;
       a.b = ck->bv;
       a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)slot * 3 * ck->n_pad;
@@ -468,6 +473,7 @@ void pfc_default_options(pfc_options* o) {
   o->blocks_per_sm = 0;
   o->pcg_variant = 2;
   o->inner_operator = 1;
+  o->smem_window = 1;
 }
 
 const char* pfc_status_string(int s) {
@@ -532,6 +538,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1, 2 or 3"));
   if (c->opt.inner_operator < 0 || c->opt.inner_operator > 1)
     return bail(fail(c, PFC_ERR_INVALID, "inner_operator must be 0 or 1"));
+  if (c->opt.smem_window < 0 || c->opt.smem_window > 1)
+    return bail(fail(c, PFC_ERR_INVALID, "smem_window must be 0 or 1"));
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
     return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
   c->stream = (cudaStream_t)cuda_stream;
@@ -615,6 +623,29 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     blk[(size_t)c->G * W] = S.nslices;
   }
 
+  // Shared-memory window of the stencil SpMV (float inner vectors): block b reads
+  // the source vector on its rows [rs, re) widened by the stencil reach on both
+  // sides, rounded out to multiples of 4 floats.  It is used only if the largest
+  // window keeps the residency the grid was sized with.
+  if (stencil) {
+    for (int v : S.st_off) c->st_halo = std::max(c->st_halo, v < 0 ? -v : v);
+  }
+  if (stencil && c->prec != 0 && c->opt.smem_window == 1) {
+    int winmax = 0;
+    for (int b = 0; b < c->G; ++b) {
+      const int rs = blk[(size_t)b * W] * 32, re = blk[(size_t)(b + 1) * W] * 32;
+      const int lo = std::max(0, rs - c->st_halo) & ~3;
+      const int hi = std::min(c->n_pad, (re + c->st_halo + 3) & ~3);
+      winmax = std::max(winmax, hi - lo);
+    }
+    const int need = (c->G + sms - 1) / sms;  // blocks per SM the grid needs co-resident
+    int occ_w = 0;
+    if (winmax > 0 && pfc::solve_occupancy(c->prec, &occ_w, (size_t)winmax * sizeof(float)) == cudaSuccess &&
+        occ_w >= need)
+      c->win_cap = winmax;
+    cudaGetLastError();
+  }
+
   // ---- device layout (one allocation) ----
   const size_t np3 = 3 * (size_t)c->n_pad;
   const size_t ib = inner_elem_bytes(c->prec);
@@ -664,7 +695,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t vec_end = L.take(0);
   const size_t o_arr = L.take(sizeof(unsigned) * 4);
   const size_t o_errw = L.take(sizeof(int) * 8);
-  const size_t o_part = L.take(sizeof(double4) * pfc::solve_ring() * c->G);
+  const size_t o_part = L.take(sizeof(double4_32a) * pfc::solve_ring() * c->G);
   const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);
   const size_t o_sp = L.take(sizeof(double) * pfc::step_partials());
   const size_t o_es = L.take(sizeof(double) * 2);
@@ -729,7 +760,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->ivec = (void*)(A + o_ivec);
   c->arrive = (unsigned*)(A + o_arr);
   c->errw = (int*)(A + o_errw);
-  c->part = (double4*)(A + o_part);
+  c->part = (double4_32a*)(A + o_part);
   c->stats = (pfc::DevStats*)(A + o_stats);
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);

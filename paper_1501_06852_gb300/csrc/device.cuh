@@ -58,7 +58,7 @@ struct SolveArgs {
   void* ivec;              // kInnerVecs inner vectors of n_pad TV each
   unsigned* arrive;        // grid barrier counter (zeroed before each launch)
   int* err;                // error word (zeroed before each launch)
-  double4* part;           // reduction partials, kRing x gridDim.x
+  double4_32a* part;           // reduction partials, kRing x gridDim.x
   DevStats* stats;
   unsigned long long spin_limit_ns;  // a barrier wait gives up after this long
   int barrier_extra;       // 0; > 0 only in the timeout self-test (waits cannot complete)
@@ -72,6 +72,9 @@ struct SolveArgs {
   const double* st_wM;     // M and K weights of each entry
   const double* st_wK;
   int st_types;
+  int st_halo;             // largest |column offset| of a stencil entry
+  int win_cap;             // > 0: floats of dynamic shared memory per block for the window of
+                           //   the SpMV source vector (float inner vectors only); 0: no window
   double op_cK[4];         // inner operator op = M, K, M + delta K, M + sqrt(delta) K:
   double op_cM[4];         //   weights op_cM[op] * wM + op_cK[op] * wK
 };

@@ -10,7 +10,7 @@ namespace pfc {
 // persistent solver (solver.cu); prec: 0 float64, 1 float32, 2 float16 values
 int solve_threads();
 int solve_ring();
-cudaError_t solve_occupancy(int prec, int* blocks_per_sm);
+cudaError_t solve_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem = 0);
 cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t stream);
 cudaError_t batch_occupancy(int prec, int* blocks_per_sm);
 cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream);

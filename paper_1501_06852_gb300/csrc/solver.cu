@@ -50,16 +50,19 @@ namespace {
 // (which caps registers per thread), and the SpMV row form (0: rolled loop
 // unrolled by 4; 1: CH loads of a row issued before its gathers).
 #ifndef PFC_SOLVER_THREADS
-#define PFC_SOLVER_THREADS 512
+#define PFC_SOLVER_THREADS 1024
 #endif
 #ifndef PFC_SOLVER_MINBLOCKS
-#define PFC_SOLVER_MINBLOCKS 2
+#define PFC_SOLVER_MINBLOCKS 1
 #endif
 #ifndef PFC_SPMV_WIDE
 #define PFC_SPMV_WIDE 1
 #endif
 #ifndef PFC_GROUP
 #define PFC_GROUP 1
+#endif
+#ifndef PFC_INTERLEAVE
+#define PFC_INTERLEAVE 0
 #endif
 #ifndef PFC_ST_UNROLL
 #define PFC_ST_UNROLL 4
@@ -77,7 +80,7 @@ enum : int { kPhSpmv = 0, kPhVec = 1, kPhOuter = 2, kPhInit = 3 };
 
 struct Grid {
   unsigned* arrive;
-  double4* part;
+  double4_32a* part;
   int* err;
   unsigned long long limit_ns;
   int G;
@@ -86,10 +89,17 @@ struct Grid {
   int ring;
   int bid;         // block index inside this solve's grid (its segment in a batched launch)
   int w_lo, w_hi;  // this warp's contiguous slice range (cost balanced on the host)
-  int sp_lane;     // slice_ptr[w_lo + lane] (valid when the range has at most 31 slices)
-  bool sp_reg;     // the slice pointers of this warp live in sp_lane
+  int b_lo, b_hi;  // this block's slice range
+  int wid;         // warp index in the block
+  int sp_lane;     // start slot of this warp's lane-th slice (when sp_reg)
+  int sp_end;      // end slot of this warp's lane-th slice (when sp_reg)
+  bool sp_reg;     // the slot bounds of all of this warp's slices live in sp_lane / sp_end
   bool prof;       // block 0, thread 0 (accumulators live in shared memory)
+  int win_lo, win_n;  // rows [win_lo, win_lo + win_n) of the SpMV source held in s_win
+  bool staged;        // stencil SpMVs read the source vector from s_win
+  bool ri_smem;       // the block's row-info bytes are in s_rowinfo (row - 32 b_lo)
 };
+
 
 __shared__ unsigned long long s_t_last;
 __shared__ long long s_prof[8];
@@ -99,26 +109,74 @@ __shared__ int s_st_start[9];   // first table entry of each dof type (type * st
 __shared__ int s_st_cnt[9];     // entries of each dof type; the last type is all padding
 __shared__ __align__(16) unsigned char s_st_raw[4 * kMaxStencil * 16];
 
+// the row-info bytes of the block's rows (structured stencils), when they fit
+constexpr int kRowInfoCap = 16384;
+__shared__ __align__(16) unsigned char s_rowinfo[kRowInfoCap];
+
+// Row-info byte of row (one of this block's rows): dof type in bits 0-2, interior bit 3.
+__device__ __forceinline__ unsigned row_info(const Grid& g, const SolveArgs& a, int row) {
+  return g.ri_smem ? (unsigned)s_rowinfo[row - g.b_lo * 32] : (unsigned)__ldg(a.rowinfo + row);
+}
+
+// dynamic shared memory: the block's window of the SpMV source vector (float
+// inner vectors, structured stencils; see stage_window)
+extern __shared__ __align__(16) float s_win[];
+
 // one stencil entry: column offset and weight, read with a single shared load
 template <class Acc> struct StEntry;
 template <> struct __align__(8) StEntry<float> { int off; float w; };
 template <> struct __align__(16) StEntry<double> { int off; int pad; double w; };
 
-// Every warp owns a contiguous range of slices (the host splits each block's
-// range so that the warps carry equal SpMV-plus-vector cost).  Groups of kGroup
-// consecutive slices are staged together in vector phases: rows (s0 + u) * 32 + lane.
+// Slices of a block are dealt to its warps.  Interleaved (default): warp w takes
+// the groups of kGroup consecutive slices starting at b_lo + (w + m kWarps) kGroup,
+// m = 0, 1, ..., so that every warp gets the same mix of slice kinds (on the
+// structured mesh, lattice rows of vertex dofs have longer stencils than rows of
+// edge dofs, and a contiguous range would keep a warp inside one lattice row).
+// Contiguous: warp w takes the range [w_lo, w_hi) the host cut by cost.  Rows of
+// a group: (s0 + u) * 32 + lane, u < nsl.
+#if PFC_INTERLEAVE
+#define FOR_MY_GROUPS(g, s0, nsl)                                                                 \
+  for (int s0 = (g).b_lo + (g).wid * kGroup; s0 < (g).b_hi; s0 += kGroup * kWarps) \
+    if (const int nsl = min(kGroup, (g).b_hi - s0); true)
+#define FOR_MY_SLICES(g, s) for (int s = (g).b_lo + (g).wid; s < (g).b_hi; s += kWarps)
+#else
 #define FOR_MY_GROUPS(g, s0, nsl)                                     \
   for (int s0 = (g).w_lo; s0 < (g).w_hi; s0 += kGroup) \
     if (const int nsl = min(kGroup, (g).w_hi - s0); true)
-
 #define FOR_MY_SLICES(g, s) for (int s = (g).w_lo; s < (g).w_hi; ++s)
+#endif
+
+#if PFC_INTERLEAVE
+#define PFC_WARP_END(g) (g).b_hi
+#else
+#define PFC_WARP_END(g) (g).w_hi
+#endif
+
+// Position of slice s in this warp's list of slices (the order of the loops above).
+__device__ __forceinline__ int my_slice_index(const Grid& g, int s) {
+#if PFC_INTERLEAVE
+  const int d = s - g.b_lo - g.wid * kGroup;
+  return (d / (kGroup * kWarps)) * kGroup + d % (kGroup * kWarps);
+#else
+  return s - g.w_lo;
+#endif
+}
+
+// The k-th slice of this warp's list (may lie past the block's range).
+__device__ __forceinline__ int my_slice(const Grid& g, int k) {
+#if PFC_INTERLEAVE
+  return g.b_lo + g.wid * kGroup + (k / kGroup) * kGroup * kWarps + k % kGroup;
+#else
+  return g.w_lo + k;
+#endif
+}
 
 // First slot and end slot of slice s (one of this warp's slices).  Called by
 // all 32 lanes together.
 __device__ __forceinline__ int2 slice_bounds(const Grid& g, const int* __restrict__ sp, int s) {
   if (g.sp_reg) {
-    const int k = s - g.w_lo;
-    return make_int2(__shfl_sync(0xffffffffu, g.sp_lane, k), __shfl_sync(0xffffffffu, g.sp_lane, k + 1));
+    const int k = my_slice_index(g, s);
+    return make_int2(__shfl_sync(0xffffffffu, g.sp_lane, k), __shfl_sync(0xffffffffu, g.sp_end, k));
   }
   return make_int2(__ldg(sp + s), __ldg(sp + s + 1));
 }
@@ -144,8 +202,9 @@ __device__ bool grid_sync(Grid& g, int tag) {
     }
     g.epoch += 1;
     const unsigned target = g.epoch * (unsigned)g.expect;
-    __threadfence();
-    atomicAdd(g.arrive, 1u);
+    // release: this block's writes (ordered before by the __syncthreads above) are
+    // visible to every block whose acquire load below sees the new count
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(g.arrive) : "memory");
     unsigned spins = 0;
     unsigned long long t0 = 0;
     int ok = 1;
@@ -160,9 +219,7 @@ __device__ bool grid_sync(Grid& g, int tag) {
           break;
         }
       }
-      __nanosleep(32);
     }
-    __threadfence();
     if (ok && (ld_relaxed_i32(g.err) & kErrTimeout)) ok = 0;
     s_ok = ok;
     if (g.prof) {
@@ -180,23 +237,23 @@ __device__ bool grid_sync(Grid& g, int tag) {
 // kThreads blocks), so the read-back is one memory round trip, and the partials
 // are summed in a fixed order.
 template <class T>
-__device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
+__device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
   // T is the arithmetic of every stage of the tree: float for the float32 inner
   // solves (float64 throughput is scarce on this GPU), double everywhere else
-  __shared__ double4 s_w[kWarps];
-  __shared__ double4 s_res;
+  __shared__ double4_32a s_w[kWarps];
+  __shared__ double4_32a s_res;
   a = warp_sum(a);
   b = warp_sum(b);
   c = warp_sum(c);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) s_w[w] = make_double4((double)a, (double)b, (double)c, 0.0);
+  if (l == 0) s_w[w] = make_double4_32a((double)a, (double)b, (double)c, 0.0);
   __syncthreads();
   const int slot = g.ring;
   g.ring = (g.ring + 1) % kRing;
   if (w == 0) {
     T tx = T(0), ty = T(0), tz = T(0);
     if (l < kWarps) {
-      const double4 t = s_w[l];
+      const double4_32a t = s_w[l];
       tx = (T)t.x;
       ty = (T)t.y;
       tz = (T)t.z;
@@ -224,14 +281,14 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
     px = warp_sum(px);
     py = warp_sum(py);
     pz = warp_sum(pz);
-    if (l == 0) s_w[w] = make_double4((double)px, (double)py, (double)pz, 0.0);
+    if (l == 0) s_w[w] = make_double4_32a((double)px, (double)py, (double)pz, 0.0);
   }
   __syncthreads();
   if (w == 0) {
     const int nw = (g.G + 31) >> 5;
     T tx = T(0), ty = T(0), tz = T(0);
     if (l < nw) {
-      const double4 t = s_w[l];
+      const double4_32a t = s_w[l];
       tx = (T)t.x;
       ty = (T)t.y;
       tz = (T)t.z;
@@ -239,7 +296,7 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4& out, int tag) {
     tx = warp_sum(tx);
     ty = warp_sum(ty);
     tz = warp_sum(tz);
-    if (l == 0) s_res = make_double4((double)tx, (double)ty, (double)tz, 0.0);
+    if (l == 0) s_res = make_double4_32a((double)tx, (double)ty, (double)tz, 0.0);
   }
   __syncthreads();
   out = s_res;
@@ -308,7 +365,7 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
   const int2 se = slice_bounds(g, a.slice_ptr, s);
   if (a.stencil) {
     const int row = s * 32 + lane;
-    const unsigned info = __ldg(a.rowinfo + row);
+    const unsigned info = row_info(g, a, row);
     if (info & 8u) {
       const int t = info & 7u;
       const int k0 = s_st_start[t], k1 = k0 + s_st_cnt[t];
@@ -325,6 +382,24 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
   return sell_row_wide<Acc>(se, a.cols, vals, x, lane);
 }
 
+// Copies rows [win_lo, win_lo + win_n) of x into the block's shared window; called
+// by all threads of the block, only when g.staged (float vectors).  The window is
+// the block's own rows widened by the largest stencil offset on both sides and
+// rounded out to multiples of 4 floats, so every interior row's stencil reads
+// inside it; x is 16-byte aligned.  The first barrier keeps warps still reading
+// the previous window safe, the second publishes the new one.
+template <class TX>
+__device__ __forceinline__ void stage_window(const Grid& g, const TX* x) {
+  __syncthreads();
+  if constexpr (sizeof(TX) == 4) {
+    const float4* src = reinterpret_cast<const float4*>(x + g.win_lo);
+    float4* dst = reinterpret_cast<float4*>(s_win);
+    const int n4 = g.win_n >> 2;
+    for (int i = threadIdx.x; i < n4; i += kThreads) dst[i] = src[i];
+  }
+  __syncthreads();
+}
+
 // Rows (s0 + u) * 32 + lane, u < nsl, of inner operator op applied to x: the
 // group form of inner_row for the SpMV phases.  Each row of the group has its own
 // dof type; all lanes loop up to the longest stencil among the warp's rows and
@@ -335,7 +410,8 @@ __device__ __forceinline__ Acc inner_row(const Grid& g, const SolveArgs& a, int 
 // 32 lanes together.
 template <class Acc, class TM, class TX>
 __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, int op, const TM* __restrict__ vals,
-                                           const TX* x, int s0, int nsl, int lane, Acc (&out)[kGroup]) {
+                                           const TX* x, int s0, int nsl, int lane, Acc (&out)[kGroup],
+                                           bool from_win = false) {
   if (!a.stencil) {
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu)
@@ -356,7 +432,7 @@ __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, in
     interior[uu] = true;
     if (uu < nsl) {
       rowc[uu] = (s0 + uu) * 32 + lane;
-      const unsigned info = __ldg(a.rowinfo + rowc[uu]);
+      const unsigned info = row_info(g, a, rowc[uu]);
       interior[uu] = (info & 8u) != 0;
       if (interior[uu]) {
         const int t = info & 7u;
@@ -369,13 +445,27 @@ __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, in
   Acc acc[kGroup];
 #pragma unroll
   for (int uu = 0; uu < kGroup; ++uu) acc[uu] = Acc(0);
-  for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
+  if (from_win) {
+    // the interior rows' reach lies inside the window (see stage_window)
+    for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
 #pragma unroll
-    for (int j = 0; j < PFC_ST_UNROLL; ++j) {
+      for (int j = 0; j < PFC_ST_UNROLL; ++j) {
 #pragma unroll
-      for (int uu = 0; uu < kGroup; ++uu) {
-        const StEntry<Acc> e = tab[base[uu] + k + j];
-        acc[uu] = fma(e.w, (Acc)x[rowc[uu] + e.off], acc[uu]);
+        for (int uu = 0; uu < kGroup; ++uu) {
+          const StEntry<Acc> e = tab[base[uu] + k + j];
+          acc[uu] = fma(e.w, (Acc)s_win[rowc[uu] - g.win_lo + e.off], acc[uu]);
+        }
+      }
+    }
+  } else {
+    for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
+#pragma unroll
+      for (int j = 0; j < PFC_ST_UNROLL; ++j) {
+#pragma unroll
+        for (int uu = 0; uu < kGroup; ++uu) {
+          const StEntry<Acc> e = tab[base[uu] + k + j];
+          acc[uu] = fma(e.w, (Acc)x[rowc[uu] + e.off], acc[uu]);
+        }
       }
     }
   }
@@ -462,7 +552,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
       }
     }
   }
-  double4 red;
+  double4_32a red;
   if (!grid_sum<Acc>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -476,9 +566,10 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   const double thr = rtol * rtol * bb;
   for (int it = 1; it <= maxit; ++it) {
     Acc ppq = Acc(0);
+    if (g.staged) stage_window(g, p);
     FOR_MY_GROUPS(g, s0, nsl) {
       Acc qa[kGroup];
-      inner_rows<Acc>(g, a, op, AV, p, s0, nsl, lane, qa);
+      inner_rows<Acc>(g, a, op, AV, p, s0, nsl, lane, qa, g.staged);
 #pragma unroll
       for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
@@ -610,7 +701,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       }
     }
   }
-  double4 red;
+  double4_32a red;
   if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -623,9 +714,10 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   const double thr = rtol * rtol * bb;
   // w = A u, m = D w, partial (r, u), (w, u)
   Acc pg = Acc(0), pd = Acc(0);
+  if (g.staged) stage_window(g, u);
   FOR_MY_GROUPS(g, s0, nsl) {
     Acc wa[kGroup];
-    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
@@ -663,9 +755,10 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     }
     const Acc al = (Acc)alpha, be = (Acc)beta;
     Acc prg = Acc(0), pwd = Acc(0), prr = Acc(0);
+    if (g.staged) stage_window(g, mcur);
     FOR_MY_GROUPS(g, s0, nsl) {
       Acc nav[kGroup];
-      inner_rows<Acc>(g, a, op, AV, mcur, s0, nsl, lane, nav);
+      inner_rows<Acc>(g, a, op, AV, mcur, s0, nsl, lane, nav, g.staged);
 #pragma unroll
       for (int uu = 0; uu < kGroup; ++uu) {
       if (uu >= nsl) break;
@@ -752,7 +845,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
       }
     }
   }
-  double4 red;
+  double4_32a red;
   if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -765,9 +858,10 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
   const Acc thr = (Acc)(rtol * rtol * bb);
   // w = A u, partials (r, u), (w, u)
   Acc pg = Acc(0), pd = Acc(0);
+  if (g.staged) stage_window(g, u);
   FOR_MY_GROUPS(g, s0, nsl) {
     Acc wa[kGroup];
-    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
 #pragma unroll
     for (int uu = 0; uu < kGroup; ++uu) {
       if (uu < nsl) {
@@ -834,9 +928,10 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
     // phase 2: w = A u and the two inner products
     pg = Acc(0);
     pd = Acc(0);
+    if (g.staged) stage_window(g, u);
     FOR_MY_GROUPS(g, s0, nsl) {
       Acc wa[kGroup];
-      inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa);
+      inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
 #pragma unroll
       for (int uu = 0; uu < kGroup; ++uu) {
         if (uu < nsl) {
@@ -982,7 +1077,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   const int np = a.n_pad, n3 = 3 * np, m = a.restart, ld = m + 1;
   const int lane = threadIdx.x & 31;
   InnerCount cnt;
-  double4 red;
+  double4_32a red;
   double pb = 0.0;
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
@@ -1151,11 +1246,24 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
     const int wi = bid * kWarps + (int)(threadIdx.x >> 5);
     g.w_lo = __ldg(a.blk + wi);
     g.w_hi = __ldg(a.blk + wi + 1);
-    g.sp_reg = (g.w_hi - g.w_lo) <= 31;
-    const int k = g.w_lo + (int)(threadIdx.x & 31);
-    g.sp_lane = (g.sp_reg && k <= g.w_hi) ? __ldg(a.slice_ptr + k) : 0;
+    g.b_lo = __ldg(a.blk + bid * kWarps);
+    g.b_hi = __ldg(a.blk + (bid + 1) * kWarps);
+    g.wid = (int)(threadIdx.x >> 5);
+    // slot bounds of this warp's slices in registers when it has at most 32
+    g.sp_reg = my_slice(g, 32) >= PFC_WARP_END(g);
+    const int sl = my_slice(g, (int)(threadIdx.x & 31));
+    const bool have = g.sp_reg && sl < PFC_WARP_END(g);
+    g.sp_lane = have ? __ldg(a.slice_ptr + sl) : 0;
+    g.sp_end = have ? __ldg(a.slice_ptr + sl + 1) : 0;
   }
   g.prof = a.prof && bid == 0 && threadIdx.x == 0;
+  {
+    const int rs = __ldg(a.blk + bid * kWarps) * 32, re = __ldg(a.blk + (bid + 1) * kWarps) * 32;
+    g.win_lo = max(0, rs - a.st_halo) & ~3;
+    g.win_n = min(a.n_pad, (re + a.st_halo + 3) & ~3) - g.win_lo;
+    g.staged = sizeof(TV) == 4 && a.stencil && a.win_cap > 0 && re > rs && g.win_n <= a.win_cap;
+    g.ri_smem = false;
+  }
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) s_prof[k] = 0;
     s_t_last = global_ns();
@@ -1193,6 +1301,14 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
       const int t = threadIdx.x;
       s_st_start[t] = t * L;
       s_st_cnt[t] = t < a.st_types ? __ldg(a.st_start + t + 1) - __ldg(a.st_start + t) : 0;
+    }
+    // this block's row-info bytes, 16 at a time (the row ranges start at multiples of 32)
+    const int nrow = (g.b_hi - g.b_lo) * 32;
+    g.ri_smem = nrow <= kRowInfoCap;
+    if (g.ri_smem) {
+      const uint4* src = reinterpret_cast<const uint4*>(a.rowinfo + g.b_lo * 32);
+      uint4* dst = reinterpret_cast<uint4*>(s_rowinfo);
+      for (int i = threadIdx.x; i < nrow / 16; i += kThreads) dst[i] = __ldg(src + i);
     }
     __syncthreads();
   }
@@ -1257,14 +1373,26 @@ const void* kernel_for(int prec, bool batch = false) {
 int solve_threads() { return kThreads; }
 int solve_ring() { return kRing; }
 
-cudaError_t solve_occupancy(int prec, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(prec), kThreads, 0);
+// Allows dyn_smem bytes of dynamic shared memory for the kernel (above the 48 KiB
+// default a kernel must opt in).
+cudaError_t allow_dyn_smem(const void* fn, size_t dyn_smem) {
+  if (dyn_smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+}
+
+cudaError_t solve_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem) {
+  cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn_smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(prec), kThreads, dyn_smem);
 }
 
 cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t stream) {
   SolveArgs local = args;
   void* params[] = {&local};
-  return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, 0, stream);
+  const size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
+  cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, dyn, stream);
 }
 
 cudaError_t batch_occupancy(int prec, int* blocks_per_sm) {

@@ -335,3 +335,21 @@ def test_no_growth_right_after_a_rejection_matches_oracle():
         assert tau2 == pytest.approx(ref2.tau_next, rel=1e-4)
         if acc2:
             assert tau2 <= tau1
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[2], CASES[1]], ids=[IDS[0], IDS[2], IDS[1]])
+def test_smem_window_gives_the_same_bits(case):
+    """The shared-memory window of the float32 stencil SpMV changes where the source
+    vector is read from, not the arithmetic: stage solutions and statistics are equal
+    bit for bit with the window on and off."""
+    dim, side, L, r, pm, amp = case
+    x, b, yref = oracle_stage(case, 0.7)
+    out = []
+    for win in (1, 0):
+        with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", outer_tol=1e-11, smem_window=win) as s:
+            s.assemble(cuda(x), 0.7)
+            y, st = s.stage_solve(cuda(b))
+            out.append((y, st))
+    (y1, s1), (y0, s0) = out
+    assert torch.equal(y1, y0) and s1 == s0
+    assert np.linalg.norm(host(y1) - yref) <= 1e-8 * np.linalg.norm(yref)
