@@ -104,7 +104,7 @@ typedef struct {
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
- * smem_window = 1. */
+ * smem_window = 0. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

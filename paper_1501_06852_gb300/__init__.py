@@ -198,7 +198,7 @@ class PFCSolver:
                  outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
-                 inner_operator: int = 1, smem_window: int = 1, stream=None):
+                 inner_operator: int = 1, smem_window: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():

@@ -473,7 +473,7 @@ void pfc_default_options(pfc_options* o) {
   o->blocks_per_sm = 0;
   o->pcg_variant = 2;
   o->inner_operator = 1;
-  o->smem_window = 1;
+  o->smem_window = 0;
 }
 
 const char* pfc_status_string(int s) {
