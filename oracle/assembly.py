@@ -9,6 +9,13 @@ Definitions (Section 3, the block matrices below Eq. 3.4):
 * nonlinear mass N(psi)_ij = (-3 psi^2 phi_j, phi_i)
 * load vector   l(u)_i = (u, phi_i), used with u = psi^3 in the stage right-hand side.
 
+PFC1 (mobility psi^+ = psi - psi_min, Eq. 2.3 and the matrices of Eq. 3.10):
+
+* mobility stiffness  K_+(psi)_ij = (psi^+ grad phi_j, grad phi_i)
+* mobility derivative F(mu)_ij   = (phi_j grad mu, grad phi_i)
+* mobility load       k(psi, mu)_i = (psi^+ grad mu, grad phi_i) = (K_+(psi) mu)_i, assembled
+  directly (one integrand, no matrix) so that tests can pin K_+ and F against it.
+
 Each element integral is evaluated with the collapsed Gauss rule of
 ``quadrature.simplex_rule`` after the affine map x = X0 + J xi; gradients follow
 the chain rule grad_x = J^{-T} grad_xi.  The default rule has 5 points per
@@ -77,6 +84,22 @@ def element_nonlinear_mass(mesh: Mesh, ref: Reference, psi: np.ndarray, sl=slice
     return np.einsum("e,q,eq,qa,qb->eab", det, ref.w, coef, ref.phi, ref.phi, optimize=True)
 
 
+def element_mobility_stiffness(mesh: Mesh, ref: Reference, coef: np.ndarray, sl=slice(None)) -> np.ndarray:
+    """(c grad phi_b, grad phi_a) for c the P2 function with coefficients coef."""
+    det, inv = _geometry(mesh.elem_verts[sl])
+    gx = np.einsum("eji,qaj->eqai", inv, ref.dphi, optimize=True)
+    c_q = coef[mesh.elem_dofs[sl]] @ ref.phi.T                   # [E, Q]
+    return np.einsum("e,q,eq,eqai,eqbi->eab", det, ref.w, c_q, gx, gx, optimize=True)
+
+
+def element_mobility_derivative(mesh: Mesh, ref: Reference, mu: np.ndarray, sl=slice(None)) -> np.ndarray:
+    """Row a, column b: (phi_b grad mu, grad phi_a)."""
+    det, inv = _geometry(mesh.elem_verts[sl])
+    gx = np.einsum("eji,qaj->eqai", inv, ref.dphi, optimize=True)   # [E, Q, nl, d]
+    gmu = np.einsum("ea,eqai->eqi", mu[mesh.elem_dofs[sl]], gx, optimize=True)
+    return np.einsum("e,q,eqi,eqai,qb->eab", det, ref.w, gmu, gx, ref.phi, optimize=True)
+
+
 def _chunks(mesh: Mesh):
     e = mesh.elem_dofs.shape[0]
     for s in range(0, e, _CHUNK):
@@ -109,6 +132,34 @@ def load_cubed(mesh: Mesh, psi: np.ndarray, ref: Reference | None = None) -> np.
         det, _ = _geometry(mesh.elem_verts[s])
         psi_q = psi[mesh.elem_dofs[s]] @ ref.phi.T
         le = np.einsum("e,q,eq,qa->ea", det, ref.w, psi_q ** 3, ref.phi, optimize=True)
+        np.add.at(out, mesh.elem_dofs[s].ravel(), le.ravel())
+    return out
+
+
+def mobility_stiffness(mesh: Mesh, psi_plus: np.ndarray, ref: Reference | None = None) -> sp.csr_matrix:
+    """K_+(psi) = ((psi^+ grad phi_j, grad phi_i)) for psi^+ given by its P2 coefficients."""
+    ref = ref or Reference(mesh.dim)
+    return _to_csr(mesh, ((mesh.elem_dofs[s], element_mobility_stiffness(mesh, ref, psi_plus, s))
+                          for s in _chunks(mesh)))
+
+
+def mobility_derivative(mesh: Mesh, mu: np.ndarray, ref: Reference | None = None) -> sp.csr_matrix:
+    """F(mu) = ((phi_j grad mu, grad phi_i)): the derivative of K_+(psi) mu in psi."""
+    ref = ref or Reference(mesh.dim)
+    return _to_csr(mesh, ((mesh.elem_dofs[s], element_mobility_derivative(mesh, ref, mu, s))
+                          for s in _chunks(mesh)))
+
+
+def mobility_load(mesh: Mesh, psi_plus: np.ndarray, mu: np.ndarray, ref: Reference | None = None) -> np.ndarray:
+    """k_i = (psi^+ grad mu, grad phi_i), integrated directly."""
+    ref = ref or Reference(mesh.dim)
+    out = np.zeros(mesh.n)
+    for s in _chunks(mesh):
+        det, inv = _geometry(mesh.elem_verts[s])
+        gx = np.einsum("eji,qaj->eqai", inv, ref.dphi, optimize=True)
+        gmu = np.einsum("ea,eqai->eqi", mu[mesh.elem_dofs[s]], gx, optimize=True)
+        c_q = psi_plus[mesh.elem_dofs[s]] @ ref.phi.T
+        le = np.einsum("e,q,eq,eqi,eqai->ea", det, ref.w, c_q, gmu, gx, optimize=True)
         np.add.at(out, mesh.elem_dofs[s].ravel(), le.ravel())
     return out
 

@@ -1,4 +1,4 @@
-"""Ros3Pw Rosenbrock stages for the PFC2 model, step combination and step control.
+"""Ros3Pw Rosenbrock stages for the PFC2 and PFC1 models, step combination and step control.
 
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
@@ -22,6 +22,17 @@ multiplied by tau:
     b0 = -M mu_i + (1+r) M psi_i - 2 K psi_i - K omega_i + l(psi_i^3)
     b1 = -tau K mu_i + sum_{j<i} c_ij M dpsi_j
     b2 = -M omega_i - K psi_i
+
+For the PFC1 model (Wasserstein flow, Eq. 2.3, mobility psi^+ = psi - psi_min with
+psi_min = -1.5) the second block row of Eq. (3.10) becomes
+
+    [tau K_+(psi_k), M / gamma + tau F(mu_k), 0],   b1 = -tau K_+(psi_i) mu_i + sum_{j<i} c_ij M dpsi_j
+
+(K_+ and F as in ``assembly``).  Readings: psi^+ is psi - psi_min without clipping
+(the Jacobian of Section 3.1 is taken under that assumption), and the preconditioner
+uses the constant-mobility approximation K_+ ~ M0 K of Section 4 with M0 the mean of
+psi_k^+ over the domain and F dropped: P_CH is built as for PFC2 with tau replaced by
+M0 tau.
 
 Reading of Table 1 (garbled): the diagonal entries "a22", "a33", "c11", "c22",
 "c33" of the printed table are stage-time sums of the standard form and are not
@@ -93,13 +104,16 @@ def rosenbrock_ode_step(f, jac, x: np.ndarray, tau: float, coef: Ros3Pw = ROS3PW
 
 @dataclass
 class PFCProblem:
-    """Mesh, constant matrices and parameters of one PFC2 simulation."""
+    """Mesh, constant matrices and parameters of one PFC simulation (model 2: PFC2,
+    mobility 1; model 1: PFC1, mobility psi - psi_min)."""
 
     mesh: Mesh
     r: float
     M: sp.csr_matrix = None
     K: sp.csr_matrix = None
     ref: assembly.Reference = None
+    model: int = 2
+    psi_min: float = -1.5
 
     def __post_init__(self):
         self.ref = self.ref or assembly.Reference(self.mesh.dim)
@@ -121,10 +135,27 @@ class PFCProblem:
         N = assembly.nonlinear_mass(self.mesh, psi_k, self.ref)
         return (-(1.0 + self.r) * self.M + 2.0 * self.K + N).tocsr()
 
-    def stage_matrix(self, psi_k: np.ndarray, tau: float, coef: Ros3Pw = ROS3PW) -> sp.csr_matrix:
+    def kplus(self, psi: np.ndarray) -> sp.csr_matrix:
+        """K_+(psi): K for PFC2, the mobility stiffness of psi - psi_min for PFC1."""
+        if self.model == 2:
+            return self.K
+        return assembly.mobility_stiffness(self.mesh, psi - self.psi_min, self.ref)
+
+    def m0(self, psi: np.ndarray) -> float:
+        """Mean mobility <psi^+> = (1^T M psi) / (1^T M 1) - psi_min (PFC1); 1 for PFC2."""
+        if self.model == 2:
+            return 1.0
+        one = np.ones(self.n)
+        return float(one @ (self.M @ psi)) / float(one @ (self.M @ one)) - self.psi_min
+
+    def stage_matrix(self, psi_k: np.ndarray, tau: float, coef: Ros3Pw = ROS3PW,
+                     mu_k: np.ndarray | None = None) -> sp.csr_matrix:
         M, K = self.M, self.K
+        a11 = M / coef.gamma
+        if self.model == 1:
+            a11 = a11 + tau * assembly.mobility_derivative(self.mesh, mu_k, self.ref)
         return sp.bmat([[M, self.a01(psi_k), K],
-                        [tau * K, M / coef.gamma, None],
+                        [tau * self.kplus(psi_k), a11, None],
                         [None, K, M]], format="csr")
 
     def stage_rhs(self, x_i: np.ndarray, dpsi_prev: list, c_row: list, tau: float) -> np.ndarray:
@@ -133,7 +164,7 @@ class PFCProblem:
         mu, psi, om = self.split(x_i)
         b0 = -(M @ mu) + (1.0 + r) * (M @ psi) - 2.0 * (K @ psi) - K @ om \
             + assembly.load_cubed(self.mesh, psi, self.ref)
-        b1 = -tau * (K @ mu)
+        b1 = -tau * (self.kplus(psi) @ mu)
         for cij, dpsi in zip(c_row, dpsi_prev):
             b1 = b1 + cij * (M @ dpsi)
         b2 = -(M @ om) - K @ psi
@@ -141,8 +172,10 @@ class PFCProblem:
 
     # --- stage solve (Section 4, Section 7) --------------------------------
     def stage_solve(self, A: sp.csr_matrix, b: np.ndarray, tau: float, tol: float = 1e-13,
-                    inner: str = "pcg", restart: int = 30, max_outer: int = 2000, coef: Ros3Pw = ROS3PW):
-        pc = PCH(self.M, self.K, tau, coef.gamma, inner=inner)
+                    inner: str = "pcg", restart: int = 30, max_outer: int = 2000, coef: Ros3Pw = ROS3PW,
+                    m0: float = 1.0):
+        """FGMRES with P_CH; m0 is the mean mobility of the constant-mobility approximation."""
+        pc = PCH(self.M, self.K, m0 * tau, coef.gamma, inner=inner)
         y, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
         st.inner = pc.log
         return y, st
@@ -211,18 +244,19 @@ class StepResult:
 def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = StepControl(),
              tol: float = 1e-13, inner: str = "pcg", coef: Ros3Pw = ROS3PW,
              prev_rejected: bool = False) -> StepResult:
-    """One attempted Ros3Pw step (Eq. 3.6, 3.7, 3.12) with the error estimate.
+    """One attempted Ros3Pw step (Eq. 3.6, 3.7, 3.10) with the error estimate.
 
     The matrix N(psi) is frozen at psi^k for all three stages (W-method).
     ``prev_rejected``: the previous attempt was rejected (no growth after it)."""
     n = prob.n
-    psi_k = prob.split(x_k)[1]
-    A = prob.stage_matrix(psi_k, tau, coef)
+    mu_k, psi_k, _ = prob.split(x_k)
+    A = prob.stage_matrix(psi_k, tau, coef, mu_k=mu_k)
+    m0 = prob.m0(psi_k)
     ys, rhs, stats = [], [], []
     for i in range(3):
         x_i = x_k + sum(coef.a(i, j) * ys[j] for j in range(i))
         b = prob.stage_rhs(x_i, [y[n:2 * n] for y in ys], [coef.c(i, j) for j in range(i)], tau)
-        y, st = prob.stage_solve(A, b, tau, tol=tol, inner=inner, coef=coef)
+        y, st = prob.stage_solve(A, b, tau, tol=tol, inner=inner, coef=coef, m0=m0)
         ys.append(y)
         rhs.append(b)
         stats.append(st)
@@ -238,10 +272,11 @@ def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = S
 
 # --- linearised semi-implicit Euler (Section 3, Eq. 3.3-3.4) -----------------------
 def euler_matrix(prob: PFCProblem, psi_k: np.ndarray, tau: float) -> sp.csr_matrix:
-    """A of the linearised semi-implicit Euler step for PFC2 (K_+ = K):
-    [[M, -(1+r) M + N(psi_k) + 2 K, K], [tau K, M, 0], [0, K, M]]."""
+    """A of the linearised semi-implicit Euler step (Eq. 3.4):
+    [[M, -(1+r) M + N(psi_k) + 2 K, K], [tau K_+(psi_k), M, 0], [0, K, M]]
+    (K_+ = K for PFC2; the mobility is taken at psi_k, as in Eq. 3.3)."""
     M, K = prob.M, prob.K
-    return sp.bmat([[M, prob.a01(psi_k), K], [tau * K, M, None], [None, K, M]], format="csr")
+    return sp.bmat([[M, prob.a01(psi_k), K], [tau * prob.kplus(psi_k), M, None], [None, K, M]], format="csr")
 
 
 def euler_rhs(prob: PFCProblem, psi_k: np.ndarray) -> np.ndarray:
@@ -256,7 +291,7 @@ def euler_step(prob: PFCProblem, x_k: np.ndarray, tau: float, tol: float = 1e-13
     psi_k = prob.split(x_k)[1]
     A = euler_matrix(prob, psi_k, tau)
     b = euler_rhs(prob, psi_k)
-    pc = PCH(prob.M, prob.K, tau, 1.0, inner=inner)
+    pc = PCH(prob.M, prob.K, prob.m0(psi_k) * tau, 1.0, inner=inner)
     x, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
     st.inner = pc.log
     return x, st
