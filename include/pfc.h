@@ -86,6 +86,18 @@ typedef struct {
                          sides) into shared memory once per product, when that window fits
                          without lowering the grid's residency; 0: stencil reads go to
                          global memory.  Same results bit for bit either way. */
+  int model;          /* 2: PFC2, the H^-1 gradient flow of Eq. (2.2) (mobility 1);
+                         1: PFC1, the Wasserstein flow of Eq. (2.3) with mobility
+                         psi^+ = psi - psi_min: the second block row of the stage
+                         system (Eq. 3.10) becomes [tau K_+(psi_k), M / gamma +
+                         tau F(mu_k), 0] with K_+(psi) = ((psi^+ grad phi_j, grad phi_i))
+                         and F(mu) = ((phi_j grad mu, grad phi_i)), b1 uses
+                         -tau K_+(psi_i) mu_i, and P_CH takes the constant-mobility
+                         approximation K_+ ~ M0 K of Section 4, M0 = <psi_k^+>
+                         (its assembly reads M0 back: one extra synchronisation).
+                         The Euler system keeps the mobility explicit:
+                         [tau K_+(psi_k), M, 0]. */
+  double psi_min;     /* PFC1: lower bound psi_min of the density (-1.5, Section 2) */
 } pfc_options;
 
 typedef struct {
@@ -104,7 +116,7 @@ typedef struct {
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
- * smem_window = 0. */
+ * smem_window = 0, model = 2, psi_min = -1.5. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

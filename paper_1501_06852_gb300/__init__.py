@@ -37,7 +37,9 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("step_atol", ctypes.c_double), ("step_rtol", ctypes.c_double),
                 ("tau_max", ctypes.c_double), ("blocks_per_sm", ctypes.c_int), ("pcg_variant", ctypes.c_int),
                 ("inner_operator", ctypes.c_int),
-                ("smem_window", ctypes.c_int)]
+                ("smem_window", ctypes.c_int),
+                ("model", ctypes.c_int),
+                ("psi_min", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -198,7 +200,8 @@ class PFCSolver:
                  outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
-                 inner_operator: int = 1, smem_window: int = 0, stream=None):
+                 inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
+                 stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -215,6 +218,8 @@ class PFCSolver:
         o.pcg_variant = pcg_variant
         o.inner_operator = inner_operator
         o.smem_window = smem_window
+        o.model = model
+        o.psi_min = psi_min
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -92,6 +92,12 @@ struct pfc_ctx {
   bool last_rejected = false;   // the previous pfc_step attempt was rejected
   double tau = 0.0, delta = 0.0;
   double gamma = kGamma;        // scaling of the (1,1) block: Ros3Pw gamma, or 1 for the Euler system
+  // PFC1 (model 1): second block row A10 = tau K_+(psi_k), A11 = M / gamma + tau F(mu_k),
+  // the element mobility tensor, int phi_j per row, and the mean mobility M0
+  int model = 2;
+  double psi_min = -1.5;
+  double m0 = 1.0;
+  double *A10v = nullptr, *A11v = nullptr, *mob = nullptr, *wint = nullptr;
   // batched launches: this instance's warp slice ranges for a segment of blk_b_G blocks
   std::vector<long long> slice_cost_prefix;   // host, nslices + 1
   int* blk_b = nullptr;                       // device, G * W + 1
@@ -138,6 +144,8 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.Mv = c->Mv;
   a.Kv = c->Kv;
   a.Av = c->Av;
+  a.A10 = c->model == 1 ? c->A10v : nullptr;
+  a.A11 = c->model == 1 ? c->A11v : nullptr;
   if (prec == 0) {
     a.iM = c->Mv;
     a.iK = c->Kv;
@@ -158,7 +166,7 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.tau = c->tau;
   a.gamma = c->gamma;
   a.inv_gamma = 1.0 / c->gamma;
-  a.tau_e = c->gamma * c->tau;
+  a.tau_e = c->gamma * c->tau * c->m0;  // PFC1: constant-mobility approximation K_+ ~ M0 K
   a.inv_delta = c->delta > 0 ? 1.0 / c->delta : 0.0;
   a.tol = c->opt.outer_tol;
   a.inner_rtol = c->opt.inner_rtol;
@@ -242,24 +250,57 @@ void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
   for (int k = 0; k < 8; ++k) s->phase_ms[k] = d.prof_ns[k] * 1e-6;
 }
 
+// b^R from the stage value c->xi and (when with_d) d = sum c_ij dpsi_j in c->dvec:
+// element loads (psi_i^3, phi) and, for PFC1, (psi_i^+ grad mu_i, grad phi), then
+// the row kernel.
+pfc_status rhs_at_stage(pfc_ctx* c, bool with_d) {
+  const int np = c->n_pad;
+  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+  double* lbuf2 = nullptr;
+  if (c->model == 1) {
+    lbuf2 = c->ebuf + (size_t)c->nl * c->E;
+    LAUNCH(pfc::launch_elem_mobload(c->dim, c->E, c->ntypes, c->elem, c->xi + np, c->xi, c->psi_min, c->mob, lbuf2,
+                                    c->stream));
+  }
+  LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
+                         with_d ? c->dvec : nullptr, c->opt.r, c->tau, lbuf2, c->bv, c->stream));
+  return PFC_OK;
+}
+
 // b_i^R for stage nprev from c->xi (stage value) and the increments c->ys.
 pfc_status stage_rhs_internal(pfc_ctx* c, int nprev) {
   const int np = c->n_pad;
   const double c0 = nprev > 0 ? kC[nprev][0] : 0.0, c1 = nprev > 1 ? kC[nprev][1] : 0.0;
   if (nprev > 0) LAUNCH(pfc::launch_combine_field(np, c->ys + np, c0, nprev > 1 ? c->ys + 3 * np + np : nullptr, c1, c->dvec, c->stream));
-  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
-  LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
-                     nprev > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
-  return PFC_OK;
+  return rhs_at_stage(c, nprev > 0);
 }
 
-pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma) {
+// with_f: the Rosenbrock matrix (A11 = M / gamma + tau F(mu_k)); false for the Euler
+// system, whose mobility is explicit (A11 = M).
+pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma, bool with_f = true) {
   const int np = c->n_pad;
   LAUNCH(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
   c->tau = tau;
   c->gamma = gamma;
-  c->delta = std::sqrt(gamma * tau);
+  c->m0 = 1.0;
+  if (c->model == 1) {
+    // M0 = <psi_k^+> = (sum_j int phi_j psi_j) / |Omega| - psi_min
+    const int parts = pfc::step_partials();
+    LAUNCH(pfc::launch_dot_partials(np, c->wint, c->xk + np, c->step_part, parts, c->stream));
+    LAUNCH(pfc::launch_sum_partials(parts, c->step_part, 1.0, c->err_scalar + 1, c->stream));
+    CK(cudaMemcpyAsync(c->h_err + 1, c->err_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const double omega = std::pow(c->length, c->dim);
+    c->m0 = c->h_err[1] / omega - c->psi_min;
+    if (!(c->m0 > 0.0) || !std::isfinite(c->m0))
+      return fail(c, PFC_ERR_INVALID, "PFC1: the mean mobility <psi - psi_min> must be positive");
+    LAUNCH(pfc::launch_elem_mobility(c->dim, c->E, c->ntypes, c->elem, c->xk + np, c->xk, c->psi_min, c->mob, c->ebuf,
+                                     c->stream));
+    LAUNCH(pfc::launch_assemble_mob(c->dim, c->nnz_sell, c->cptr, c->cidx, c->cols, c->elem, c->E, c->ebuf, c->Mv, tau,
+                                    1.0 / gamma, with_f ? 1 : 0, c->A10v, c->A11v, c->stream));
+  }
+  c->delta = std::sqrt(gamma * tau * c->m0);
   const double sdelta = std::sqrt(c->delta);
   LAUNCH(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
                             c->stream));
@@ -474,6 +515,8 @@ void pfc_default_options(pfc_options* o) {
   o->pcg_variant = 2;
   o->inner_operator = 1;
   o->smem_window = 0;
+  o->model = 2;
+  o->psi_min = -1.5;
 }
 
 const char* pfc_status_string(int s) {
@@ -540,6 +583,10 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "inner_operator must be 0 or 1"));
   if (c->opt.smem_window < 0 || c->opt.smem_window > 1)
     return bail(fail(c, PFC_ERR_INVALID, "smem_window must be 0 or 1"));
+  if ((c->opt.model != 1 && c->opt.model != 2) || !std::isfinite(c->opt.psi_min))
+    return bail(fail(c, PFC_ERR_INVALID, "model must be 1 (PFC1) or 2 (PFC2) and psi_min finite"));
+  c->model = c->opt.model;
+  c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
     return bail(fail(c, PFC_ERR_INVALID, "tolerances must be > 0 and iteration caps >= 1"));
   c->stream = (cudaStream_t)cuda_stream;
@@ -688,7 +735,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
                o_xnew = L.take(sizeof(double) * np3), o_tmp3 = L.take(sizeof(double) * np3);
   const size_t o_dvec = L.take(sizeof(double) * c->n_pad), o_lvec = L.take(sizeof(double) * c->n_pad),
                o_tmpn = L.take(sizeof(double) * c->n_pad);
-  const size_t o_ebuf = L.take(sizeof(double) * (size_t)c->np * c->E);
+  // element buffer: N(psi) pair values (PFC2); PFC1 needs 3 values per pair
+  const size_t o_ebuf = L.take(sizeof(double) * (size_t)c->np * c->E * (c->model == 1 ? 3 : 1));
   const size_t o_V = L.take(sizeof(double) * np3 * (c->opt.restart + 1));
   const size_t o_Z = L.take(sizeof(double) * np3 * c->opt.restart);
   const size_t o_ivec = L.take((size_t)pfc::kInnerVecs * c->n_pad * 8);
@@ -699,6 +747,13 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);
   const size_t o_sp = L.take(sizeof(double) * pfc::step_partials());
   const size_t o_es = L.take(sizeof(double) * 2);
+  size_t o_a10 = 0, o_a11 = 0, o_mob = 0;
+  if (c->model == 1) {
+    o_a10 = L.take(sizeof(double) * S.nnz_sell);
+    o_a11 = L.take(sizeof(double) * S.nnz_sell);
+    o_mob = L.take(sizeof(double) * S.ref.mob.size());
+  }
+  const size_t o_wint = L.take(sizeof(double) * c->n_pad);
   c->arena_bytes = L.take(0);
   {
     cudaError_t e = cudaMalloc((void**)&c->arena, c->arena_bytes);
@@ -764,6 +819,12 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->stats = (pfc::DevStats*)(A + o_stats);
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);
+  c->wint = (double*)(A + o_wint);
+  if (c->model == 1) {
+    c->A10v = (double*)(A + o_a10);
+    c->A11v = (double*)(A + o_a11);
+    c->mob = (double*)(A + o_mob);
+  }
   {
     cudaError_t e = cudaMallocHost((void**)&c->h_stats, sizeof(pfc::DevStats) * 4 + sizeof(double) * 2 + sizeof(int) * 8 +
                                                          sizeof(int) * blk.size());
@@ -814,14 +875,21 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
       std::vector<double> unit(S.ref.quartic.size());
       for (size_t q = 0; q < unit.size(); ++q) unit[q] = S.ref.quartic[q] / S.ref.vol;
       CK_SETUP(pfc::upload_quartic(dim, unit.data(), S.ref.npairs));
+      CK_SETUP(pfc::upload_pairs(dim, S.ref.pair_j.data(), S.ref.npairs));
       g_const_done[di][c->device] = true;
     }
   }
   CK_SETUP(cudaMemsetAsync(A + vec_begin, 0, vec_end - vec_begin, c->stream));
   CK_SETUP(cudaMemsetAsync(A + o_arr, 0, c->arena_bytes - o_arr, c->stream));
+  // the mobility tensor lies in the zeroed tail: upload it after, on the same stream
+  if (c->model == 1)
+    CK_SETUP(cudaMemcpyAsync(c->mob, S.ref.mob.data(), sizeof(double) * S.ref.mob.size(), cudaMemcpyHostToDevice,
+                             c->stream));
   CK_SETUP(pfc::launch_assemble_mk(c->nnz_sell, c->cptr, c->cidx, c->E, c->ntypes, c->np, c->mass_tab, c->stiff_tab,
                                    c->Mv, c->Kv, c->stream));
   CK_SETUP(pfc::launch_diag_inv(c->n_pad, c->diag, c->Mv, c->dM, c->prec ? c->fdM : nullptr, c->stream));
+  // int phi_j = row sums of M (padding rows: 0), for the mean mobility of PFC1
+  CK_SETUP(pfc::launch_row_sums(c->nslices, c->slice_ptr, c->Mv, c->wint, c->stream));
   if (c->prec) {
     CK_SETUP(pfc::launch_convert(c->prec, c->nnz_sell, c->Mv, c->iM, c->stream));
     CK_SETUP(pfc::launch_convert(c->prec, c->nnz_sell, c->Kv, c->iK, c->stream));
@@ -893,9 +961,8 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
     LAUNCH(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1], c->xi,
                                  c->dvec, c->stream));
     // d = sum_j c_ij dpsi_j comes from stage_combine; the RHS kernel reads it
-    LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
-    LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
-                       i > 0 ? c->dvec : nullptr, c->opt.r, c->tau, c->bv, c->stream));
+    st = rhs_at_stage(c, i > 0);
+    if (st != PFC_OK) return st;
     pfc::SolveArgs a = base_args(c, c->prec);
     a.mode = 0;
     a.b = c->bv;
@@ -943,7 +1010,7 @@ pfc_status pfc_euler_step(pfc_ctx* c, double* state, double tau, pfc_solve_stats
   const int np = c->n_pad;
   LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
   // A of Eq. (3.4): the stage matrix with gamma = 1, A01 = -(1+r) M + N(psi_k) + 2 K
-  st = assemble_internal(c, tau, 1.0);
+  st = assemble_internal(c, tau, 1.0, false);
   if (st != PFC_OK) return st;
   LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_euler_rhs(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->dptr, c->didx, c->ebuf, c->xk + np,
@@ -1018,7 +1085,8 @@ pfc_status pfc_apply(pfc_ctx* c, int op, const double* x, double* y) {
     LAUNCH(pfc::launch_scatter_out(c->n, np, 1, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_AR) {
     LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, x, c->tmp3, c->stream));
-    LAUNCH(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / c->gamma, c->tmp3,
+    LAUNCH(pfc::launch_spmv_ar(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->Kv, c->Av, c->tau, 1.0 / c->gamma,
+                               c->model == 1 ? c->A10v : nullptr, c->model == 1 ? c->A11v : nullptr, c->tmp3,
                            c->xnew, c->stream));
     LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, y, c->stream));
   } else if (op == PFC_OP_PCH) {
@@ -1154,9 +1222,8 @@ pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states
       const size_t np3 = 3 * (size_t)np;
       LAUNCH(pfc::launch_stage_combine(np, ck->xk, ck->ys, ck->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1],
                                        ck->xi, ck->dvec, ck->stream));
-      LAUNCH(pfc::launch_elem_load(ck->dim, ck->E, ck->elem, ck->xi + np, ck->vol, ck->ebuf, ck->stream));
-      LAUNCH(pfc::launch_rhs(ck->nslices, ck->slice_ptr, ck->cols, ck->Mv, ck->Kv, ck->dptr, ck->didx, ck->ebuf, ck->xi,
-                             i > 0 ? ck->dvec : nullptr, ck->opt.r, ck->tau, ck->bv, ck->stream));
+      st = rhs_at_stage(ck, i > 0);
+      if (st != PFC_OK) return st;
     }
     c = ctxs[0];
     st = run_batch(ctxs, count, i, false, space, (size_t)i * region);

@@ -39,6 +39,8 @@ struct SolveArgs {
   const double* Mv;        // float64 M, K, A01 values (outer operator A^R)
   const double* Kv;
   const double* Av;
+  const double* A10;       // PFC1: tau K_+(psi_k) and M / gamma + tau F(mu_k) (second block row); PFC2: null
+  const double* A11;
   const void* iM;          // inner values M, K, M + delta K, M + sqrt(delta) K
   const void* iK;
   const void* iMdK;

@@ -23,6 +23,7 @@ struct RefTensors {
   std::vector<double> mass;                  // ntypes x npairs: int phi_i phi_j
   std::vector<double> stiff;                 // ntypes x npairs: int grad phi_i . grad phi_j
   std::vector<double> quartic;               // npairs(ab) x npairs(ij): w_ab int phi_a phi_b phi_i phi_j, w_ab = 2 (a != b), 1
+  std::vector<double> mob;                   // ntypes x nl x nl x nl: int phi_a grad phi_b . grad phi_c (physical)
 };
 
 // Structured mesh, P2 dofs, SELL-C-sigma pattern and the maps the assembly

@@ -19,6 +19,9 @@ namespace {
 
 __constant__ double c_quart2[21 * 21];
 __constant__ double c_quart3[55 * 55];
+// second node of unordered local pair p = (i <= j), per dimension
+__constant__ int c_pair_j2[21];
+__constant__ int c_pair_j3[55];
 
 constexpr int kBlock = 256;
 
@@ -135,6 +138,128 @@ __global__ void k_assemble_a01(long long nnz, const int* __restrict__ cptr, cons
   }
 }
 
+// ---------------------------------------------------------------- PFC1 mobility
+// T = mob + t * NL^3 holds int phi_a grad phi_b . grad phi_c over an element of
+// type t (t = e mod ntypes: elements are stored cell-major, types inner).
+//
+// Per element and unordered local pair p = (i <= j):
+//   ebuf[(3p)   E + e] = (psi^+ grad phi_j, grad phi_i)      -> K_+(psi)
+//   ebuf[(3p+1) E + e] = (phi_j grad mu, grad phi_i)         -> F(mu), row node i
+//   ebuf[(3p+2) E + e] = (phi_i grad mu, grad phi_j)         -> F(mu), row node j
+template <int NL>
+__global__ void __launch_bounds__(128) k_elem_mobility(int E, int ntypes, const int* __restrict__ elem,
+                                                        const double* __restrict__ psi, const double* __restrict__ mu,
+                                                        double psi_min, const double* __restrict__ mob, double* ebuf) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const double* T = mob + (size_t)(e % ntypes) * NL * NL * NL;
+    double pp[NL], mm[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int d = __ldg(elem + (size_t)l * E + e);
+      pp[l] = psi[d] - psi_min;
+      mm[l] = mu[d];
+    }
+    int p = 0;
+#pragma unroll 1
+    for (int i = 0; i < NL; ++i) {
+#pragma unroll 1
+      for (int j = i; j < NL; ++j) {
+        double kp = 0.0, fij = 0.0, fji = 0.0;
+#pragma unroll
+        for (int a = 0; a < NL; ++a) {
+          kp = fma(pp[a], __ldg(T + ((size_t)a * NL + i) * NL + j), kp);
+          fij = fma(mm[a], __ldg(T + ((size_t)j * NL + a) * NL + i), fij);
+          fji = fma(mm[a], __ldg(T + ((size_t)i * NL + a) * NL + j), fji);
+        }
+        ebuf[(size_t)(3 * p) * E + e] = kp;
+        ebuf[(size_t)(3 * p + 1) * E + e] = fij;
+        ebuf[(size_t)(3 * p + 2) * E + e] = fji;
+        ++p;
+      }
+    }
+  }
+}
+
+// lbuf[l E + e] = (psi^+ grad mu, grad phi_l) over element e
+template <int NL>
+__global__ void __launch_bounds__(128) k_elem_mobload(int E, int ntypes, const int* __restrict__ elem,
+                                                       const double* __restrict__ psi, const double* __restrict__ mu,
+                                                       double psi_min, const double* __restrict__ mob, double* lbuf) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const double* T = mob + (size_t)(e % ntypes) * NL * NL * NL;
+    double pp[NL], mm[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int d = __ldg(elem + (size_t)l * E + e);
+      pp[l] = psi[d] - psi_min;
+      mm[l] = mu[d];
+    }
+#pragma unroll 1
+    for (int c = 0; c < NL; ++c) {
+      double s = 0.0;
+#pragma unroll 1
+      for (int a = 0; a < NL; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int b = 0; b < NL; ++b) t = fma(mm[b], __ldg(T + ((size_t)a * NL + b) * NL + c), t);
+        s = fma(pp[a], t, s);
+      }
+      lbuf[(size_t)c * E + e] = s;
+    }
+  }
+}
+
+// A10 = tau K_+(psi_k), A11 = M / gamma + tau F(mu_k) (F only when with_f) on every
+// slot: for a contribution of pair p = (i, j) of element e, the slot's column is
+// node j (then the slot's row is node i) or node i.
+template <int NL>
+__global__ void k_assemble_mob(long long nnz, const int* __restrict__ cptr, const int* __restrict__ cidx,
+                               const int* __restrict__ cols, const int* __restrict__ elem, int E,
+                               const double* __restrict__ ebuf, const double* __restrict__ Mv, double tau,
+                               double inv_gamma, int with_f, double* A10, double* A11) {
+  const int* pj = NL == 6 ? c_pair_j2 : c_pair_j3;
+  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nnz; s += (long long)gridDim.x * blockDim.x) {
+    const int col = cols[s];
+    double kp = 0.0, f = 0.0;
+    for (int c = cptr[s]; c < cptr[s + 1]; ++c) {
+      const int idx = cidx[c];
+      const int p = idx / E;
+      const int e = idx - p * E;
+      kp += ebuf[(size_t)(3 * p) * E + e];
+      if (with_f) {
+        const int nj = __ldg(elem + (size_t)pj[p] * E + e);
+        f += ebuf[(size_t)(3 * p + (nj == col ? 1 : 2)) * E + e];
+      }
+    }
+    A10[s] = tau * kp;
+    A11[s] = inv_gamma * Mv[s] + tau * f;
+  }
+}
+
+// w[row] = sum of the row's stored values (SELL-32 slices, one warp per slice)
+__global__ void k_row_sums(int nslices, const int* __restrict__ sp, const double* __restrict__ vals, double* w) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= nslices) return;
+  double acc = 0.0;
+  for (int idx = sp[s] + lane; idx < sp[s + 1]; idx += 32) acc += vals[idx];
+  w[s * 32 + lane] = acc;
+}
+
+// partial[b] = sum over block b's strided share of a[i] * b[i] (fixed order)
+__global__ void k_dot_partials(int n, const double* __restrict__ a, const double* __restrict__ b, double* partial) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc = fma(a[i], b[i], acc);
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
 template <class TM>
 __device__ __forceinline__ TM cvt_to(double v);
 template <>
@@ -186,7 +311,8 @@ __global__ void k_diag_inv(int n_pad, const int* __restrict__ diag, const double
 __global__ void k_rhs(int nslices, int n_pad, const int* __restrict__ sp, const int* __restrict__ cols,
                       const double* __restrict__ Mv, const double* __restrict__ Kv, const int* __restrict__ dptr,
                       const int* __restrict__ didx, const double* __restrict__ lbuf, const double* __restrict__ x,
-                      const double* __restrict__ d, double r, double tau, double* b) {
+                      const double* __restrict__ d, double r, double tau, const double* __restrict__ lbuf2,
+                      double* b) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= nslices) return;
@@ -208,10 +334,14 @@ __global__ void k_rhs(int nslices, int n_pad, const int* __restrict__ sp, const 
     k_om = fma(kv, zo, k_om);
     if (d) m_d = fma(mv, d[c], m_d);
   }
-  double l = 0.0;
-  for (int q = dptr[row]; q < dptr[row + 1]; ++q) l += lbuf[didx[q]];
+  double l = 0.0, l2 = 0.0;
+  for (int q = dptr[row]; q < dptr[row + 1]; ++q) {
+    l += lbuf[didx[q]];
+    if (lbuf2) l2 += lbuf2[didx[q]];
+  }
   b[row] = -m_mu + (1.0 + r) * m_psi - 2.0 * k_psi - k_om + l;
-  b[n_pad + row] = -tau * k_mu + m_d;
+  // PFC2: -tau K mu; PFC1: -tau (psi^+ grad mu, grad phi) from the element loads
+  b[n_pad + row] = -tau * (lbuf2 ? l2 : k_mu) + m_d;
   b[2 * n_pad + row] = -m_om - k_psi;
 }
 
@@ -276,7 +406,8 @@ __global__ void k_spmv(int nslices, const int* __restrict__ sp, const int* __res
 
 __global__ void k_spmv_ar(int nslices, int n_pad, const int* __restrict__ sp, const int* __restrict__ cols,
                           const double* __restrict__ Mv, const double* __restrict__ Kv, const double* __restrict__ Av,
-                          double tau, double inv_gamma, const double* __restrict__ z, double* w) {
+                          double tau, double inv_gamma, const double* __restrict__ A10,
+                          const double* __restrict__ A11, const double* __restrict__ z, double* w) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (s >= nslices) return;
@@ -290,13 +421,14 @@ __global__ void k_spmv_ar(int nslices, int n_pad, const int* __restrict__ sp, co
     m_mu = fma(mv, zm, m_mu);
     a_psi = fma(av, zp, a_psi);
     k_om = fma(kv, zo, k_om);
-    k_mu = fma(kv, zm, k_mu);
-    m_psi = fma(mv, zp, m_psi);
+    // PFC1: the second block row is A10, A11 (see k_assemble_mob)
+    k_mu = fma(A10 ? A10[idx] : kv, zm, k_mu);
+    m_psi = fma(A11 ? A11[idx] : mv, zp, m_psi);
     k_psi = fma(kv, zp, k_psi);
     m_om = fma(mv, zo, m_om);
   }
   w[row] = m_mu + a_psi + k_om;
-  w[n_pad + row] = tau * k_mu + inv_gamma * m_psi;
+  w[n_pad + row] = A10 ? k_mu + m_psi : tau * k_mu + inv_gamma * m_psi;
   w[2 * n_pad + row] = k_psi + m_om;
 }
 
@@ -368,6 +500,21 @@ __global__ void k_reduce_partials(int nparts, const double* __restrict__ partial
   }
 }
 
+// out = scale * sum of the partials (fixed order), no square root
+__global__ void k_sum_partials(int nparts, const double* __restrict__ partial, double scale, double* out) {
+  __shared__ double sw[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[i];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (int)(blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) *out = t * scale;
+  }
+}
+
 __global__ void k_gather_in(int n, int n_pad, int nf, const int* __restrict__ perm, const double* __restrict__ lex,
                             double* internal) {
   const long long tot = (long long)nf * n_pad;
@@ -399,6 +546,57 @@ int step_partials() { return kStepParts; }
 cudaError_t upload_quartic(int dim, const double* q, int npairs) {
   const size_t bytes = sizeof(double) * npairs * npairs;
   return dim == 2 ? cudaMemcpyToSymbol(c_quart2, q, bytes) : cudaMemcpyToSymbol(c_quart3, q, bytes);
+}
+
+cudaError_t upload_pairs(int dim, const int* pair_j, int npairs) {
+  const size_t bytes = sizeof(int) * npairs;
+  return dim == 2 ? cudaMemcpyToSymbol(c_pair_j2, pair_j, bytes) : cudaMemcpyToSymbol(c_pair_j3, pair_j, bytes);
+}
+
+cudaError_t launch_elem_mobility(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+                                 double psi_min, const double* mob, double* ebuf, cudaStream_t st) {
+  if (dim == 2)
+    k_elem_mobility<6><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, ebuf);
+  else
+    k_elem_mobility<10><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, ebuf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_elem_mobload(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+                                double psi_min, const double* mob, double* lbuf, cudaStream_t st) {
+  if (dim == 2)
+    k_elem_mobload<6><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, lbuf);
+  else
+    k_elem_mobload<10><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, lbuf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const int* cidx, const int* cols,
+                                const int* elem, int E, const double* ebuf, const double* Mv, double tau,
+                                double inv_gamma, int with_f, double* A10, double* A11, cudaStream_t st) {
+  if (dim == 2)
+    k_assemble_mob<6><<<blocks_for(nnz, kBlock), kBlock, 0, st>>>(nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
+                                                                  inv_gamma, with_f, A10, A11);
+  else
+    k_assemble_mob<10><<<blocks_for(nnz, kBlock), kBlock, 0, st>>>(nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
+                                                                   inv_gamma, with_f, A10, A11);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sums(int nslices, const int* sp, const double* vals, double* w, cudaStream_t st) {
+  k_row_sums<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, sp, vals, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(int nparts, const double* partial, double scale, double* out, cudaStream_t st) {
+  k_sum_partials<<<1, 1024, 0, st>>>(nparts, partial, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_partials(int n, const double* a, const double* b, double* partial, int nparts,
+                                cudaStream_t st) {
+  k_dot_partials<<<nparts, 256, 0, st>>>(n, a, b, partial);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_mk(long long nnz, const int* cptr, const int* cidx, int E, int ntypes, int np,
@@ -459,10 +657,10 @@ cudaError_t launch_diag_inv(int n_pad, const int* diag, const double* A, double*
 
 cudaError_t launch_rhs(int nslices, const int* sp, const int* cols, const double* Mv, const double* Kv,
                        const int* dptr, const int* didx, const double* lbuf, const double* x, const double* d,
-                       double r, double tau, double* b, cudaStream_t st) {
+                       double r, double tau, const double* lbuf2, double* b, cudaStream_t st) {
   const int n_pad = nslices * 32;
   k_rhs<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, n_pad, sp, cols, Mv, Kv, dptr, didx,
-                                                                       lbuf, x, d, r, tau, b);
+                                                                       lbuf, x, d, r, tau, lbuf2, b);
   return cudaGetLastError();
 }
 
@@ -494,10 +692,10 @@ cudaError_t launch_spmv(int nslices, const int* sp, const int* cols, const doubl
 }
 
 cudaError_t launch_spmv_ar(int nslices, int n_pad, const int* sp, const int* cols, const double* Mv, const double* Kv,
-                           const double* Av, double tau, double inv_gamma, const double* z, double* w,
-                           cudaStream_t st) {
+                           const double* Av, double tau, double inv_gamma, const double* A10, const double* A11,
+                           const double* z, double* w, cudaStream_t st) {
   k_spmv_ar<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, n_pad, sp, cols, Mv, Kv, Av, tau,
-                                                                           inv_gamma, z, w);
+                                                                           inv_gamma, A10, A11, z, w);
   return cudaGetLastError();
 }
 

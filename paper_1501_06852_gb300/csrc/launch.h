@@ -33,7 +33,21 @@ cudaError_t launch_diag_inv(int n_pad, const int* diag_pos, const double* A, dou
                             cudaStream_t st);
 cudaError_t launch_rhs(int nslices, const int* slice_ptr, const int* cols, const double* Mv, const double* Kv,
                        const int* dptr, const int* didx, const double* lbuf, const double* x, const double* d,
-                       double r, double tau, double* b, cudaStream_t st);
+                       double r, double tau, const double* lbuf2, double* b, cudaStream_t st);
+// PFC1 mobility (Eq. 3.10): element values of K_+(psi) and F(mu), element loads
+// (psi^+ grad mu, grad phi), slot assembly of A10 = tau K_+ and A11 = M / gamma + tau F
+cudaError_t upload_pairs(int dim, const int* pair_j, int npairs);
+cudaError_t launch_elem_mobility(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+                                 double psi_min, const double* mob, double* ebuf, cudaStream_t st);
+cudaError_t launch_elem_mobload(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+                                double psi_min, const double* mob, double* lbuf, cudaStream_t st);
+cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const int* cidx, const int* cols,
+                                const int* elem, int E, const double* ebuf, const double* Mv, double tau,
+                                double inv_gamma, int with_f, double* A10, double* A11, cudaStream_t st);
+cudaError_t launch_row_sums(int nslices, const int* sp, const double* vals, double* w, cudaStream_t st);
+cudaError_t launch_sum_partials(int nparts, const double* partial, double scale, double* out, cudaStream_t st);
+cudaError_t launch_dot_partials(int n, const double* a, const double* b, double* partial, int nparts,
+                                cudaStream_t st);
 cudaError_t launch_euler_rhs(int nslices, int n_pad, const int* slice_ptr, const int* cols, const double* Mv,
                              const int* dptr, const int* didx, const double* lbuf, const double* psi, double* b,
                              cudaStream_t st);
@@ -46,8 +60,8 @@ cudaError_t launch_spmv_combo(int nslices, const int* slice_ptr, const int* cols
 cudaError_t launch_spmv(int nslices, const int* slice_ptr, const int* cols, const double* vals, const double* x,
                         double* y, cudaStream_t st);
 cudaError_t launch_spmv_ar(int nslices, int n_pad, const int* slice_ptr, const int* cols, const double* Mv,
-                           const double* Kv, const double* Av, double tau, double inv_gamma, const double* z,
-                           double* w, cudaStream_t st);
+                           const double* Kv, const double* Av, double tau, double inv_gamma, const double* A10,
+                           const double* A11, const double* z, double* w, cudaStream_t st);
 cudaError_t launch_stage_combine(int n_pad, const double* xk, const double* y0, const double* y1, int nprev,
                                  double a0, double a1, double c0, double c1, double* xi, double* d,
                                  cudaStream_t st);

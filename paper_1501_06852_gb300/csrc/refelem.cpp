@@ -8,7 +8,10 @@
 //     int_T lambda^e dx = |T| d! prod_k e_k! / (|e| + d)!,
 // so the mass matrix, the stiffness matrix (through grad phi = sum_k
 // d phi / d lambda_k grad lambda_k) and the quartic tensor that gives the
-// nonlinear mass N(psi)_ij = (-3 psi^2 phi_j, phi_i) are exact to rounding.
+// nonlinear mass N(psi)_ij = (-3 psi^2 phi_j, phi_i) are exact to rounding, as is
+// the mobility tensor int phi_a grad phi_b . grad phi_c of the PFC1 model, from
+// which K_+(psi) = ((psi^+ grad phi_j, grad phi_i)), F(mu) = ((phi_j grad mu,
+// grad phi_i)) and the load (psi^+ grad mu, grad phi_i) follow (Eq. 3.10).
 #include <array>
 #include <cmath>
 #include <map>
@@ -154,6 +157,17 @@ bool build_reference(int dim, double h, RefTensors& out, std::string& err) {
           D[((i * nb + k) * nl + j) * nb + l] = integrate(mul(di, dlambda(phi[j], l)), dim);
     }
 
+  // Dm[a][b][k][c][l] = int phi_a d_k phi_b d_l phi_c (unit volume)
+  std::vector<double> Dm((size_t)nl * nl * nb * nl * nb);
+  for (int a = 0; a < nl; ++a)
+    for (int b = 0; b < nl; ++b)
+      for (int k = 0; k < nb; ++k) {
+        const Poly ab = mul(phi[a], dlambda(phi[b], k));
+        for (int c = 0; c < nl; ++c)
+          for (int l = 0; l < nb; ++l)
+            Dm[((((size_t)a * nl + b) * nb + k) * nl + c) * nb + l] = integrate(mul(ab, dlambda(phi[c], l)), dim);
+      }
+  out.mob.assign((size_t)ntypes * nl * nl * nl, 0.0);
   out.mass.assign((size_t)ntypes * np, 0.0);
   out.stiff.assign((size_t)ntypes * np, 0.0);
   double vol0 = -1.0;
@@ -208,6 +222,14 @@ bool build_reference(int dim, double h, RefTensors& out, std::string& err) {
       out.stiff[(size_t)t * np + p] = vol * s;
       out.mass[(size_t)t * np + p] = vol * mref[p];
     }
+    for (int a = 0; a < nl; ++a)
+      for (int b = 0; b < nl; ++b)
+        for (int c = 0; c < nl; ++c) {
+          double s = 0.0;
+          for (int k = 0; k < nb; ++k)
+            for (int l = 0; l < nb; ++l) s += G[k][l] * Dm[((((size_t)a * nl + b) * nb + k) * nl + c) * nb + l];
+          out.mob[(((size_t)t * nl + a) * nl + b) * nl + c] = vol * s;
+        }
   }
   out.vol = vol0;
   out.quartic.resize((size_t)np * np);

@@ -13,7 +13,9 @@
 // where tau_e = gamma tau and delta = sqrt(tau_e): the preconditioner of Eq. (4.1)
 // is derived for gamma = 1, so the second block row of A^R is scaled by gamma
 // and step (2) uses the forward substitution of the lower factor of Eq. (4.1)
-// (right-hand side b1 - tau K y0).  Every inner solve is Jacobi-PCG from zero
+// (right-hand side b1 - tau K y0).  For PFC1 the second block row of A^R is
+// [tau K_+(psi_k), M / gamma + tau F(mu_k), 0] (assembled A10, A11), and P_CH uses
+// the constant-mobility approximation K_+ ~ M0 K of Section 4: tau_e = gamma M0 tau.  Every inner solve is Jacobi-PCG from zero
 // to ||r|| <= inner_rtol ||rhs|| (Table 2).
 //
 // GB300 design.  The grid is co-resident (cooperative launch, a multiple of the
@@ -1040,13 +1042,14 @@ __device__ __forceinline__ void block_row(const SolveArgs& a, const double* z, i
     m_mu = fma(mv, zm, m_mu);
     a_psi = fma(av, zp, a_psi);
     k_om = fma(kv, zo, k_om);
-    k_mu = fma(kv, zm, k_mu);
-    m_psi = fma(mv, zp, m_psi);
+    k_mu = fma(a.A10 ? __ldg(a.A10 + idx) : kv, zm, k_mu);
+    m_psi = fma(a.A11 ? __ldg(a.A11 + idx) : mv, zp, m_psi);
     k_psi = fma(kv, zp, k_psi);
     m_om = fma(mv, zo, m_om);
   }
   w0 = m_mu + a_psi + k_om;
-  w1 = a.tau * k_mu + a.inv_gamma * m_psi;
+  // PFC1: the second block row is [tau K_+(psi_k), M / gamma + tau F(mu_k)], stored
+  w1 = a.A10 ? k_mu + m_psi : a.tau * k_mu + a.inv_gamma * m_psi;
   w2 = k_psi + m_om;
 }
 
