@@ -54,7 +54,9 @@ def parse_args(argv=None):
                    help="c2 (default) the 2D 512^2 metric; c1/c3 other single instances; c4 256 batched "
                         "instances; c5 the serving stream; c0 the paper's ~66k-unknown Euler solver tables")
     p.add_argument("--model", type=int, choices=[2, 1], default=2,
-                   help="2: PFC2 (mobility 1, default); 1: PFC1 (mobility psi + 1.5) for c1/c2/c3")
+                   help="2: PFC2 (mobility 1, default); 1: PFC1 (mobility psi + 1.5) for c0-c3.  The "
+                        "white-noise starts of c1-c3 on their fine meshes give large grad mu, which makes "
+                        "PFC1 Rosenbrock stage systems stiff; c0 (h ~ pi/4, Euler) is the PFC1 measurement")
     p.add_argument("--requests", type=int, default=300, help="c5: number of requests")
     p.add_argument("--rate", type=float, default=3.0, help="c5: Poisson arrival rate (requests/s)")
     p.add_argument("--instances", type=int, default=256, help="c4: number of instances")
@@ -172,7 +174,8 @@ def euler_tables(args):
         psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
         for precision in ("fp64", args.precision):
             for tol in (w.outer_tol, 1e-6):
-                with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=tol) as s:
+                with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=tol,
+                                   model=args.model) as s:
                     x0 = s.init_state(psi0)
                     s.set_timing(True)
                     for tau in sorted(PAPER_EULER[w.dim]):
@@ -204,19 +207,20 @@ def euler_tables(args):
                                   "r = psi_bar = -0.35; 3D [3d]^3, 14^3 cubes, r = -0.3, psi_bar = -0.34; "
                                   "d = 4 pi/sqrt(3); noise amp 0.1/0.05; 20 Euler steps per tau from a "
                                   "consistent start; headline at outer tol 1e-8; inputs are L2-resident",
-                      "vs_baseline": "GPU solve time / the paper's 3.04 s (Table 3, CPU)"},
+                      "vs_baseline": "GPU solve time / the paper's 3.04 s (Table 3, CPU)",
+                      "model": "PFC2 (H^-1 flow)" if args.model == 2 else "PFC1 (mobility psi + 1.5)"},
            "table": rows}
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_euler_sample(synth.C0_2D_EULER)
+        out["cpu_baseline"] = oracle_euler_sample(synth.C0_2D_EULER, args.model)
     return out
 
 
-def oracle_euler_sample(w: synth.Workload):
+def oracle_euler_sample(w: synth.Workload, model: int = 2):
     """The oracle's Euler solve (tau = 0.1, tolerance 1e-8) of the 2D problem, one step."""
     from oracle.mesh import structured_mesh
     from oracle.rosenbrock import PFCProblem, euler_step
 
-    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r)
+    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=model)
     x0 = prob.consistent_state(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed))
     t0 = time.perf_counter()
     _, st = euler_step(prob, x0, w.tau0, tol=w.outer_tol)
