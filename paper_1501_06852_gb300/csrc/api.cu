@@ -16,6 +16,13 @@
 #include "launch.h"
 #include "pfc.h"
 
+#ifndef PFC_BOUNDARY_COST
+#define PFC_BOUNDARY_COST 1
+#endif
+#ifndef PFC_VEC_COST
+#define PFC_VEC_COST 320
+#endif
+
 namespace {
 
 // Ros3Pw in the modified Rosenbrock form (Table 1 of Praetorius & Voigt).  The
@@ -214,7 +221,7 @@ pfc_status status_from_err(int err) {
 // Enqueue one persistent-kernel launch; stats go to c->stats[slot].
 pfc_status run_solver(pfc_ctx* c, pfc::SolveArgs a, int prec, int slot) {
   a.stats = c->stats + slot;
-  CK(cudaMemsetAsync(c->arrive, 0, sizeof(unsigned), c->stream));
+  CK(cudaMemsetAsync(c->arrive, 0, sizeof(unsigned) * (4 + (size_t)c->G), c->stream));
   CK(cudaMemsetAsync(c->errw + slot, 0, sizeof(int), c->stream));
   CK(cudaMemsetAsync(a.stats, 0, sizeof(pfc::DevStats), c->stream));
   a.err = c->errw + slot;
@@ -456,7 +463,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs, int count, int slot, bool to_tmp, Bat
       a.err = ck->errw + slot;
       hargs[i] = a;
       hseg[i + 1] = hseg[i] + Gs[wv.first + i];
-      CK(cudaMemsetAsync(ck->arrive, 0, sizeof(unsigned), ck->stream));
+      CK(cudaMemsetAsync(ck->arrive, 0, sizeof(unsigned) * (4 + (size_t)ck->G), ck->stream));
       CK(cudaMemsetAsync(ck->errw + slot, 0, sizeof(int), ck->stream));
       CK(cudaMemsetAsync(ck->stats + slot, 0, sizeof(pfc::DevStats), ck->stream));
     }
@@ -643,12 +650,27 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->G = std::max(1, std::min(std::min(sms * bps, c->nslices), pfc::solve_threads()));
   // Slice ranges: blocks and, inside each block, warps get contiguous runs of
   // slices of equal cost, cost(slice) = 32 * (width + 10) ~ bytes of one SpMV
-  // row plus the vector traffic of the inner iteration.
+  // row plus the vector traffic of the inner iteration.  With structured stencils
+  // a slice holding rows with a missing element (boundary rows, which read their
+  // assembled SELL values and indices) costs kBoundaryExtra more per such row and
+  // slot: in 3D whole lattice planes are boundary rows, and without the extra
+  // weight the blocks holding them set the pace of every phase.
+  constexpr long long kBoundaryExtra = PFC_BOUNDARY_COST;
   const int W = pfc::solve_threads() / 32;
   std::vector<int> blk((size_t)c->G * W + 1, 0);
   {
     std::vector<long long> pre(S.nslices + 1, 0);
-    for (int s = 0; s < S.nslices; ++s) pre[s + 1] = pre[s] + (S.slice_ptr[s + 1] - S.slice_ptr[s]) + 320;
+    for (int s = 0; s < S.nslices; ++s) {
+      const long long width = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / 32;
+      long long cost = 32 * width + PFC_VEC_COST;
+      if (stencil) {
+        int nb = 0;
+        for (int l = 0; l < 32; ++l)
+          if (!(S.rowinfo[(size_t)s * 32 + l] & 8)) ++nb;
+        cost += kBoundaryExtra * nb * width;
+      }
+      pre[s + 1] = pre[s] + cost;
+    }
     auto split = [&](int lo, int hi, int parts, int* out) {  // out[0..parts]
       out[0] = lo;
       int s = lo;
@@ -741,7 +763,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_Z = L.take(sizeof(double) * np3 * c->opt.restart);
   const size_t o_ivec = L.take((size_t)pfc::kInnerVecs * c->n_pad * 8);
   const size_t vec_end = L.take(0);
-  const size_t o_arr = L.take(sizeof(unsigned) * 4);
+  // barrier counter (+3 spare words), then one phase flag per block (neighbour sync)
+  const size_t o_arr = L.take(sizeof(unsigned) * (4 + (size_t)c->G));
   const size_t o_errw = L.take(sizeof(int) * 8);
   const size_t o_part = L.take(sizeof(double4_32a) * pfc::solve_ring() * c->G);
   const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);

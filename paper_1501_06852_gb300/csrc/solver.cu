@@ -66,6 +66,9 @@ namespace {
 #ifndef PFC_INTERLEAVE
 #define PFC_INTERLEAVE 0
 #endif
+#ifndef PFC_NEIGHBOR_SYNC
+#define PFC_NEIGHBOR_SYNC 0
+#endif
 #ifndef PFC_ST_UNROLL
 #define PFC_ST_UNROLL 4
 #endif
@@ -100,6 +103,12 @@ struct Grid {
   int win_lo, win_n;  // rows [win_lo, win_lo + win_n) of the SpMV source held in s_win
   bool staged;        // stencil SpMVs read the source vector from s_win
   bool ri_smem;       // the block's row-info bytes are in s_rowinfo (row - 32 b_lo)
+  // neighbour synchronisation (structured stencils): blocks nb_lo..nb_hi own the rows
+  // this block's stencils reach; flags[b] counts block b's published phases
+  bool nbsync;
+  int nb_lo, nb_hi;
+  unsigned nepoch;
+  unsigned* flags;
 };
 
 
@@ -231,6 +240,58 @@ __device__ bool grid_sync(Grid& g, int tag) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Wait until every block whose rows this block's stencil reaches has finished the
+// current phase (a point-to-point replacement for a grid barrier before an SpMV
+// whose only cross-block inputs are the source vector's halo rows).  Each block
+// publishes its phase count with a release store; thread k waits for neighbour
+// nb_lo + k with relaxed loads and one acquire load once it has seen the count.
+// The wait is bounded like grid_sync's.
+__device__ bool neighbor_sync(Grid& g, int tag) {
+  __syncthreads();
+  unsigned long long t_in = 0;
+  if (g.prof) {
+    t_in = global_ns();
+    s_prof[tag] += (long long)(t_in - s_t_last);
+  }
+  g.nepoch += 1;
+  const unsigned ep = g.nepoch;
+  if (threadIdx.x == 0)
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(g.flags + g.bid), "r"(ep) : "memory");
+  const int nb = g.nb_lo + (int)threadIdx.x;
+  int bad = 0;
+  if (nb <= g.nb_hi && nb != g.bid) {
+    unsigned v = 0, spins = 0;
+    unsigned long long t0 = 0;
+    while (true) {
+      asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(g.flags + nb) : "memory");
+      if (v >= ep) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(g.flags + nb) : "memory");
+        break;
+      }
+      if ((++spins & 255u) == 0u) {
+        const unsigned long long t = global_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > g.limit_ns) {
+          atomicOr(g.err, kErrTimeout);
+          bad = 1;
+          break;
+        }
+        if (ld_relaxed_i32(g.err) & kErrTimeout) {
+          bad = 1;
+          break;
+        }
+      }
+    }
+  }
+  bad = __syncthreads_or(bad);
+  if (g.prof) {
+    s_t_last = global_ns();
+    s_prof[4 + tag] += (long long)(s_t_last - t_in);
+  }
+  return bad == 0;
 }
 
 // Sum of up to three values over all threads of the grid, identical in every block.
@@ -917,15 +978,21 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
         }
       }
     }
-    if (!grid_sum<Acc>(g, prr, Acc(0), Acc(0), red, kPhVec)) return false;
-    its = it;
-    if (!isfinite(red.x)) {
-      flag(g, kErrNonfinite);
-      return false;
-    }
-    if ((Acc)red.x <= thr) {
-      cnt.its += it;
-      return true;
+    if (g.nbsync) {
+      // the next phase needs only the halo of u: wait for the neighbours, and
+      // reduce (r, r) together with the phase-2 products (the test follows them)
+      if (!neighbor_sync(g, kPhVec)) return false;
+    } else {
+      if (!grid_sum<Acc>(g, prr, Acc(0), Acc(0), red, kPhVec)) return false;
+      its = it;
+      if (!isfinite(red.x)) {
+        flag(g, kErrNonfinite);
+        return false;
+      }
+      if ((Acc)red.x <= thr) {
+        cnt.its += it;
+        return true;
+      }
     }
     // phase 2: w = A u and the two inner products
     pg = Acc(0);
@@ -945,7 +1012,18 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
         }
       }
     }
-    if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
+    if (!grid_sum<Acc>(g, pg, pd, g.nbsync ? prr : Acc(0), red, kPhSpmv)) return false;
+    if (g.nbsync) {
+      its = it;
+      if (!isfinite(red.z)) {
+        flag(g, kErrNonfinite);
+        return false;
+      }
+      if ((Acc)red.z <= thr) {
+        cnt.its += it;
+        return true;
+      }
+    }
     const Acc gnew = (Acc)red.x, dnew = (Acc)red.y;
     beta = gnew / gam;
     const Acc den = dnew - beta * gnew / alpha;
@@ -1266,6 +1344,16 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
     g.win_n = min(a.n_pad, (re + a.st_halo + 3) & ~3) - g.win_lo;
     g.staged = sizeof(TV) == 4 && a.stencil && a.win_cap > 0 && re > rs && g.win_n <= a.win_cap;
     g.ri_smem = false;
+    // neighbour range: blocks whose rows meet [rs - halo, re + halo)
+    g.nbsync = PFC_NEIGHBOR_SYNC && !PFC_INTERLEAVE && a.stencil && a.st_halo > 0 && a.barrier_extra == 0;
+    g.nepoch = 0;
+    g.flags = a.arrive + 4;
+    g.nb_lo = g.nb_hi = bid;
+    if (g.nbsync) {
+      while (g.nb_lo > 0 && __ldg(a.blk + g.nb_lo * kWarps) * 32 > rs - a.st_halo) --g.nb_lo;
+      while (g.nb_hi + 1 < G && __ldg(a.blk + (g.nb_hi + 1) * kWarps) * 32 < re + a.st_halo) ++g.nb_hi;
+      g.nbsync = g.nb_hi - g.nb_lo < kThreads;
+    }
   }
   if (threadIdx.x == 0) {
     for (int k = 0; k < 8; ++k) s_prof[k] = 0;
