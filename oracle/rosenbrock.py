@@ -173,9 +173,10 @@ class PFCProblem:
     # --- stage solve (Section 4, Section 7) --------------------------------
     def stage_solve(self, A: sp.csr_matrix, b: np.ndarray, tau: float, tol: float = 1e-13,
                     inner: str = "pcg", restart: int = 30, max_outer: int = 2000, coef: Ros3Pw = ROS3PW,
-                    m0: float = 1.0):
-        """FGMRES with P_CH; m0 is the mean mobility of the constant-mobility approximation."""
-        pc = PCH(self.M, self.K, m0 * tau, coef.gamma, inner=inner)
+                    m0: float = 1.0, schur: str = "ch"):
+        """FGMRES with P(S_CH) (or P(S_D), schur="sd"); m0 is the mean mobility of the
+        constant-mobility approximation."""
+        pc = PCH(self.M, self.K, m0 * tau, coef.gamma, inner=inner, schur=schur)
         y, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
         st.inner = pc.log
         return y, st
@@ -286,12 +287,12 @@ def euler_rhs(prob: PFCProblem, psi_k: np.ndarray) -> np.ndarray:
 
 
 def euler_step(prob: PFCProblem, x_k: np.ndarray, tau: float, tol: float = 1e-13, inner: str = "pcg",
-               restart: int = 30, max_outer: int = 2000):
+               restart: int = 30, max_outer: int = 2000, schur: str = "ch"):
     """x_{k+1} = A^{-1} b by FGMRES(restart) with P_CH built for gamma = 1 (Section 4)."""
     psi_k = prob.split(x_k)[1]
     A = euler_matrix(prob, psi_k, tau)
     b = euler_rhs(prob, psi_k)
-    pc = PCH(prob.M, prob.K, prob.m0(psi_k) * tau, 1.0, inner=inner)
+    pc = PCH(prob.M, prob.K, prob.m0(psi_k) * tau, 1.0, inner=inner, schur=schur)
     x, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
     st.inner = pc.log
     return x, st

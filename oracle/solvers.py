@@ -13,7 +13,10 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``).
   solve stops once ||b - A x||_2 <= tol ||b||_2.
 * ``PCH``         - the block preconditioner of Eq. (4.1) with the Cahn-Hilliard
   approximation S_CH of the Schur complement (Section 4.2), applied in the
-  steps (1), (2), (3.1), (3.2), (4), (5).
+  steps (1), (2), (3.1), (3.2), (4), (5); or, with ``schur="sd"``, with the
+  diagonal approximation S_D = M - 2 delta K + delta K M_D^{-1} K, M_D = diag(M)
+  (Section 4.1), whose step (3) S_D x1 = M y1 runs a fixed number of Jacobi-PCG
+  iterations (Table 2: 20).
 
 Readings of garbled or silent passages (each applies to ``PCH.apply``):
 
@@ -42,7 +45,9 @@ class PCGResult:
 
 
 def pcg_jacobi(A: sp.csr_matrix, b: np.ndarray, rtol: float, maxit: int) -> PCGResult:
-    """Jacobi-preconditioned CG for SPD A from x0 = 0."""
+    """Jacobi-preconditioned CG for SPD A from x0 = 0.  rtol = 0 runs maxit iterations.
+    Reading: if p^T A p <= 0 (A not positive definite along p) the iteration stops
+    and returns the current iterate."""
     dinv = 1.0 / A.diagonal()
     x = np.zeros_like(b)
     bnorm = math.sqrt(float(b @ b))
@@ -54,7 +59,10 @@ def pcg_jacobi(A: sp.csr_matrix, b: np.ndarray, rtol: float, maxit: int) -> PCGR
     rz = float(r @ z)
     for it in range(1, maxit + 1):
         q = A @ p
-        alpha = rz / float(p @ q)
+        pq = float(p @ q)
+        if not pq > 0.0:
+            return PCGResult(x, it - 1, False)
+        alpha = rz / pq
         x += alpha * p
         r -= alpha * q
         if math.sqrt(float(r @ r)) <= rtol * bnorm:
@@ -152,24 +160,33 @@ class PCH:
     """
 
     def __init__(self, M, K, tau: float, gamma: float, inner: str = "pcg",
-                 inner_rtol: float = 1e-3, max_inner: int = 10000):
+                 inner_rtol: float = 1e-3, max_inner: int = 10000, schur: str = "ch", sd_its: int = 20):
         self.M, self.K = M.tocsr(), K.tocsr()
         self.gamma = gamma
         self.tau_e = gamma * tau
         self.delta = math.sqrt(self.tau_e)
         self.MdK = (self.M + self.delta * self.K).tocsr()            # step (2)
         self.MsK = (self.M + math.sqrt(self.delta) * self.K).tocsr() # steps (3.1), (3.2)
+        self.schur, self.sd_its = schur, sd_its
+        mats = [self.M, self.MdK, self.MsK]
+        if schur == "sd":
+            # S_D = M - 2 delta K + delta K M_D^{-1} K, M_D = diag(M)   (Section 4.1)
+            md_inv = sp.diags(1.0 / self.M.diagonal())
+            self.SD = (self.M - 2.0 * self.delta * self.K + self.delta * (self.K @ md_inv @ self.K)).tocsr()
+            mats.append(self.SD)
+        elif schur != "ch":
+            raise ValueError("schur must be 'ch' or 'sd'")
         self.inner, self.inner_rtol, self.max_inner = inner, inner_rtol, max_inner
         self.log = InnerLog()
         self.n = M.shape[0]
         if inner == "exact":
             import scipy.sparse.linalg as spla
-            self._lu = {id(A): spla.splu(A.tocsc()) for A in (self.M, self.MdK, self.MsK)}
+            self._lu = {id(A): spla.splu(A.tocsc()) for A in mats}
 
-    def _solve(self, A, b):
+    def _solve(self, A, b, fixed_its: int = 0):
         if self.inner == "exact":
             return self._lu[id(A)].solve(b)
-        res = pcg_jacobi(A, b, self.inner_rtol, self.max_inner)
+        res = pcg_jacobi(A, b, 0.0, fixed_its) if fixed_its else pcg_jacobi(A, b, self.inner_rtol, self.max_inner)
         self.log.calls += 1
         self.log.iterations += res.iterations
         self.log.per_call.append(res.iterations)
@@ -180,8 +197,11 @@ class PCH:
         v0, v1, v2 = v[:n], v[n:2 * n], v[2 * n:]
         y0 = self._solve(self.M, v0)                                       # (1)  M y0 = v0
         y1 = self._solve(self.MdK, self.gamma * v1 - self.tau_e * (self.K @ y0))  # (2)
-        w = self._solve(self.MsK, self.M @ y1)                             # (3.1)
-        x1 = self._solve(self.MsK, self.M @ w)                             # (3.2)
+        if self.schur == "sd":
+            x1 = self._solve(self.SD, self.M @ y1, self.sd_its)            # (3)  S_D x1 = M y1
+        else:
+            w = self._solve(self.MsK, self.M @ y1)                         # (3.1)
+            x1 = self._solve(self.MsK, self.M @ w)                         # (3.2)
         x0 = y0 + (y1 - x1) / self.delta                                   # (4)
         x2 = self._solve(self.M, v2 - self.K @ x1)                         # (5)
         return np.concatenate([x0, x1, x2])
