@@ -98,6 +98,12 @@ typedef struct {
                          The Euler system keeps the mobility explicit:
                          [tau K_+(psi_k), M, 0]. */
   double psi_min;     /* PFC1: lower bound psi_min of the density (-1.5, Section 2) */
+  int schur;          /* Schur-complement approximation in step (3) of the preconditioner:
+                         0: S_CH of Section 4.2, steps (3.1) and (3.2);
+                         1: S_D = M - 2 delta K + delta K M_D^{-1} K, M_D = diag(M)
+                         (Section 4.1), one Jacobi-PCG solve of schur_its iterations
+                         (Table 2: 20), applied without forming K M_D^{-1} K */
+  int schur_its;      /* fixed PCG iterations of the S_D step (>= 1) */
 } pfc_options;
 
 typedef struct {
@@ -116,7 +122,7 @@ typedef struct {
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
- * smem_window = 0, model = 2, psi_min = -1.5. */
+ * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

@@ -39,7 +39,9 @@ class _Options(ctypes.Structure):
                 ("inner_operator", ctypes.c_int),
                 ("smem_window", ctypes.c_int),
                 ("model", ctypes.c_int),
-                ("psi_min", ctypes.c_double)]
+                ("psi_min", ctypes.c_double),
+                ("schur", ctypes.c_int),
+                ("schur_its", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -201,7 +203,7 @@ class PFCSolver:
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
                  inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
-                 stream=None):
+                 schur: int = 0, schur_its: int = 20, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -220,6 +222,8 @@ class PFCSolver:
         o.smem_window = smem_window
         o.model = model
         o.psi_min = psi_min
+        o.schur = schur
+        o.schur_its = schur_its
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -105,6 +105,9 @@ struct pfc_ctx {
   double psi_min = -1.5;
   double m0 = 1.0;
   double *A10v = nullptr, *A11v = nullptr, *mob = nullptr, *wint = nullptr;
+  // P(S_D): Jacobi inverse of diag(S_D) in float64 and float32
+  double* dSD = nullptr;
+  float* fdSD = nullptr;
   // batched launches: this instance's warp slice ranges for a segment of blk_b_G blocks
   std::vector<long long> slice_cost_prefix;   // host, nslices + 1
   int* blk_b = nullptr;                       // device, G * W + 1
@@ -152,6 +155,9 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.Kv = c->Kv;
   a.Av = c->Av;
   a.A10 = c->model == 1 ? c->A10v : nullptr;
+  a.schur = c->opt.schur;
+  a.schur_its = c->opt.schur_its;
+  a.dSD = prec == 0 ? (const void*)c->dSD : (const void*)c->fdSD;
   a.A11 = c->model == 1 ? c->A11v : nullptr;
   if (prec == 0) {
     a.iM = c->Mv;
@@ -308,6 +314,9 @@ pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma, bool
                                     1.0 / gamma, with_f ? 1 : 0, c->A10v, c->A11v, c->stream));
   }
   c->delta = std::sqrt(gamma * tau * c->m0);
+  if (c->opt.schur == 1)
+    LAUNCH(pfc::launch_sd_diag_inv(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->diag, c->dM, c->delta, c->dSD,
+                                   c->prec ? c->fdSD : nullptr, c->stream));
   const double sdelta = std::sqrt(c->delta);
   LAUNCH(pfc::launch_inner_mats(c->prec, c->nnz_sell, c->Mv, c->Kv, c->delta, sdelta, c->MdKv, c->MsKv, c->iMdK, c->iMsK,
                             c->stream));
@@ -524,6 +533,8 @@ void pfc_default_options(pfc_options* o) {
   o->smem_window = 0;
   o->model = 2;
   o->psi_min = -1.5;
+  o->schur = 0;
+  o->schur_its = 20;
 }
 
 const char* pfc_status_string(int s) {
@@ -592,6 +603,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "smem_window must be 0 or 1"));
   if ((c->opt.model != 1 && c->opt.model != 2) || !std::isfinite(c->opt.psi_min))
     return bail(fail(c, PFC_ERR_INVALID, "model must be 1 (PFC1) or 2 (PFC2) and psi_min finite"));
+  if ((c->opt.schur != 0 && c->opt.schur != 1) || c->opt.schur_its < 1)
+    return bail(fail(c, PFC_ERR_INVALID, "schur must be 0 (S_CH) or 1 (S_D) and schur_its >= 1"));
   c->model = c->opt.model;
   c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
@@ -777,6 +790,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     o_mob = L.take(sizeof(double) * S.ref.mob.size());
   }
   const size_t o_wint = L.take(sizeof(double) * c->n_pad);
+  const size_t o_dsd = L.take(sizeof(double) * c->n_pad);
+  const size_t o_fdsd = L.take(sizeof(float) * c->n_pad);
   c->arena_bytes = L.take(0);
   {
     cudaError_t e = cudaMalloc((void**)&c->arena, c->arena_bytes);
@@ -843,6 +858,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);
   c->wint = (double*)(A + o_wint);
+  c->dSD = (double*)(A + o_dsd);
+  c->fdSD = (float*)(A + o_fdsd);
   if (c->model == 1) {
     c->A10v = (double*)(A + o_a10);
     c->A11v = (double*)(A + o_a11);

@@ -74,6 +74,9 @@ struct SolveArgs {
   const double* st_wM;     // M and K weights of each entry
   const double* st_wK;
   int st_types;
+  int schur;               // 0: S_CH (steps 3.1, 3.2); 1: S_D (step 3, schur_its Jacobi-PCG iterations)
+  int schur_its;
+  const void* dSD;         // inner-type Jacobi inverse of diag(S_D) (schur == 1)
   int st_halo;             // largest |column offset| of a stencil entry
   int win_cap;             // > 0: floats of dynamic shared memory per block for the window of
                            //   the SpMV source vector (float inner vectors only); 0: no window

@@ -236,6 +236,31 @@ __global__ void k_assemble_mob(long long nnz, const int* __restrict__ cptr, cons
   }
 }
 
+// Jacobi inverse of S_D = M - 2 delta K + delta K M_D^{-1} K (Section 4.1):
+//   d_i = M_ii - 2 delta K_ii + delta sum_j K_ij^2 / M_jj
+// (mdinv = 1 / diag(M)), one thread per SELL row; padding rows get 0.
+__global__ void k_sd_diag_inv(int nslices, const int* __restrict__ sp, const int* __restrict__ cols,
+                              const double* __restrict__ Mv, const double* __restrict__ Kv,
+                              const int* __restrict__ diag_pos, const double* __restrict__ mdinv, double delta,
+                              double* out, float* fout) {
+  const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (s >= nslices) return;
+  const int row = s * 32 + lane;
+  const int dp = diag_pos[row];
+  double v = 0.0;
+  if (dp >= 0) {
+    double kk = 0.0;
+    for (int idx = sp[s] + lane; idx < sp[s + 1]; idx += 32) {
+      const double k = Kv[idx];
+      kk = fma(k * k, mdinv[cols[idx]], kk);
+    }
+    v = 1.0 / (Mv[dp] - 2.0 * delta * Kv[dp] + delta * kk);
+  }
+  out[row] = v;
+  if (fout) fout[row] = (float)v;
+}
+
 // w[row] = sum of the row's stored values (SELL-32 slices, one warp per slice)
 __global__ void k_row_sums(int nslices, const int* __restrict__ sp, const double* __restrict__ vals, double* w) {
   const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -580,6 +605,14 @@ cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const i
   else
     k_assemble_mob<10><<<blocks_for(nnz, kBlock), kBlock, 0, st>>>(nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
                                                                    inv_gamma, with_f, A10, A11);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sd_diag_inv(int nslices, const int* sp, const int* cols, const double* Mv, const double* Kv,
+                               const int* diag_pos, const double* mdinv, double delta, double* out, float* fout,
+                               cudaStream_t st) {
+  k_sd_diag_inv<<<blocks_for((long long)nslices * 32, kBlock), kBlock, 0, st>>>(nslices, sp, cols, Mv, Kv, diag_pos,
+                                                                               mdinv, delta, out, fout);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,9 @@ cudaError_t launch_elem_mobload(int dim, int E, int ntypes, const int* elem, con
 cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const int* cidx, const int* cols,
                                 const int* elem, int E, const double* ebuf, const double* Mv, double tau,
                                 double inv_gamma, int with_f, double* A10, double* A11, cudaStream_t st);
+cudaError_t launch_sd_diag_inv(int nslices, const int* sp, const int* cols, const double* Mv, const double* Kv,
+                               const int* diag_pos, const double* mdinv, double delta, double* out, float* fout,
+                               cudaStream_t st);
 cudaError_t launch_row_sums(int nslices, const int* sp, const double* vals, double* w, cudaStream_t st);
 cudaError_t launch_sum_partials(int nparts, const double* partial, double scale, double* out, cudaStream_t st);
 cudaError_t launch_dot_partials(int n, const double* a, const double* b, double* partial, int nparts,

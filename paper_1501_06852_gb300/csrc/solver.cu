@@ -565,7 +565,7 @@ struct Ctx {
 };
 
 enum : int { kVr = 0, kVp = 1, kVq = 2, kVu = 3, kVw = 4, kVm0 = 5, kVm1 = 6, kVz = 7, kVs = 8,
-             kVy0 = 9, kVy1 = 10, kVwv = 11, kVx1 = 12, kVx2 = 13 };
+             kVy0 = 9, kVy1 = 10, kVwv = 11, kVx1 = 12, kVx2 = 13, kVt = 14, kVsd = 15 };
 
 // Right-hand side of an inner solve, per owned row:
 //   rhs(row) = alpha vin[row] + beta (mat x vx)[row]   (either term may be absent)
@@ -721,6 +721,139 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   }
   cnt.its += maxit;
   cnt.capped += 1;
+  return true;
+}
+
+// Step (3) of P(S_D) (Section 4.1): Jacobi-PCG on
+//     S_D = M - 2 delta K + delta K M_D^{-1} K,   M_D = diag(M),
+// applied without forming K M_D^{-1} K: t = K p and s = M_D^{-1} t on the owned
+// rows, a barrier (s is read on halo rows), then q = M p - 2 delta t + delta K s.
+// DI is the Jacobi inverse of diag(S_D).  Runs exactly maxit iterations (Table 2:
+// a fixed count) unless the residual vanishes or p.S_D p <= 0, which stops it.
+template <class TM, class TV>
+__device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, TV* x, RhsSpec<TM, TV> rhs, int maxit,
+                                    InnerCount& cnt, int& its) {
+  Ctx<TM, TV> c(a);
+  using Acc = typename Ctx<TM, TV>::Acc;
+  TV* r = c.vec(kVr);
+  TV* p = c.vec(kVp);
+  TV* q = c.vec(kVq);
+  TV* t = c.vec(kVt);
+  TV* sv = c.vec(kVsd);
+  const TV* dm = c.dM();
+  const Acc delta = (Acc)(1.0 / a.inv_delta);
+  const int lane = threadIdx.x & 31;
+  Acc pb = Acc(0), pz = Acc(0);
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int s = s0 + uu, row = s * 32 + lane;
+        const TV rv = (TV)rhs(g, a, s, lane, row);
+        const TV zz = (TV)((Acc)DI[row] * (Acc)rv);
+        x[row] = TV(0);
+        r[row] = rv;
+        p[row] = zz;
+        pb = fma((Acc)rv, (Acc)rv, pb);
+        pz = fma((Acc)rv, (Acc)zz, pz);
+      }
+    }
+  }
+  double4_32a red;
+  if (!grid_sum<Acc>(g, pb, pz, Acc(0), red, kPhInit)) return false;
+  its = 0;
+  cnt.calls += 1;
+  const double bb = red.x;
+  Acc rz = (Acc)red.y;
+  if (!isfinite(bb)) {
+    flag(g, kErrNonfinite);
+    return false;
+  }
+  if (bb == 0.0) return true;
+  for (int it = 1; it <= maxit; ++it) {
+    // t = K p, s = M_D^{-1} t
+    FOR_MY_GROUPS(g, s0, nsl) {
+      Acc ka[kGroup];
+      inner_rows<Acc>(g, a, kOpK, c.iK(), p, s0, nsl, lane, ka);
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          t[row] = (TV)ka[uu];
+          sv[row] = (TV)((Acc)dm[row] * ka[uu]);
+        }
+      }
+    }
+    if (!grid_sync(g, kPhSpmv)) return false;
+    // q = M p - 2 delta t + delta K s
+    Acc ppq = Acc(0);
+    FOR_MY_GROUPS(g, s0, nsl) {
+      Acc ma[kGroup], ks[kGroup];
+      inner_rows<Acc>(g, a, kOpM, c.iM(), p, s0, nsl, lane, ma);
+      inner_rows<Acc>(g, a, kOpK, c.iK(), sv, s0, nsl, lane, ks);
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc qv = ma[uu] - Acc(2) * delta * (Acc)t[row] + delta * ks[uu];
+          q[row] = (TV)qv;
+          ppq = fma((Acc)p[row], qv, ppq);
+        }
+      }
+    }
+    if (!grid_sum<Acc>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
+    const Acc pq = (Acc)red.x;
+    if (!isfinite(pq)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    if (!(pq > Acc(0))) {
+      its = it - 1;
+      cnt.its += it - 1;
+      return true;
+    }
+    const Acc alpha = rz / pq;
+    Acc prr = Acc(0), prz = Acc(0);
+    FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          const Acc xn = (Acc)x[row] + alpha * (Acc)p[row];
+          const Acc rn = (Acc)r[row] - alpha * (Acc)q[row];
+          x[row] = (TV)xn;
+          r[row] = (TV)rn;
+          const Acc zz = (Acc)DI[row] * rn;
+          prr = fma(rn, rn, prr);
+          prz = fma(rn, zz, prz);
+        }
+      }
+    }
+    if (!grid_sum<Acc>(g, prr, prz, Acc(0), red, kPhVec)) return false;
+    its = it;
+    if (!isfinite(red.x)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    if (red.x == 0.0) {
+      cnt.its += it;
+      return true;
+    }
+    const Acc rz_new = (Acc)red.y;
+    const Acc beta = rz_new / rz;
+    rz = rz_new;
+    FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+      for (int uu = 0; uu < kGroup; ++uu) {
+        if (uu < nsl) {
+          const int row = (s0 + uu) * 32 + lane;
+          p[row] = (TV)((Acc)DI[row] * (Acc)r[row] + beta * (Acc)p[row]);
+        }
+      }
+    }
+    if (!grid_sync(g, kPhVec)) return false;
+  }
+  cnt.its += maxit;
   return true;
 }
 
@@ -1070,14 +1203,21 @@ __device__ bool apply_pch(Grid& g, Ctx<TM, TV>& c, const double* v, double* z, I
   if (!pcg(g, c, c.iMdK(), kOpMdK, c.dMdK(), c.vec(kVy1), R{v1, a.gamma, c.iK(), kOpK, c.vec(kVy0), -a.tau_e}, rt,
            mi, cnt, its))
     return false;
-  // (3.1) (M + sqrt(delta) K) w = M y1
-  if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVwv), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVy1), 1.0}, rt, mi,
-           cnt, its))
-    return false;
-  // (3.2) (M + sqrt(delta) K) x1 = M w
-  if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVx1), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVwv), 1.0}, rt, mi,
-           cnt, its))
-    return false;
+  if (a.schur == 1) {
+    // (3) S_D x1 = M y1, a fixed number of Jacobi-PCG iterations (Section 4.1, Table 2)
+    if (!pcg_sd<TM, TV>(g, a, (const TV*)a.dSD, c.vec(kVx1), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVy1), 1.0},
+                        a.schur_its, cnt, its))
+      return false;
+  } else {
+    // (3.1) (M + sqrt(delta) K) w = M y1
+    if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVwv), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVy1), 1.0}, rt, mi,
+             cnt, its))
+      return false;
+    // (3.2) (M + sqrt(delta) K) x1 = M w
+    if (!pcg(g, c, c.iMsK(), kOpMsK, c.dMsK(), c.vec(kVx1), R{nullptr, 0.0, c.iM(), kOpM, c.vec(kVwv), 1.0}, rt, mi,
+             cnt, its))
+      return false;
+  }
   // (4) x0 = y0 + (y1 - x1) / delta, and z = (x0, x1, .)
   FOR_MY_GROUPS(g, s0, nsl) {
 #pragma unroll
