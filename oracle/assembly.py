@@ -36,11 +36,13 @@ _CHUNK = 1 << 16
 
 
 class Reference:
-    """Basis values/gradients of the P2 element at the quadrature points of one rule."""
+    """Basis values/gradients of the P2 (or P1) element at the quadrature points of one rule."""
 
-    def __init__(self, dim: int, npts: int = DEFAULT_POINTS):
+    def __init__(self, dim: int, npts: int = DEFAULT_POINTS, degree: int = 2):
         self.xi, self.w = simplex_rule(dim, npts)
-        self.phi, self.dphi = p2.basis(self.xi)   # [Q, nl], [Q, nl, d]
+        self.degree = degree
+        basis = p2.basis if degree == 2 else p2.basis_p1
+        self.phi, self.dphi = basis(self.xi)   # [Q, nl], [Q, nl, d]
 
 
 def _geometry(verts: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
@@ -107,18 +109,18 @@ def _chunks(mesh: Mesh):
 
 
 def mass_matrix(mesh: Mesh, ref: Reference | None = None) -> sp.csr_matrix:
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     return _to_csr(mesh, ((mesh.elem_dofs[s], element_mass(mesh, ref, s)) for s in _chunks(mesh)))
 
 
 def stiffness_matrix(mesh: Mesh, ref: Reference | None = None) -> sp.csr_matrix:
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     return _to_csr(mesh, ((mesh.elem_dofs[s], element_stiffness(mesh, ref, s)) for s in _chunks(mesh)))
 
 
 def nonlinear_mass(mesh: Mesh, psi: np.ndarray, ref: Reference | None = None) -> sp.csr_matrix:
     """N(psi) = ((-3 psi^2 phi_j, phi_i)) for psi given by its P2 coefficients."""
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     return _to_csr(
         mesh, ((mesh.elem_dofs[s], element_nonlinear_mass(mesh, ref, psi, s)) for s in _chunks(mesh))
     )
@@ -126,7 +128,7 @@ def nonlinear_mass(mesh: Mesh, psi: np.ndarray, ref: Reference | None = None) ->
 
 def load_cubed(mesh: Mesh, psi: np.ndarray, ref: Reference | None = None) -> np.ndarray:
     """l(psi^3)_i = (psi_h^3, phi_i), psi_h the P2 function with coefficients psi."""
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     out = np.zeros(mesh.n)
     for s in _chunks(mesh):
         det, _ = _geometry(mesh.elem_verts[s])
@@ -138,21 +140,21 @@ def load_cubed(mesh: Mesh, psi: np.ndarray, ref: Reference | None = None) -> np.
 
 def mobility_stiffness(mesh: Mesh, psi_plus: np.ndarray, ref: Reference | None = None) -> sp.csr_matrix:
     """K_+(psi) = ((psi^+ grad phi_j, grad phi_i)) for psi^+ given by its P2 coefficients."""
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     return _to_csr(mesh, ((mesh.elem_dofs[s], element_mobility_stiffness(mesh, ref, psi_plus, s))
                           for s in _chunks(mesh)))
 
 
 def mobility_derivative(mesh: Mesh, mu: np.ndarray, ref: Reference | None = None) -> sp.csr_matrix:
     """F(mu) = ((phi_j grad mu, grad phi_i)): the derivative of K_+(psi) mu in psi."""
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     return _to_csr(mesh, ((mesh.elem_dofs[s], element_mobility_derivative(mesh, ref, mu, s))
                           for s in _chunks(mesh)))
 
 
 def mobility_load(mesh: Mesh, psi_plus: np.ndarray, mu: np.ndarray, ref: Reference | None = None) -> np.ndarray:
     """k_i = (psi^+ grad mu, grad phi_i), integrated directly."""
-    ref = ref or Reference(mesh.dim)
+    ref = ref or Reference(mesh.dim, degree=mesh.degree)
     out = np.zeros(mesh.n)
     for s in _chunks(mesh):
         det, inv = _geometry(mesh.elem_verts[s])

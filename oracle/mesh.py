@@ -1,4 +1,4 @@
-"""Structured simplicial meshes and the P2 degree-of-freedom lattice.
+"""Structured simplicial meshes and the P2 (or P1) degree-of-freedom lattice.
 
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
@@ -35,6 +35,7 @@ class Mesh:
     coords: np.ndarray     # [n, dim] dof coordinates
     elem_dofs: np.ndarray  # [E, nloc] global P2 dof index per local node
     elem_verts: np.ndarray # [E, dim+1, dim] vertex coordinates
+    degree: int = 2        # 2: P2 dofs (half-spacing lattice); 1: P1 dofs (the vertices)
 
     @property
     def h(self) -> float:
@@ -55,8 +56,9 @@ def _vertex_paths(dim: int) -> list[np.ndarray]:
     return paths
 
 
-def structured_mesh(dim: int, side: int, length: float) -> Mesh:
-    m = 2 * side + 1
+def structured_mesh(dim: int, side: int, length: float, degree: int = 2) -> Mesh:
+    """P2 dofs on the half-spacing lattice (degree 2) or P1 dofs on the vertices (degree 1)."""
+    m = degree * side + 1
     n = m ** dim
     h = length / side
     cells = np.stack(np.meshgrid(*[np.arange(side)] * dim, indexing="ij"), axis=-1).reshape(-1, dim)
@@ -64,15 +66,18 @@ def structured_mesh(dim: int, side: int, length: float) -> Mesh:
     cells = cells[np.lexsort(tuple(cells[:, k] for k in range(dim)))]
     elem_lat = []
     for path in _vertex_paths(dim):
-        vl = 2 * (cells[:, None, :] + path[None, :, :])          # [C, d+1, d] lattice coords
-        mids = [(vl[:, a, :] + vl[:, b, :]) // 2 for a, b in EDGES[dim]]
-        elem_lat.append(np.concatenate([vl, np.stack(mids, axis=1)], axis=1))
+        vl = degree * (cells[:, None, :] + path[None, :, :])     # [C, d+1, d] lattice coords
+        if degree == 2:
+            mids = [(vl[:, a, :] + vl[:, b, :]) // 2 for a, b in EDGES[dim]]
+            elem_lat.append(np.concatenate([vl, np.stack(mids, axis=1)], axis=1))
+        else:
+            elem_lat.append(vl)
     lat = np.concatenate(elem_lat, axis=0)                        # [E, nloc, d]
     stride = m ** np.arange(dim)
     elem_dofs = (lat * stride).sum(axis=-1)
-    elem_verts = lat[:, : dim + 1, :].astype(np.float64) * (h / 2.0)
+    elem_verts = lat[:, : dim + 1, :].astype(np.float64) * (h / degree)
     grid = np.stack(np.meshgrid(*[np.arange(m)] * dim, indexing="ij"), axis=-1).reshape(-1, dim)
     idx = (grid * stride).sum(axis=-1)
     coords = np.empty((n, dim))
-    coords[idx] = grid * (h / 2.0)
-    return Mesh(dim, side, float(length), n, coords, elem_dofs.astype(np.int64), elem_verts)
+    coords[idx] = grid * (h / degree)
+    return Mesh(dim, side, float(length), n, coords, elem_dofs.astype(np.int64), elem_verts, degree)

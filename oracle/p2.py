@@ -1,4 +1,4 @@
-"""P2 Lagrange basis on the reference simplex.
+"""P2 (and P1) Lagrange bases on the reference simplex.
 
 TEST INFRASTRUCTURE (see ``oracle/__init__``).
 
@@ -9,6 +9,7 @@ Lagrange basis of degree 2 is lambda_k (2 lambda_k - 1) at the vertices and
 lambda_k = xi_k (k >= 1) and lambda_0 = 1 - sum(xi).
 
 Local numbering: vertices 0..d first, then the edges in ``EDGES[dim]`` order.
+The P1 basis (p = 1, also used in the paper's experiments) is lambda_k at the vertices.
 """
 from __future__ import annotations
 
@@ -50,6 +51,13 @@ def basis(xi: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
         val[:, d + 1 + e] = 4.0 * lam[:, a] * lam[:, b]
         grad[:, d + 1 + e, :] = 4.0 * (lam[:, b][:, None] * glam[a][None, :] + lam[:, a][:, None] * glam[b][None, :])
     return val, grad
+
+
+def basis_p1(xi: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Values [Q, d+1] and reference gradients [Q, d+1, d] of the P1 basis at points xi."""
+    q, d = xi.shape
+    lam, glam = barycentric(xi)
+    return lam, np.broadcast_to(glam[None, :, :], (q, d + 1, d)).copy()
 
 
 def nodes(dim: int) -> np.ndarray:

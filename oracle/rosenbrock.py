@@ -116,7 +116,7 @@ class PFCProblem:
     psi_min: float = -1.5
 
     def __post_init__(self):
-        self.ref = self.ref or assembly.Reference(self.mesh.dim)
+        self.ref = self.ref or assembly.Reference(self.mesh.dim, degree=self.mesh.degree)
         if self.M is None:
             self.M = assembly.mass_matrix(self.mesh, self.ref)
         if self.K is None:

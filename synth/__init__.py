@@ -48,9 +48,15 @@ def p2_dofs_per_field(dim: int, side: int) -> int:
     return (2 * side + 1) ** dim
 
 
-def initial_psi(dim: int, side: int, psi_mean: float, amp: float, seed: int) -> np.ndarray:
+def dofs_per_field(dim: int, side: int, degree: int = 2) -> int:
+    """Lattice points of a structured grid with ``side`` cells per axis: P2 (degree 2)
+    uses the half-spacing lattice, P1 (degree 1) the vertices."""
+    return (degree * side + 1) ** dim
+
+
+def initial_psi(dim: int, side: int, psi_mean: float, amp: float, seed: int, degree: int = 2) -> np.ndarray:
     """Seeded noise psi0 (lexicographic dof order, x fastest), float64."""
-    n = p2_dofs_per_field(dim, side)
+    n = dofs_per_field(dim, side, degree)
     return psi_mean + amp * (2.0 * uniform01(seed, n) - 1.0)
 
 
