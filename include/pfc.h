@@ -14,6 +14,8 @@
  *   [0, length]^dim (2D: each square cut into 2 triangles along the diagonal
  *   from (i, j) to (i+1, j+1); 3D: each cube cut into the 6 Kuhn tetrahedra).
  *   Dofs are numbered lexicographically on the half-spacing lattice, x fastest.
+ *   With options.degree = 1 (P1) the dofs are the (side + 1)^dim mesh vertices,
+ *   numbered the same way.  pfc_host_pattern and pfc_host_stencil describe P2.
  * - A state or stage vector has 3n doubles: [mu (n) | psi (n) | omega (n)]
  *   (the unknowns x = (mu, psi, omega) of Section 3).
  * - Every vector argument is a DEVICE pointer (cudaMalloc'd or from a framework
@@ -104,6 +106,8 @@ typedef struct {
                          (Section 4.1), one Jacobi-PCG solve of schur_its iterations
                          (Table 2: 20), applied without forming K M_D^{-1} K */
   int schur_its;      /* fixed PCG iterations of the S_D step (>= 1) */
+  int degree;         /* Lagrange degree of V_h (Section 3): 2 (P2, default) or 1 (P1,
+                         dofs on the mesh vertices, n = (side + 1)^dim per field) */
 } pfc_options;
 
 typedef struct {
@@ -122,7 +126,7 @@ typedef struct {
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
- * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20. */
+ * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20, degree = 2. */
 void pfc_default_options(pfc_options* opt);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the

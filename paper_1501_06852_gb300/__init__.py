@@ -41,7 +41,8 @@ class _Options(ctypes.Structure):
                 ("model", ctypes.c_int),
                 ("psi_min", ctypes.c_double),
                 ("schur", ctypes.c_int),
-                ("schur_its", ctypes.c_int)]
+                ("schur_its", ctypes.c_int),
+                ("degree", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -203,7 +204,7 @@ class PFCSolver:
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
                  inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
-                 schur: int = 0, schur_its: int = 20, stream=None):
+                 schur: int = 0, schur_its: int = 20, degree: int = 2, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -224,6 +225,7 @@ class PFCSolver:
         o.psi_min = psi_min
         o.schur = schur
         o.schur_its = schur_its
+        o.degree = degree
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -45,7 +45,7 @@ struct Layout {
 };
 
 std::mutex g_const_mutex;
-bool g_const_done[2][64] = {};
+bool g_const_done[4][64] = {};   // element kind (P2 tri, P2 tet, P1 tri, P1 tet) x device
 
 }  // namespace
 
@@ -268,11 +268,11 @@ void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
 // the row kernel.
 pfc_status rhs_at_stage(pfc_ctx* c, bool with_d) {
   const int np = c->n_pad;
-  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_elem_load(c->nl, c->E, c->elem, c->xi + np, c->vol, c->ebuf, c->stream));
   double* lbuf2 = nullptr;
   if (c->model == 1) {
     lbuf2 = c->ebuf + (size_t)c->nl * c->E;
-    LAUNCH(pfc::launch_elem_mobload(c->dim, c->E, c->ntypes, c->elem, c->xi + np, c->xi, c->psi_min, c->mob, lbuf2,
+    LAUNCH(pfc::launch_elem_mobload(c->nl, c->E, c->ntypes, c->elem, c->xi + np, c->xi, c->psi_min, c->mob, lbuf2,
                                     c->stream));
   }
   LAUNCH(pfc::launch_rhs(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, c->dptr, c->didx, c->ebuf, c->xi,
@@ -292,7 +292,7 @@ pfc_status stage_rhs_internal(pfc_ctx* c, int nprev) {
 // system, whose mobility is explicit (A11 = M).
 pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma, bool with_f = true) {
   const int np = c->n_pad;
-  LAUNCH(pfc::launch_elem_quartic(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_elem_quartic(c->nl, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_assemble_a01(c->nnz_sell, c->cptr, c->cidx, c->ebuf, c->Mv, c->Kv, c->opt.r, c->Av, c->stream));
   c->tau = tau;
   c->gamma = gamma;
@@ -308,9 +308,9 @@ pfc_status assemble_internal(pfc_ctx* c, double tau, double gamma = kGamma, bool
     c->m0 = c->h_err[1] / omega - c->psi_min;
     if (!(c->m0 > 0.0) || !std::isfinite(c->m0))
       return fail(c, PFC_ERR_INVALID, "PFC1: the mean mobility <psi - psi_min> must be positive");
-    LAUNCH(pfc::launch_elem_mobility(c->dim, c->E, c->ntypes, c->elem, c->xk + np, c->xk, c->psi_min, c->mob, c->ebuf,
+    LAUNCH(pfc::launch_elem_mobility(c->nl, c->E, c->ntypes, c->elem, c->xk + np, c->xk, c->psi_min, c->mob, c->ebuf,
                                      c->stream));
-    LAUNCH(pfc::launch_assemble_mob(c->dim, c->nnz_sell, c->cptr, c->cidx, c->cols, c->elem, c->E, c->ebuf, c->Mv, tau,
+    LAUNCH(pfc::launch_assemble_mob(c->nl, c->nnz_sell, c->cptr, c->cidx, c->cols, c->elem, c->E, c->ebuf, c->Mv, tau,
                                     1.0 / gamma, with_f ? 1 : 0, c->A10v, c->A11v, c->stream));
   }
   c->delta = std::sqrt(gamma * tau * c->m0);
@@ -535,6 +535,7 @@ void pfc_default_options(pfc_options* o) {
   o->psi_min = -1.5;
   o->schur = 0;
   o->schur_its = 20;
+  o->degree = 2;
 }
 
 const char* pfc_status_string(int s) {
@@ -562,7 +563,7 @@ size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt) {
   pfc_default_options(&o);
   if (opt) o = *opt;
   if ((dim != 2 && dim != 3) || side < 1) return 0;
-  return pfc::footprint_estimate(dim, side, o.restart, o.precision);
+  return pfc::footprint_estimate(dim, side, o.restart, o.precision, o.degree == 1 ? 1 : 2);
 }
 
 void pfc_destroy(pfc_ctx* c) {
@@ -605,6 +606,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "model must be 1 (PFC1) or 2 (PFC2) and psi_min finite"));
   if ((c->opt.schur != 0 && c->opt.schur != 1) || c->opt.schur_its < 1)
     return bail(fail(c, PFC_ERR_INVALID, "schur must be 0 (S_CH) or 1 (S_D) and schur_its >= 1"));
+  if (c->opt.degree != 1 && c->opt.degree != 2) return bail(fail(c, PFC_ERR_INVALID, "degree must be 1 or 2"));
   c->model = c->opt.model;
   c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
@@ -622,7 +624,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   pfc::HostSetup S;
   std::string err;
   const bool stencil = c->opt.inner_operator == 1;
-  if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma))
+  if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma, c->opt.degree))
     return bail(fail(c, PFC_ERR_INVALID, err));
   if (stencil) {
     // the kernel pads every type to the longest stencil (rounded up to 4) and adds
@@ -909,13 +911,13 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   UP(c->stiff_tab, S.ref.stiff);
   {
     std::lock_guard<std::mutex> lk(g_const_mutex);
-    const int di = dim - 2;
+    const int di = (dim - 2) + (S.degree == 1 ? 2 : 0);
     if (c->device < 0 || c->device >= 64) return bail(fail(c, PFC_ERR_INVALID, "device index out of range"));
     if (!g_const_done[di][c->device]) {
       std::vector<double> unit(S.ref.quartic.size());
       for (size_t q = 0; q < unit.size(); ++q) unit[q] = S.ref.quartic[q] / S.ref.vol;
-      CK_SETUP(pfc::upload_quartic(dim, unit.data(), S.ref.npairs));
-      CK_SETUP(pfc::upload_pairs(dim, S.ref.pair_j.data(), S.ref.npairs));
+      CK_SETUP(pfc::upload_quartic(S.nl, unit.data(), S.ref.npairs));
+      CK_SETUP(pfc::upload_pairs(S.nl, S.ref.pair_j.data(), S.ref.npairs));
       g_const_done[di][c->device] = true;
     }
   }
@@ -1052,7 +1054,7 @@ pfc_status pfc_euler_step(pfc_ctx* c, double* state, double tau, pfc_solve_stats
   // A of Eq. (3.4): the stage matrix with gamma = 1, A01 = -(1+r) M + N(psi_k) + 2 K
   st = assemble_internal(c, tau, 1.0, false);
   if (st != PFC_OK) return st;
-  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_elem_load(c->nl, c->E, c->elem, c->xk + np, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_euler_rhs(c->nslices, np, c->slice_ptr, c->cols, c->Mv, c->dptr, c->didx, c->ebuf, c->xk + np,
                                c->bv, c->stream));
   pfc::SolveArgs a = base_args(c, c->prec);
@@ -1082,7 +1084,7 @@ pfc_status pfc_init_state(pfc_ctx* c, const double* psi0, double* state) {
   double* psi = c->xk + np;
   double* om = c->xk + 2 * np;
   LAUNCH(pfc::launch_gather_in(c->n, np, 1, c->perm, psi0, psi, c->stream));
-  LAUNCH(pfc::launch_elem_load(c->dim, c->E, c->elem, psi, c->vol, c->ebuf, c->stream));
+  LAUNCH(pfc::launch_elem_load(c->nl, c->E, c->elem, psi, c->vol, c->ebuf, c->stream));
   LAUNCH(pfc::launch_dof_gather(np, c->dptr, c->didx, c->ebuf, c->lvec, c->stream));
   // M omega = -K psi
   LAUNCH(pfc::launch_spmv_combo(c->nslices, c->slice_ptr, c->cols, c->Mv, c->Kv, 0.0, nullptr, -1.0, psi, 0.0, nullptr, 0.0,

@@ -1,4 +1,4 @@
-// Structured simplicial mesh, P2 dof lattice, SELL-C-sigma pattern and the
+// Structured simplicial mesh, P2 (or P1) dof lattice, SELL-C-sigma pattern and the
 // gather maps of the assembly kernels (host side, once per instance).
 //
 // Mesh (Section 3 and Section 7 use regular simplicial meshes): side^dim cells of
@@ -6,7 +6,7 @@
 // a monotone lattice path from the cell's low corner to its high corner (2 in 2D,
 // the 6 Kuhn tetrahedra in 3D).  P2 dofs are the half-spacing lattice points,
 // numbered lexicographically (x fastest); the node of edge (a, b) is the lattice
-// midpoint of its end points.
+// midpoint of its end points.  P1 dofs (degree 1) are the vertices themselves.
 //
 // Device layout.  All blocks of the stage matrix (M, K, A01 and the inner
 // matrices) share one sparsity pattern, stored once as SELL-32-sigma: rows are
@@ -31,7 +31,7 @@ namespace pfc {
 void element_path(int dim, int t, int verts[4][3]);
 void local_edge(int dim, int e, int& a, int& b);
 
-bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma) {
+bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma, int degree) {
   if (dim != 2 && dim != 3) {
     err = "dim must be 2 or 3";
     return false;
@@ -40,11 +40,15 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
     err = "side must be >= 1 and length > 0";
     return false;
   }
-  const int64_t lat = 2 * (int64_t)side + 1;
+  if (degree != 1 && degree != 2) {
+    err = "degree must be 1 or 2";
+    return false;
+  }
+  const int64_t lat = degree * (int64_t)side + 1;
   const int64_t n64 = dim == 2 ? lat * lat : lat * lat * lat;
   const int64_t cells64 = dim == 2 ? (int64_t)side * side : (int64_t)side * side * side;
   const int ntypes = dim == 2 ? 2 : 6;
-  const int nl = dim == 2 ? 6 : 10;
+  const int nl = degree == 1 ? dim + 1 : (dim == 2 ? 6 : 10);
   const int np = nl * (nl + 1) / 2;
   if (n64 > (1LL << 28) || cells64 * ntypes * np > (1LL << 31) - 1) {
     err = "mesh too large for 32-bit indices";
@@ -52,6 +56,7 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   }
   S = HostSetup{};
   S.dim = dim;
+  S.degree = degree;
   S.side = side;
   S.length = length;
   S.h = length / side;
@@ -60,7 +65,7 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   S.ntypes = ntypes;
   S.nl = nl;
   S.sigma = sigma < 1 ? 1 : sigma;
-  if (!build_reference(dim, S.h, S.ref, err)) return false;
+  if (!build_reference(dim, S.h, S.ref, err, degree)) return false;
   const int n = S.n;
   const int E = (int)(cells64 * ntypes);
   S.E = E;
@@ -75,11 +80,11 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
       int e = (int)(c * ntypes + t);
       int L[10][3];
       for (int k = 0; k <= dim; ++k) {
-        L[k][0] = 2 * (ci + path[t][k][0]);
-        L[k][1] = 2 * (cj + path[t][k][1]);
-        L[k][2] = 2 * (ck + path[t][k][2]);
+        L[k][0] = degree * (ci + path[t][k][0]);
+        L[k][1] = degree * (cj + path[t][k][1]);
+        L[k][2] = degree * (ck + path[t][k][2]);
       }
-      int ne = dim == 2 ? 3 : 6;
+      int ne = degree == 1 ? 0 : (dim == 2 ? 3 : 6);
       for (int q = 0; q < ne; ++q) {
         int a, b;
         local_edge(dim, q, a, b);
@@ -295,13 +300,13 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   return true;
 }
 
-size_t footprint_estimate(int dim, int side, int restart, int precision) {
-  const double lat = 2.0 * side + 1.0;
+size_t footprint_estimate(int dim, int side, int restart, int precision, int degree) {
+  const double lat = degree * side + 1.0;
   const double n = dim == 2 ? lat * lat : lat * lat * lat;
-  const double nnz_row = dim == 2 ? 11.6 : 28.6;      // stored slots per row incl. padding
+  const double nnz_row = degree == 1 ? (dim == 2 ? 7.2 : 15.2) : (dim == 2 ? 11.6 : 28.6);  // slots per row
   const double nnz = n * nnz_row;
   const double E = dim == 2 ? 2.0 * side * side : 6.0 * side * side * side;
-  const double np = dim == 2 ? 21 : 55, nl = dim == 2 ? 6 : 10;
+  const double nl = degree == 1 ? dim + 1 : (dim == 2 ? 6 : 10), np = nl * (nl + 1) / 2;
   double b = 0;
   b += nnz * 4;                             // columns
   b += nnz * 8 * 5;                         // M, K, A01, M+dK, M+sK (float64)

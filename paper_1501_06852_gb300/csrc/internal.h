@@ -30,8 +30,9 @@ struct RefTensors {
 // kernels gather through.  All indices are int32.
 struct HostSetup {
   int dim = 0, side = 0;
+  int degree = 2;                 // Lagrange degree: 2 (P2) or 1 (P1)
   double length = 0.0, h = 0.0;
-  int lat = 0;                    // 2 side + 1 lattice points per axis
+  int lat = 0;                    // degree * side + 1 lattice points per axis
   int n = 0;                      // dofs per field
   int n_pad = 0;                  // n rounded up to a multiple of kSellC
   int nslices = 0;
@@ -64,10 +65,11 @@ struct HostSetup {
   std::vector<unsigned char> rowinfo;  // n_pad: bits 0-2 dof type, bit 3 interior
 };
 
-bool build_reference(int dim, double h, RefTensors& out, std::string& err);
-bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err, int sigma = kSellSigma);
+bool build_reference(int dim, double h, RefTensors& out, std::string& err, int degree = 2);
+bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err, int sigma = kSellSigma,
+                 int degree = 2);
 
 // Bytes of device memory a context of this size holds (estimate used for admission).
-size_t footprint_estimate(int dim, int side, int restart, int precision);
+size_t footprint_estimate(int dim, int side, int restart, int precision, int degree = 2);
 
 }  // namespace pfc

@@ -17,11 +17,15 @@
 namespace pfc {
 namespace {
 
-__constant__ double c_quart2[21 * 21];
-__constant__ double c_quart3[55 * 55];
-// second node of unordered local pair p = (i <= j), per dimension
+__constant__ double c_quart2[21 * 21];   // P2 triangles
+__constant__ double c_quart3[55 * 55];   // P2 tetrahedra
+__constant__ double c_quart1_2[6 * 6];   // P1 triangles
+__constant__ double c_quart1_3[10 * 10]; // P1 tetrahedra
+// second node of unordered local pair p = (i <= j), per element kind
 __constant__ int c_pair_j2[21];
 __constant__ int c_pair_j3[55];
+__constant__ int c_pair_j1_2[6];
+__constant__ int c_pair_j1_3[10];
 
 constexpr int kBlock = 256;
 
@@ -59,6 +63,19 @@ __device__ __forceinline__ const double* quart_table<6>() {
 template <>
 __device__ __forceinline__ const double* quart_table<10>() {
   return c_quart3;
+}
+template <>
+__device__ __forceinline__ const double* quart_table<3>() {
+  return c_quart1_2;
+}
+template <>
+__device__ __forceinline__ const double* quart_table<4>() {
+  return c_quart1_3;
+}
+
+template <int NL>
+__device__ __forceinline__ const int* pair_j_table() {
+  return NL == 6 ? c_pair_j2 : NL == 10 ? c_pair_j3 : NL == 3 ? c_pair_j1_2 : c_pair_j1_3;
 }
 
 // ebuf[p * E + e] = vol * int psi^2 phi_i phi_j (unit-volume tensor times vol), p = (i <= j)
@@ -217,7 +234,7 @@ __global__ void k_assemble_mob(long long nnz, const int* __restrict__ cptr, cons
                                const int* __restrict__ cols, const int* __restrict__ elem, int E,
                                const double* __restrict__ ebuf, const double* __restrict__ Mv, double tau,
                                double inv_gamma, int with_f, double* A10, double* A11) {
-  const int* pj = NL == 6 ? c_pair_j2 : c_pair_j3;
+  const int* pj = pair_j_table<NL>();
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < nnz; s += (long long)gridDim.x * blockDim.x) {
     const int col = cols[s];
     double kp = 0.0, f = 0.0;
@@ -568,43 +585,57 @@ __global__ void k_combine_field(int n_pad, const double* __restrict__ a, double 
 
 int step_partials() { return kStepParts; }
 
-cudaError_t upload_quartic(int dim, const double* q, int npairs) {
+cudaError_t upload_quartic(int nl, const double* q, int npairs) {
   const size_t bytes = sizeof(double) * npairs * npairs;
-  return dim == 2 ? cudaMemcpyToSymbol(c_quart2, q, bytes) : cudaMemcpyToSymbol(c_quart3, q, bytes);
+  switch (nl) {
+    case 6: return cudaMemcpyToSymbol(c_quart2, q, bytes);
+    case 10: return cudaMemcpyToSymbol(c_quart3, q, bytes);
+    case 3: return cudaMemcpyToSymbol(c_quart1_2, q, bytes);
+    case 4: return cudaMemcpyToSymbol(c_quart1_3, q, bytes);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t upload_pairs(int dim, const int* pair_j, int npairs) {
+cudaError_t upload_pairs(int nl, const int* pair_j, int npairs) {
   const size_t bytes = sizeof(int) * npairs;
-  return dim == 2 ? cudaMemcpyToSymbol(c_pair_j2, pair_j, bytes) : cudaMemcpyToSymbol(c_pair_j3, pair_j, bytes);
+  switch (nl) {
+    case 6: return cudaMemcpyToSymbol(c_pair_j2, pair_j, bytes);
+    case 10: return cudaMemcpyToSymbol(c_pair_j3, pair_j, bytes);
+    case 3: return cudaMemcpyToSymbol(c_pair_j1_2, pair_j, bytes);
+    case 4: return cudaMemcpyToSymbol(c_pair_j1_3, pair_j, bytes);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_elem_mobility(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+// the element kernels are instantiated per local node count: 6 / 10 (P2), 3 / 4 (P1)
+#define PFC_NL_DISPATCH(nl, KERNEL, GRID, BLOCK, ...)                                   \
+  do {                                                                                  \
+    switch (nl) {                                                                       \
+      case 6: KERNEL<6><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); break;                    \
+      case 10: KERNEL<10><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); break;                  \
+      case 3: KERNEL<3><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); break;                    \
+      case 4: KERNEL<4><<<GRID, BLOCK, 0, st>>>(__VA_ARGS__); break;                    \
+      default: return cudaErrorInvalidValue;                                            \
+    }                                                                                   \
+  } while (0)
+
+cudaError_t launch_elem_mobility(int nl, int E, int ntypes, const int* elem, const double* psi, const double* mu,
                                  double psi_min, const double* mob, double* ebuf, cudaStream_t st) {
-  if (dim == 2)
-    k_elem_mobility<6><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, ebuf);
-  else
-    k_elem_mobility<10><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, ebuf);
+  PFC_NL_DISPATCH(nl, k_elem_mobility, blocks_for(E, 128), 128, E, ntypes, elem, psi, mu, psi_min, mob, ebuf);
   return cudaGetLastError();
 }
 
-cudaError_t launch_elem_mobload(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+cudaError_t launch_elem_mobload(int nl, int E, int ntypes, const int* elem, const double* psi, const double* mu,
                                 double psi_min, const double* mob, double* lbuf, cudaStream_t st) {
-  if (dim == 2)
-    k_elem_mobload<6><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, lbuf);
-  else
-    k_elem_mobload<10><<<blocks_for(E, 128), 128, 0, st>>>(E, ntypes, elem, psi, mu, psi_min, mob, lbuf);
+  PFC_NL_DISPATCH(nl, k_elem_mobload, blocks_for(E, 128), 128, E, ntypes, elem, psi, mu, psi_min, mob, lbuf);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const int* cidx, const int* cols,
+cudaError_t launch_assemble_mob(int nl, long long nnz, const int* cptr, const int* cidx, const int* cols,
                                 const int* elem, int E, const double* ebuf, const double* Mv, double tau,
                                 double inv_gamma, int with_f, double* A10, double* A11, cudaStream_t st) {
-  if (dim == 2)
-    k_assemble_mob<6><<<blocks_for(nnz, kBlock), kBlock, 0, st>>>(nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
-                                                                  inv_gamma, with_f, A10, A11);
-  else
-    k_assemble_mob<10><<<blocks_for(nnz, kBlock), kBlock, 0, st>>>(nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
-                                                                   inv_gamma, with_f, A10, A11);
+  PFC_NL_DISPATCH(nl, k_assemble_mob, blocks_for(nnz, kBlock), kBlock, nnz, cptr, cidx, cols, elem, E, ebuf, Mv, tau,
+                  inv_gamma, with_f, A10, A11);
   return cudaGetLastError();
 }
 
@@ -638,21 +669,15 @@ cudaError_t launch_assemble_mk(long long nnz, const int* cptr, const int* cidx, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_elem_quartic(int dim, int E, const int* elem, const double* psi, double vol, double* ebuf,
+cudaError_t launch_elem_quartic(int nl, int E, const int* elem, const double* psi, double vol, double* ebuf,
                                 cudaStream_t st) {
-  if (dim == 2)
-    k_elem_quartic<6><<<blocks_for(E, 128), 128, 0, st>>>(E, elem, psi, vol, ebuf);
-  else
-    k_elem_quartic<10><<<blocks_for(E, 128), 128, 0, st>>>(E, elem, psi, vol, ebuf);
+  PFC_NL_DISPATCH(nl, k_elem_quartic, blocks_for(E, 128), 128, E, elem, psi, vol, ebuf);
   return cudaGetLastError();
 }
 
-cudaError_t launch_elem_load(int dim, int E, const int* elem, const double* psi, double vol, double* lbuf,
+cudaError_t launch_elem_load(int nl, int E, const int* elem, const double* psi, double vol, double* lbuf,
                              cudaStream_t st) {
-  if (dim == 2)
-    k_elem_load<6><<<blocks_for(E, 128), 128, 0, st>>>(E, elem, psi, vol, lbuf);
-  else
-    k_elem_load<10><<<blocks_for(E, 128), 128, 0, st>>>(E, elem, psi, vol, lbuf);
+  PFC_NL_DISPATCH(nl, k_elem_load, blocks_for(E, 128), 128, E, elem, psi, vol, lbuf);
   return cudaGetLastError();
 }
 

@@ -16,13 +16,14 @@ cudaError_t batch_occupancy(int prec, int* blocks_per_sm);
 cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream);
 
 // element and vector kernels (kernels.cu)
-cudaError_t upload_quartic(int dim, const double* unit_quartic, int npairs);
+// element kernels take the local node count nl: 6 / 10 (P2 triangles / tetrahedra), 3 / 4 (P1)
+cudaError_t upload_quartic(int nl, const double* unit_quartic, int npairs);
 cudaError_t launch_assemble_mk(long long nnz_sell, const int* cptr, const int* cidx, int E, int ntypes, int np,
                                const double* mass_tab, const double* stiff_tab, double* Mv, double* Kv,
                                cudaStream_t st);
-cudaError_t launch_elem_quartic(int dim, int E, const int* elem, const double* psi, double vol, double* ebuf,
+cudaError_t launch_elem_quartic(int nl, int E, const int* elem, const double* psi, double vol, double* ebuf,
                                 cudaStream_t st);
-cudaError_t launch_elem_load(int dim, int E, const int* elem, const double* psi, double vol, double* lbuf,
+cudaError_t launch_elem_load(int nl, int E, const int* elem, const double* psi, double vol, double* lbuf,
                              cudaStream_t st);
 cudaError_t launch_assemble_a01(long long nnz_sell, const int* cptr, const int* cidx, const double* ebuf,
                                 const double* Mv, const double* Kv, double r, double* Av, cudaStream_t st);
@@ -36,12 +37,12 @@ cudaError_t launch_rhs(int nslices, const int* slice_ptr, const int* cols, const
                        double r, double tau, const double* lbuf2, double* b, cudaStream_t st);
 // PFC1 mobility (Eq. 3.10): element values of K_+(psi) and F(mu), element loads
 // (psi^+ grad mu, grad phi), slot assembly of A10 = tau K_+ and A11 = M / gamma + tau F
-cudaError_t upload_pairs(int dim, const int* pair_j, int npairs);
-cudaError_t launch_elem_mobility(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+cudaError_t upload_pairs(int nl, const int* pair_j, int npairs);
+cudaError_t launch_elem_mobility(int nl, int E, int ntypes, const int* elem, const double* psi, const double* mu,
                                  double psi_min, const double* mob, double* ebuf, cudaStream_t st);
-cudaError_t launch_elem_mobload(int dim, int E, int ntypes, const int* elem, const double* psi, const double* mu,
+cudaError_t launch_elem_mobload(int nl, int E, int ntypes, const int* elem, const double* psi, const double* mu,
                                 double psi_min, const double* mob, double* lbuf, cudaStream_t st);
-cudaError_t launch_assemble_mob(int dim, long long nnz, const int* cptr, const int* cidx, const int* cols,
+cudaError_t launch_assemble_mob(int nl, long long nnz, const int* cptr, const int* cidx, const int* cols,
                                 const int* elem, int E, const double* ebuf, const double* Mv, double tau,
                                 double inv_gamma, int with_f, double* A10, double* A11, cudaStream_t st);
 cudaError_t launch_sd_diag_inv(int nslices, const int* sp, const int* cols, const double* Mv, const double* Kv,

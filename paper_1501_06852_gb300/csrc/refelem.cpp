@@ -71,6 +71,17 @@ Mono unit(int k, int p) {
 const int kEdges2[3][2] = {{1, 2}, {0, 2}, {0, 1}};
 const int kEdges3[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
 
+// P1: lambda_k at vertex k
+std::vector<Poly> p1_basis(int dim) {
+  std::vector<Poly> b;
+  for (int k = 0; k <= dim; ++k) {
+    Poly p;
+    p[unit(k, 1)] = 1.0;
+    b.push_back(p);
+  }
+  return b;
+}
+
 std::vector<Poly> p2_basis(int dim) {
   std::vector<Poly> b;
   for (int k = 0; k <= dim; ++k) {
@@ -115,12 +126,16 @@ void local_edge(int dim, int e, int& a, int& b) {
   b = dim == 2 ? kEdges2[e][1] : kEdges3[e][1];
 }
 
-bool build_reference(int dim, double h, RefTensors& out, std::string& err) {
+bool build_reference(int dim, double h, RefTensors& out, std::string& err, int degree) {
   if (dim != 2 && dim != 3) {
     err = "dim must be 2 or 3";
     return false;
   }
-  const int nl = dim == 2 ? 6 : 10;
+  if (degree != 1 && degree != 2) {
+    err = "degree must be 1 or 2";
+    return false;
+  }
+  const int nl = degree == 1 ? dim + 1 : (dim == 2 ? 6 : 10);
   const int ntypes = dim == 2 ? 2 : 6;
   out = RefTensors{};
   out.dim = dim;
@@ -136,7 +151,7 @@ bool build_reference(int dim, double h, RefTensors& out, std::string& err) {
   const int np = (int)out.pair_i.size();
   out.npairs = np;
 
-  std::vector<Poly> phi = p2_basis(dim);
+  std::vector<Poly> phi = degree == 2 ? p2_basis(dim) : p1_basis(dim);
   // unit-volume integrals
   std::vector<double> mref(np), quart((size_t)np * np);
   for (int p = 0; p < np; ++p) mref[p] = integrate(mul(phi[out.pair_i[p]], phi[out.pair_j[p]]), dim);
