@@ -60,6 +60,9 @@ def parse_args(argv=None):
     p.add_argument("--schur", choices=["ch", "sd"], default="ch",
                    help="Schur approximation of the preconditioner: ch (S_CH, default) or sd (S_D, 20 fixed "
                         "PCG iterations); sd with c0 gives the paper's Table 4 comparison")
+    p.add_argument("--degree", type=int, choices=[2, 1], default=2,
+                   help="c0: Lagrange degree, 2 (P2) or 1 (P1 on the same domains with twice the cells per "
+                        "axis, hence the same unknowns; the paper's Tables 3-4 list both)")
     p.add_argument("--requests", type=int, default=300, help="c5: number of requests")
     p.add_argument("--rate", type=float, default=3.0, help="c5: Poisson arrival rate (requests/s)")
     p.add_argument("--instances", type=int, default=256, help="c4: number of instances")
@@ -163,6 +166,9 @@ PAPER_EULER = {2: {0.01: (2.50, 13), 0.1: (3.04, 15), 1.0: (4.53, 19), 10.0: (10
                3: {0.01: (8.01, 17), 0.1: (9.62, 19), 1.0: (14.29, 24), 10.0: (34.94, 58)}}
 # the same with the S_D approximation (Table 4, tau = 0.1 only)
 PAPER_EULER_SD = {2: {0.1: (7.03, 20)}, 3: {0.1: (81.49, 55)}}
+# P1 (Tables 3 and 4, tau = 0.1): S_CH and S_D
+PAPER_EULER_P1 = {2: {0.1: (1.65, 14)}, 3: {0.1: (3.36, 18)}}
+PAPER_EULER_P1_SD = {2: {0.1: (2.72, 16)}, 3: {0.1: (8.14, 21)}}
 
 
 def euler_tables(args):
@@ -175,16 +181,22 @@ def euler_tables(args):
     import paper_1501_06852_gb300 as pfc
 
     rows = []
+    deg = args.degree
+    if deg == 2:
+        paper = PAPER_EULER if args.schur == "ch" else PAPER_EULER_SD
+    else:
+        paper = PAPER_EULER_P1 if args.schur == "ch" else PAPER_EULER_P1_SD
     for w in (synth.C0_2D_EULER, synth.C0_3D_EULER):
-        psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
+        side = w.side * (2 // deg)     # P1: twice the cells, the same vertex lattice as the P2 dofs
+        psi0 = torch.from_numpy(synth.initial_psi(w.dim, side, w.psi_mean, w.amp, w.seed, degree=deg)).cuda()
         for precision in ("fp64", args.precision):
             for tol in (w.outer_tol, 1e-6):
-                with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=tol,
-                                   model=args.model, schur=1 if args.schur == "sd" else 0) as s:
+                with pfc.PFCSolver(w.dim, side, w.length, r=w.r, precision=precision, outer_tol=tol,
+                                   model=args.model, schur=1 if args.schur == "sd" else 0, degree=deg) as s:
                     x0 = s.init_state(psi0)
                     s.set_timing(True)
                     # S_D: the paper's tau = 0.1 and a smaller one (its critical tau is ~0.6 for P2)
-                    for tau in (sorted(PAPER_EULER[w.dim]) if args.schur == "ch" else (0.01, 0.1)):
+                    for tau in (sorted(PAPER_EULER[w.dim]) if args.schur == "ch" and deg == 2 else (0.01, 0.1)):
                         warm = x0.clone()
                         for _ in range(args.warmup):
                             s.euler_step(warm, tau, check=False)
@@ -198,41 +210,42 @@ def euler_tables(args):
                             its.append(st.outer_its)
                             failed += int(st.status != 0)
                         ms1 = s.counters()["solver_ms"]
-                        paper = PAPER_EULER if args.schur == "ch" else PAPER_EULER_SD
                         p_s, p_its = paper[w.dim].get(tau, (None, None))
-                        rows.append({"workload": w.name, "unknowns": w.unknowns, "tau": tau, "precision": precision,
+                        rows.append({"workload": w.name if deg == 2 else f"{w.dim}d-s{side}-P1", "unknowns": w.unknowns,
+                                     "tau": tau, "precision": precision,
                                      "outer_tol": tol, "solve_ms": (ms1 - ms0) / w.steps,
                                      "step_wall_ms": statistics.mean(wall), "outer_its_mean": statistics.mean(its),
                                      "failed_solves": failed, "paper_s": p_s, "paper_its": p_its})
-    head = next(r for r in rows if r["workload"] == synth.C0_2D_EULER.name and r["tau"] == 0.1
+    head = next(r for r in rows if r["workload"].startswith("2d") and r["tau"] == 0.1
                 and r["precision"] == args.precision and r["outer_tol"] == synth.C0_2D_EULER.outer_tol)
-    out = {"metric": "linear solve time of the linearised Euler system, 2D P2, 66,603 unknowns, tau = 0.1",
+    out = {"metric": f"linear solve time of the linearised Euler system, 2D P{deg}, 66,603 unknowns, tau = 0.1",
            "value": head["solve_ms"], "unit": "ms/solve", "n_gpus": 1, "steps": synth.C0_2D_EULER.steps,
            "warmup": args.warmup, "ms_per_step": head["step_wall_ms"], "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": head["solve_ms"] / (1e3 * (PAPER_EULER if args.schur == "ch"
-                                                                            else PAPER_EULER_SD)[2][0.1][0]),
+           "scaling": "weak", "vs_baseline": head["solve_ms"] / (1e3 * paper[2][0.1][0]),
            "dtype": f"f64+{'f32' if args.precision == 'fp32' else 'f16'}", "data": "synthetic",
            "config": {"workload": "the paper's ~66k-unknown solver-table problems: 2D [16d]^2, 74^2 squares, "
                                   "r = psi_bar = -0.35; 3D [3d]^3, 14^3 cubes, r = -0.3, psi_bar = -0.34; "
                                   "d = 4 pi/sqrt(3); noise amp 0.1/0.05; 20 Euler steps per tau from a "
                                   "consistent start; headline at outer tol 1e-8; inputs are L2-resident",
-                      "vs_baseline": ("GPU solve time / the paper's 3.04 s (Table 3, CPU)" if args.schur == "ch"
-                                      else "GPU solve time / the paper's 7.03 s (Table 4, S_D, CPU)"),
+                      "vs_baseline": f"GPU solve time / the paper's {paper[2][0.1][0]} s (P{deg}, "
+                                     f"{'S_CH' if args.schur == 'ch' else 'S_D'}, Tables 3-4, CPU)",
+                      "degree": deg,
                       "model": "PFC2 (H^-1 flow)" if args.model == 2 else "PFC1 (mobility psi + 1.5)",
                       "schur": "S_CH" if args.schur == "ch" else "S_D (20 PCG iterations)"},
            "table": rows}
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = oracle_euler_sample(synth.C0_2D_EULER, args.model)
+        out["cpu_baseline"] = oracle_euler_sample(synth.C0_2D_EULER, args.model, deg)
     return out
 
 
-def oracle_euler_sample(w: synth.Workload, model: int = 2):
+def oracle_euler_sample(w: synth.Workload, model: int = 2, degree: int = 2):
     """The oracle's Euler solve (tau = 0.1, tolerance 1e-8) of the 2D problem, one step."""
     from oracle.mesh import structured_mesh
     from oracle.rosenbrock import PFCProblem, euler_step
 
-    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=model)
-    x0 = prob.consistent_state(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed))
+    side = w.side * (2 // degree)
+    prob = PFCProblem(structured_mesh(w.dim, side, w.length, degree=degree), w.r, model=model)
+    x0 = prob.consistent_state(synth.initial_psi(w.dim, side, w.psi_mean, w.amp, w.seed, degree=degree))
     t0 = time.perf_counter()
     _, st = euler_step(prob, x0, w.tau0, tol=w.outer_tol)
     t = time.perf_counter() - t0
