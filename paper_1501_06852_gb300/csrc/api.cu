@@ -433,9 +433,15 @@ void plan_segments(pfc_ctx* const* ctxs, int count, int max_blocks, std::vector<
 
 // Enqueues the batched FGMRES solves of stage `slot` for every instance: b = ctx->bv,
 // y = ys + slot * 3 n_pad (or tmp3 for slot 3), stats and error word in `slot`.
-pfc_status run_batch(pfc_ctx* const* ctxs, int count, int slot, bool to_tmp, BatchSpace* space, size_t region) {
-  pfc_ctx* c0 = ctxs[0];
-  pfc_ctx* c = c0;
+pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, BatchSpace* space, size_t region) {
+  // Instances are taken largest first, so that when they need several waves each wave
+  // holds instances of similar size (a wave lasts as long as its largest solve).  All
+  // outputs are per context, so the order changes nothing else.
+  std::vector<pfc_ctx*> order(ctxs_in, ctxs_in + count);
+  std::stable_sort(order.begin(), order.end(), [](const pfc_ctx* x, const pfc_ctx* y) { return x->n_pad > y->n_pad; });
+  pfc_ctx* const* ctxs = order.data();
+  pfc_ctx* c0 = ctxs[0];      // stream, device and precision are shared by all
+  pfc_ctx* c = ctxs_in[0];    // errors are reported on the caller's first context
   int occ = 0;
   CK(pfc::batch_occupancy(c0->prec, &occ));
   int sms = 0;
@@ -476,7 +482,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs, int count, int slot, bool to_tmp, Bat
       CK(cudaMemsetAsync(ck->errw + slot, 0, sizeof(int), ck->stream));
       CK(cudaMemsetAsync(ck->stats + slot, 0, sizeof(pfc::DevStats), ck->stream));
     }
-    c = c0;
+    c = ctxs_in[0];
     const size_t bytes = sizeof(pfc::SolveArgs) * n + sizeof(int) * (n + 1);
     CK(cudaMemcpyAsync(dbase + off, hbase + off, bytes, cudaMemcpyHostToDevice, c0->stream));
     pfc::BatchArgs ba;
