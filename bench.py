@@ -311,15 +311,18 @@ def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, v
     (interior rows read no matrix data).
       PCG iteration:       S + 13 n sv (textbook: SpMV; x, r, p, q, D passes)
                            S + 19 n sv (pipelined: SpMV; 9 recurrences read and written, D)
-      PCG set-up (x5 per P_CH): 4 n sv (textbook) or S + 14 n sv (pipelined, incl. w = A u)
+                           S + 15 n sv (Chronopoulos-Gear: u, p, w, s, x, r, D read and p, s, x,
+                                        r, u written; SpMV gathers u, reads r, writes w)
+      PCG set-up (x5 per P_CH): 4 n sv (textbook), S + 14 n sv (pipelined, incl. w = A u) or
+                           S + 9 n sv (Chronopoulos-Gear: x, r, u, s, p written, D read, w = A u)
       P_CH application:    4 (S + n sv) right-hand-side SpMVs + 24 n (v reads) + 4 n sv + 24 n (steps 4, 5)
       outer iteration j:   28 N + 192 n + 96 j n  (A^R SpMV with 3 value streams, MGS, scaling)
       restart cycle:       28 N + 96 n + 24 n (k + 2) (true residual, basis scaling, y update)
     """
     sM, sv = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 4)}[precision]
     S = (nnz if inner_nnz is None else inner_nnz) * (sM + 4)
-    it = S + (19 if variant == 1 else 13) * n * sv
-    setup = (S + 14 * n * sv) if variant == 1 else 4 * n * sv
+    it = S + {1: 19, 3: 15}.get(variant, 13) * n * sv
+    setup = {1: S + 14 * n * sv, 3: S + 9 * n * sv}.get(variant, 4 * n * sv)
     b = st.inner_its * it
     b += st.outer_its * (4 * (S + n * sv) + 24 * n + 4 * n * sv + 24 * n + 5 * setup)
     left = st.outer_its
@@ -491,7 +494,8 @@ def native(args, world, rank, local, pg):
     n = s.n
     nnz = pfc.host_pattern(w.dim, w.side, w.length)["nnz"]
     inner_nnz = pfc.host_stencil(w.dim, w.side, w.length)["boundary_nnz"]   # stencil inner operators
-    variant = 1 if args.precision == "fp64" else 0                           # automatic PCG form
+    # the automatic PCG form of the library: Chronopoulos-Gear for float32/float16 inner solves
+    variant = 1 if args.precision == "fp64" else 3
     state0 = s.init_state(psi0)
     state = state0.clone()
     tau = w.tau0

@@ -24,6 +24,9 @@ def test_stage_solve_bytes_counts_pcg_iterations():
     c = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32", variant=1)
     d = bench.stage_solve_bytes(_St(27, 2700), n, nnz, "fp32", variant=1)
     assert (d - c) / 100 == pytest.approx(8 * nnz + 19 * 4 * n)
+    g = bench.stage_solve_bytes(_St(27, 2600), n, nnz, "fp32", variant=3)
+    h = bench.stage_solve_bytes(_St(27, 2700), n, nnz, "fp32", variant=3)
+    assert (h - g) / 100 == pytest.approx(8 * nnz + 15 * 4 * n)
     f64 = bench.stage_solve_bytes(_St(27, 2500), n, nnz, "fp64")
     assert f64 > a
     assert bench.stage_solve_bytes(_St(0, 0), n, nnz, "fp32") == 28 * nnz + 48 * n
