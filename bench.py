@@ -748,9 +748,14 @@ def profile_case(args):
 
 
 def kernel_source_sha() -> str:
+    """SHA-256 of the stage-solve kernel's source with // comments and blank lines
+    removed: a capture stays valid across comment-only edits, not across code edits."""
     import hashlib
+    import re
 
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_1501_06852_gb300", "csrc", "solver.cu"), "rb").read()).hexdigest()
+    src = open(os.path.join(ROOT, "paper_1501_06852_gb300", "csrc", "solver.cu")).read()
+    code = [re.sub(r"\s*//.*$", "", line).rstrip() for line in src.splitlines()]
+    return hashlib.sha256("\n".join(line for line in code if line).encode()).hexdigest()
 
 
 def main(argv=None):

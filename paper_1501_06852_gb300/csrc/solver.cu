@@ -22,8 +22,9 @@
 // SM count), every block owns a contiguous, nnz-balanced range of SELL-32 slices
 // and the same rows of every vector, and the phases of the algorithm are
 // separated by a grid barrier with a time-bounded spin.  Inside a phase each warp
-// takes groups of kGroup consecutive slices and issues the loads of all of them
-// before it consumes any, so enough bytes are in flight to cover HBM latency.
+// walks its contiguous run of slices (kGroup at a time; 1 by default: wider
+// staging spilled registers), and the block ranges are cut by a cost model that
+// weights the boundary rows' assembled SELL rows above the stencil rows.
 // Dot products reduce in a fixed order (warp shuffles, then block partials
 // summed identically by every block), so all blocks take the same branch
 // decisions and repeated runs are bitwise identical.  The scalar Arnoldi/Givens
