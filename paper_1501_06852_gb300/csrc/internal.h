@@ -70,6 +70,6 @@ bool build_setup(int dim, int side, double length, HostSetup& out, std::string& 
                  int degree = 2);
 
 // Bytes of device memory a context of this size holds (estimate used for admission).
-size_t footprint_estimate(int dim, int side, int restart, int precision, int degree = 2);
+size_t footprint_estimate(int dim, int side, int restart, int precision, int degree = 2, int model = 2);
 
 }  // namespace pfc
