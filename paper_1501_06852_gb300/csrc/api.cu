@@ -569,7 +569,7 @@ size_t pfc_footprint_bytes(int dim, int side, const pfc_options* opt) {
   pfc_default_options(&o);
   if (opt) o = *opt;
   if ((dim != 2 && dim != 3) || side < 1) return 0;
-  return pfc::footprint_estimate(dim, side, o.restart, o.precision, o.degree == 1 ? 1 : 2);
+  return pfc::footprint_estimate(dim, side, o.restart, o.precision, o.degree == 1 ? 1 : 2, o.model == 1 ? 1 : 2);
 }
 
 void pfc_destroy(pfc_ctx* c) {

@@ -300,7 +300,7 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   return true;
 }
 
-size_t footprint_estimate(int dim, int side, int restart, int precision, int degree) {
+size_t footprint_estimate(int dim, int side, int restart, int precision, int degree, int model) {
   const double lat = degree * side + 1.0;
   const double n = dim == 2 ? lat * lat : lat * lat * lat;
   const double nnz_row = degree == 1 ? (dim == 2 ? 7.2 : 15.2) : (dim == 2 ? 11.6 : 28.6);  // slots per row
@@ -315,6 +315,7 @@ size_t footprint_estimate(int dim, int side, int restart, int precision, int deg
   b += E * np * 8 + E * nl * 4 * 2;         // element buffer, element dofs, dof map
   b += n * 8 * 3 * (2.0 * restart + 1 + 8); // Krylov bases and step vectors
   b += n * 8 * 12;                          // inner vectors, diagonals
+  if (model == 1) b += nnz * 8 * 2 + E * np * 8 * 2;  // PFC1: A10, A11 and the wider element buffer
   return (size_t)(b * 1.05) + (64u << 20);
 }
 
