@@ -300,15 +300,16 @@ __device__ bool neighbor_sync(Grid& g, int tag) {
 // barrier every thread of a block loads at most one partial (the grid has at most
 // kThreads blocks), so the read-back is one memory round trip, and the partials
 // are summed in a fixed order.
-template <class T>
+// NV: how many of a, b, c are live (the others are zero and skip their trees).
+template <class T, int NV = 3>
 __device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
   // T is the arithmetic of every stage of the tree: float for the float32 inner
   // solves (float64 throughput is scarce on this GPU), double everywhere else
   __shared__ double4_32a s_w[kWarps];
   __shared__ double4_32a s_res;
   a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
+  if constexpr (NV >= 2) b = warp_sum(b);
+  if constexpr (NV >= 3) c = warp_sum(c);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) s_w[w] = make_double4_32a((double)a, (double)b, (double)c, 0.0);
   __syncthreads();
@@ -323,12 +324,12 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
       tz = (T)t.z;
     }
     tx = warp_sum(tx);
-    ty = warp_sum(ty);
-    tz = warp_sum(tz);
+    if constexpr (NV >= 2) ty = warp_sum(ty);
+    if constexpr (NV >= 3) tz = warp_sum(tz);
     if (l == 0) {
       double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + g.bid);
       __stcg(dst, make_double2((double)tx, (double)ty));
-      __stcg(dst + 1, make_double2((double)tz, 0.0));
+      if constexpr (NV >= 3) __stcg(dst + 1, make_double2((double)tz, 0.0));
     }
   }
   if (!grid_sync(g, tag)) return false;
@@ -337,14 +338,14 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
     T px = T(0), py = T(0), pz = T(0);
     if ((int)threadIdx.x < g.G) {
       const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + threadIdx.x);
-      const double2 t0 = __ldcg(src), t1 = __ldcg(src + 1);
+      const double2 t0 = __ldcg(src);
       px = (T)t0.x;
       py = (T)t0.y;
-      pz = (T)t1.x;
+      if constexpr (NV >= 3) pz = (T)__ldcg(src + 1).x;
     }
     px = warp_sum(px);
-    py = warp_sum(py);
-    pz = warp_sum(pz);
+    if constexpr (NV >= 2) py = warp_sum(py);
+    if constexpr (NV >= 3) pz = warp_sum(pz);
     if (l == 0) s_w[w] = make_double4_32a((double)px, (double)py, (double)pz, 0.0);
   }
   __syncthreads();
@@ -358,8 +359,8 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
       tz = (T)t.z;
     }
     tx = warp_sum(tx);
-    ty = warp_sum(ty);
-    tz = warp_sum(tz);
+    if constexpr (NV >= 2) ty = warp_sum(ty);
+    if constexpr (NV >= 3) tz = warp_sum(tz);
     if (l == 0) s_res = make_double4_32a((double)tx, (double)ty, (double)tz, 0.0);
   }
   __syncthreads();
@@ -617,7 +618,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     }
   }
   double4_32a red;
-  if (!grid_sum<Acc>(g, pb, pz, Acc(0), red, kPhInit)) return false;
+  if (!grid_sum<Acc, 2>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -645,7 +646,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         }
       }
     }
-    if (!grid_sum<Acc>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
+    if (!grid_sum<Acc, 1>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
     const Acc pq = (Acc)red.x;
     if (!isfinite(pq)) {
       flag(g, kErrNonfinite);
@@ -686,7 +687,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
         }
       }
     }
-    if (!grid_sum<Acc>(g, prr, prz, Acc(0), red, kPhVec)) return false;
+    if (!grid_sum<Acc, 2>(g, prr, prz, Acc(0), red, kPhVec)) return false;
     its = it;
     if (!isfinite(red.x)) {
       flag(g, kErrNonfinite);
@@ -761,7 +762,7 @@ __device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, T
     }
   }
   double4_32a red;
-  if (!grid_sum<Acc>(g, pb, pz, Acc(0), red, kPhInit)) return false;
+  if (!grid_sum<Acc, 2>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -802,7 +803,7 @@ __device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, T
         }
       }
     }
-    if (!grid_sum<Acc>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
+    if (!grid_sum<Acc, 1>(g, ppq, Acc(0), Acc(0), red, kPhSpmv)) return false;
     const Acc pq = (Acc)red.x;
     if (!isfinite(pq)) {
       flag(g, kErrNonfinite);
@@ -830,7 +831,7 @@ __device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, T
         }
       }
     }
-    if (!grid_sum<Acc>(g, prr, prz, Acc(0), red, kPhVec)) return false;
+    if (!grid_sum<Acc, 2>(g, prr, prz, Acc(0), red, kPhVec)) return false;
     its = it;
     if (!isfinite(red.x)) {
       flag(g, kErrNonfinite);
@@ -899,7 +900,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
     }
   }
   double4_32a red;
-  if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
+  if (!grid_sum<Acc, 1>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -929,7 +930,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       }
     }
   }
-  if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
+  if (!grid_sum<Acc, 2>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   double gamma = red.x, delta = red.y, gamma_old = 1.0, alpha_old = 1.0;
   for (int it = 0; it < maxit; ++it) {
     if (!isfinite(gamma) || !isfinite(delta)) {
@@ -1043,7 +1044,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
     }
   }
   double4_32a red;
-  if (!grid_sum<Acc>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
+  if (!grid_sum<Acc, 1>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
   const double bb = red.x;
@@ -1070,7 +1071,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
       }
     }
   }
-  if (!grid_sum<Acc>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
+  if (!grid_sum<Acc, 2>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   Acc gam = (Acc)red.x, del = (Acc)red.y;
   if (!(del > Acc(0))) {
     flag(g, kErrBreakdown);
@@ -1117,7 +1118,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
       // reduce (r, r) together with the phase-2 products (the test follows them)
       if (!neighbor_sync(g, kPhVec)) return false;
     } else {
-      if (!grid_sum<Acc>(g, prr, Acc(0), Acc(0), red, kPhVec)) return false;
+      if (!grid_sum<Acc, 1>(g, prr, Acc(0), Acc(0), red, kPhVec)) return false;
       its = it;
       if (!isfinite(red.x)) {
         flag(g, kErrNonfinite);
@@ -1310,7 +1311,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       a.y[f * np + row] = 0.0;
     }
   }
-  if (!grid_sum<double>(g, pb, 0.0, 0.0, red, kPhOuter)) return;
+  if (!grid_sum<double, 1>(g, pb, 0.0, 0.0, red, kPhOuter)) return;
   const double bnorm = sqrt(red.x);
   if (!isfinite(bnorm)) {
     flag(g, kErrNonfinite);
@@ -1336,7 +1337,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       V0[2 * np + row] = r2;
       pr += r0 * r0 + r1 * r1 + r2 * r2;
     }
-    if (!grid_sum<double>(g, pr, 0.0, 0.0, red, kPhOuter)) return;
+    if (!grid_sum<double, 1>(g, pr, 0.0, 0.0, red, kPhOuter)) return;
     const double beta = sqrt(red.x);
     if (!isfinite(beta)) {
       flag(g, kErrNonfinite);
@@ -1375,7 +1376,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
         w[2 * np + row] = w2;
         ph += w0 * V0[row] + w1 * V0[np + row] + w2 * V0[2 * np + row];
       }
-      if (!grid_sum<double>(g, ph, 0.0, 0.0, red, kPhOuter)) return;
+      if (!grid_sum<double, 1>(g, ph, 0.0, 0.0, red, kPhOuter)) return;
       double hij = red.x;
       for (int i = 0; i <= j; ++i) {
         if (threadIdx.x == 0) H[i + j * ld] = hij;
@@ -1391,7 +1392,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
             pn += wv * (vn ? vn[f * np + row] : wv);
           }
         }
-        if (!grid_sum<double>(g, pn, 0.0, 0.0, red, kPhOuter)) return;
+        if (!grid_sum<double, 1>(g, pn, 0.0, 0.0, red, kPhOuter)) return;
         hij = red.x;
       }
       const double hnext = sqrt(hij);

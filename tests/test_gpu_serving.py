@@ -3,7 +3,8 @@
 Four simulations of different sizes and dimensions are advanced three steps each,
 once one at a time with pfc_step and once through the continuous-batching server
 (where they share batched launches).  The final states agree to relative 1e-7
-(three steps of stage solves that each match to the 1e-8 solver tolerance)."""
+(three steps of stage solves that each match to the 1e-8 solver tolerance) and the
+next step widths to 1e-3."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,10 @@ def test_results_alone_and_in_the_mix_agree():
         for k, (x_ref, tau_ref) in enumerate(alone):
             x = srv.sims[k].state.cpu()
             assert float((x - x_ref).norm() / x_ref.norm()) <= 1e-7
-            assert srv.sims[k].tau == pytest.approx(tau_ref, rel=1e-6)
+            # tau_next = tau * 0.9 err^(-1/3), and err is the norm of sum (mhat_j - m_j) y_j,
+            # a combination about 1e-3 the size of the increments: stage solutions that agree
+            # to the solver tolerance (their block partition, hence reduction order, differs
+            # with the batch's composition) move err, and tau, by up to ~1e-4
+            assert srv.sims[k].tau == pytest.approx(tau_ref, rel=1e-3)
     finally:
         srv.close()
