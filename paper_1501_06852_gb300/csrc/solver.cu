@@ -295,73 +295,100 @@ __device__ bool neighbor_sync(Grid& g, int tag) {
   return bad == 0;
 }
 
+// Result of a grid reduction, in the arithmetic of its tree.
+template <class T>
+struct alignas(4 * sizeof(T)) Sum4 {
+  T x, y, z, w;
+};
+
+// A block's partial in its 32-byte ring slot: float4 for a float tree, two
+// double2 (the second only when the third value is live) for a double tree.
+template <class T, int NV>
+__device__ __forceinline__ void store_partial(double4_32a* slot, T x, T y, T z) {
+  if constexpr (sizeof(T) == 4) {
+    __stcg(reinterpret_cast<float4*>(slot), make_float4(x, y, z, 0.f));
+  } else {
+    double2* dst = reinterpret_cast<double2*>(slot);
+    __stcg(dst, make_double2(x, y));
+    if constexpr (NV >= 3) __stcg(dst + 1, make_double2(z, 0.0));
+  }
+}
+
+template <class T, int NV>
+__device__ __forceinline__ void load_partial(const double4_32a* slot, T& x, T& y, T& z) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(slot));
+    x = t.x;
+    y = t.y;
+    z = t.z;
+  } else {
+    const double2* src = reinterpret_cast<const double2*>(slot);
+    const double2 t0 = __ldcg(src);
+    x = t0.x;
+    y = t0.y;
+    if constexpr (NV >= 3) z = __ldcg(src + 1).x;
+  }
+}
+
 // Sum of up to three values over all threads of the grid, identical in every block.
-// Each block publishes its partial (3 doubles in a 32-byte slot); after the
-// barrier every thread of a block loads at most one partial (the grid has at most
+// Each block publishes its partial in a 32-byte ring slot; after the barrier
+// every thread of a block loads at most one partial (the grid has at most
 // kThreads blocks), so the read-back is one memory round trip, and the partials
 // are summed in a fixed order.
 // NV: how many of a, b, c are live (the others are zero and skip their trees).
+// T is the arithmetic and the storage of every stage of the tree: float for the
+// float32 inner solves, double everywhere else.  Nothing is converted between
+// the two on the way: a float64 conversion runs at the scarce float64 rate of
+// this GPU, and the caller's threads would each pay for one per value.
 template <class T, int NV = 3>
-__device__ bool grid_sum(Grid& g, T a, T b, T c, double4_32a& out, int tag) {
-  // T is the arithmetic of every stage of the tree: float for the float32 inner
-  // solves (float64 throughput is scarce on this GPU), double everywhere else
-  __shared__ double4_32a s_w[kWarps];
-  __shared__ double4_32a s_res;
+__device__ bool grid_sum(Grid& g, T a, T b, T c, Sum4<T>& out, int tag) {
+  __shared__ Sum4<T> s_w[kWarps];
+  __shared__ Sum4<T> s_res;
   a = warp_sum(a);
   if constexpr (NV >= 2) b = warp_sum(b);
   if constexpr (NV >= 3) c = warp_sum(c);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) s_w[w] = make_double4_32a((double)a, (double)b, (double)c, 0.0);
+  if (l == 0) s_w[w] = Sum4<T>{a, b, c, T(0)};
   __syncthreads();
   const int slot = g.ring;
   g.ring = (g.ring + 1) % kRing;
   if (w == 0) {
     T tx = T(0), ty = T(0), tz = T(0);
     if (l < kWarps) {
-      const double4_32a t = s_w[l];
-      tx = (T)t.x;
-      ty = (T)t.y;
-      tz = (T)t.z;
+      const Sum4<T> t = s_w[l];
+      tx = t.x;
+      ty = t.y;
+      tz = t.z;
     }
     tx = warp_sum(tx);
     if constexpr (NV >= 2) ty = warp_sum(ty);
     if constexpr (NV >= 3) tz = warp_sum(tz);
-    if (l == 0) {
-      double2* dst = reinterpret_cast<double2*>(g.part + slot * g.G + g.bid);
-      __stcg(dst, make_double2((double)tx, (double)ty));
-      if constexpr (NV >= 3) __stcg(dst + 1, make_double2((double)tz, 0.0));
-    }
+    if (l == 0) store_partial<T, NV>(g.part + slot * g.G + g.bid, tx, ty, tz);
   }
   if (!grid_sync(g, tag)) return false;
   // one partial per thread of the first ceil(G / 32) warps, summed in a fixed order
   if (w * 32 < g.G) {
     T px = T(0), py = T(0), pz = T(0);
-    if ((int)threadIdx.x < g.G) {
-      const double2* src = reinterpret_cast<const double2*>(g.part + slot * g.G + threadIdx.x);
-      const double2 t0 = __ldcg(src);
-      px = (T)t0.x;
-      py = (T)t0.y;
-      if constexpr (NV >= 3) pz = (T)__ldcg(src + 1).x;
-    }
+    if ((int)threadIdx.x < g.G) load_partial<T, NV>(g.part + slot * g.G + threadIdx.x, px, py, pz);
     px = warp_sum(px);
     if constexpr (NV >= 2) py = warp_sum(py);
     if constexpr (NV >= 3) pz = warp_sum(pz);
-    if (l == 0) s_w[w] = make_double4_32a((double)px, (double)py, (double)pz, 0.0);
+    if (l == 0) s_w[w] = Sum4<T>{px, py, pz, T(0)};
   }
   __syncthreads();
   if (w == 0) {
     const int nw = (g.G + 31) >> 5;
     T tx = T(0), ty = T(0), tz = T(0);
     if (l < nw) {
-      const double4_32a t = s_w[l];
-      tx = (T)t.x;
-      ty = (T)t.y;
-      tz = (T)t.z;
+      const Sum4<T> t = s_w[l];
+      tx = t.x;
+      ty = t.y;
+      tz = t.z;
     }
     tx = warp_sum(tx);
     if constexpr (NV >= 2) ty = warp_sum(ty);
     if constexpr (NV >= 3) tz = warp_sum(tz);
-    if (l == 0) s_res = make_double4_32a((double)tx, (double)ty, (double)tz, 0.0);
+    if (l == 0) s_res = Sum4<T>{tx, ty, tz, T(0)};
   }
   __syncthreads();
   out = s_res;
@@ -617,7 +644,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
       }
     }
   }
-  double4_32a red;
+  Sum4<Acc> red;
   if (!grid_sum<Acc, 2>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -628,7 +655,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
     return false;
   }
   if (bb == 0.0) return true;
-  const double thr = rtol * rtol * bb;
+  const Acc thr = (Acc)(rtol * rtol * bb);
   for (int it = 1; it <= maxit; ++it) {
     Acc ppq = Acc(0);
     if (g.staged) stage_window(g, p);
@@ -761,7 +788,7 @@ __device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, T
       }
     }
   }
-  double4_32a red;
+  Sum4<Acc> red;
   if (!grid_sum<Acc, 2>(g, pb, pz, Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -837,7 +864,7 @@ __device__ __noinline__ bool pcg_sd(Grid& g, const SolveArgs& a, const TV* DI, T
       flag(g, kErrNonfinite);
       return false;
     }
-    if (red.x == 0.0) {
+    if (red.x == Acc(0)) {
       cnt.its += it;
       return true;
     }
@@ -899,7 +926,7 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
       }
     }
   }
-  double4_32a red;
+  Sum4<Acc> red;
   if (!grid_sum<Acc, 1>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -1043,7 +1070,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
       }
     }
   }
-  double4_32a red;
+  Sum4<Acc> red;
   if (!grid_sum<Acc, 1>(g, pb, Acc(0), Acc(0), red, kPhInit)) return false;
   its = 0;
   cnt.calls += 1;
@@ -1162,7 +1189,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
     const Acc gnew = (Acc)red.x, dnew = (Acc)red.y;
     beta = gnew / gam;
     const Acc den = dnew - beta * gnew / alpha;
-    if (!(den > Acc(0)) || !isfinite((double)den)) {
+    if (!(den > Acc(0)) || !isfinite(den)) {
       flag(g, kErrBreakdown);
       cnt.its += it;
       return true;
@@ -1300,7 +1327,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   const int np = a.n_pad, n3 = 3 * np, m = a.restart, ld = m + 1;
   const int lane = threadIdx.x & 31;
   InnerCount cnt;
-  double4_32a red;
+  Sum4<double> red;
   double pb = 0.0;
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
