@@ -202,10 +202,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Grid-wide barrier: monotone arrival counter; the k-th barrier of a launch
 // completes when the counter reaches k * G.  The wait is bounded in time: after
 // limit_ns the block sets the timeout bit and the kernel unwinds (false), as it
-// does when another block has already flagged a timeout.
-__device__ bool grid_sync(Grid& g, int tag) {
+// does when it sees, while waiting, that another block has flagged a timeout.
+// The flag is read only inside the wait, so a completed barrier costs no extra
+// memory round trip; a block that passes a barrier after another block timed
+// out stops at the next one, which the timed-out block never reaches.
+// entry_sync = false when the caller has already synchronised the block after
+// its last global write (only thread 0's own stores may follow that barrier).
+__device__ bool grid_sync(Grid& g, int tag, bool entry_sync = true) {
   __shared__ int s_ok;
-  __syncthreads();
+  if (entry_sync) __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t_in = 0;
     if (g.prof) {
@@ -222,6 +227,10 @@ __device__ bool grid_sync(Grid& g, int tag) {
     int ok = 1;
     while (ld_acquire_u32(g.arrive) < target) {
       if ((++spins & 255u) == 0u) {
+        if (ld_relaxed_i32(g.err) & kErrTimeout) {
+          ok = 0;
+          break;
+        }
         const unsigned long long t = global_ns();
         if (t0 == 0) {
           t0 = t;
@@ -232,7 +241,6 @@ __device__ bool grid_sync(Grid& g, int tag) {
         }
       }
     }
-    if (ok && (ld_relaxed_i32(g.err) & kErrTimeout)) ok = 0;
     s_ok = ok;
     if (g.prof) {
       s_t_last = global_ns();
@@ -365,7 +373,8 @@ __device__ bool grid_sum(Grid& g, T a, T b, T c, Sum4<T>& out, int tag) {
     if constexpr (NV >= 3) tz = warp_sum(tz);
     if (l == 0) store_partial<T, NV>(g.part + slot * g.G + g.bid, tx, ty, tz);
   }
-  if (!grid_sync(g, tag)) return false;
+  // every thread's writes precede the __syncthreads above; the partial is thread 0's
+  if (!grid_sync(g, tag, false)) return false;
   // one partial per thread of the first ceil(G / 32) warps, summed in a fixed order
   if (w * 32 < g.G) {
     T px = T(0), py = T(0), pz = T(0);
