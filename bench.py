@@ -76,6 +76,10 @@ def parse_args(argv=None):
     p.add_argument("--profile-case", action="store_true",
                    help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
                         "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
+    p.add_argument("--phases", action="store_true",
+                   help="phase split of one whole stage solve (first stage at tau = 4 after a warm-up solve): "
+                        "the kernel's own clock in block 0 for inner SpMV, inner vector, outer FGMRES and PCG "
+                        "set-up phases and the waits at the grid barriers that end them")
     return p.parse_args(argv)
 
 
@@ -747,6 +751,33 @@ def profile_case(args):
     return 0
 
 
+PHASE_NAMES = ("inner_spmv", "inner_vector", "outer_fgmres", "pcg_setup")
+
+
+def phases(args):
+    import torch
+
+    import paper_1501_06852_gb300 as pfc
+
+    w = workload(args.workload)
+    psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
+    res = {"phases": w.name, "tau": 4.0}
+    for prec in (args.precision, "fp64"):
+        with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=args.outer_tol) as s:
+            x = s.init_state(psi0)
+            s.assemble(x, 4.0)
+            b = s.stage_rhs(0, x)
+            s.stage_solve(b)
+            s.set_timing(True)
+            m0 = s.counters()["solver_ms"]
+            _, st = s.stage_solve(b)
+            ph = list(st.phase_ms)
+            res[prec] = {"ms": s.counters()["solver_ms"] - m0, "outer_its": st.outer_its,
+                         "inner_its": st.inner_its,
+                         "work_ms": dict(zip(PHASE_NAMES, ph[:4])), "wait_ms": dict(zip(PHASE_NAMES, ph[4:]))}
+    return res
+
+
 def kernel_source_sha() -> str:
     """SHA-256 of the stage-solve kernel's source with // comments and blank lines
     removed: a capture stays valid across comment-only edits, not across code edits."""
@@ -764,6 +795,9 @@ def main(argv=None):
         return profile_case(args)
     if args.pcg_sweep:
         return pcg_sweep(args)
+    if args.phases:
+        print(json.dumps(phases(args)), flush=True)
+        return 0
     if args.workload in ("c4", "c5", "c0"):
         out = {"c4": batched, "c5": serve, "c0": euler_tables}[args.workload](args)
         print(json.dumps(out), flush=True)
