@@ -505,6 +505,8 @@ def native(args, world, rank, local, pg):
     tau = w.tau0
     if args.warmup:
         _, _, _, tau, _ = run_steps(s, state, tau, args.warmup, cap, torch)
+    # the end-to-end leg below repeats the timed steps from this state and step width
+    state_t0, tau_t0 = state.clone(), tau
     s.set_timing(True)
     c0 = s.counters()
     clocks = ClockSampler(local)
@@ -596,11 +598,14 @@ def native(args, world, rank, local, pg):
         out["_fp64_outer_mean"] = out["fp64"]["outer_its_mean"]
 
     # ---- end to end through the public API with host buffers ----
+    # the same steps as the timed region (same start state and step width, so the
+    # same trajectory: the solves are deterministic), with each step's state copied
+    # in from pinned host memory and the result copied back inside the timed loop
     if not args.no_e2e:
-        host = state0.cpu().pin_memory()
+        host = state_t0.cpu().pin_memory()
         back = torch.empty_like(host).pin_memory()
         dstate = torch.empty_like(state0)
-        tau = w.tau0
+        tau = tau_t0
         dist_barrier(pg, dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -347,7 +347,7 @@ __device__ __forceinline__ void load_partial(const double4_32a* slot, T& x, T& y
 // T is the arithmetic and the storage of every stage of the tree: float for the
 // float32 inner solves, double everywhere else.  Nothing is converted between
 // the two on the way: a float64 conversion runs at the scarce float64 rate of
-// this GPU, and the caller's threads would each pay for one per value.
+// GB300, and the caller's threads would each pay for one per value.
 template <class T, int NV = 3>
 __device__ bool grid_sum(Grid& g, T a, T b, T c, Sum4<T>& out, int tag) {
   __shared__ Sum4<T> s_w[kWarps];
@@ -635,7 +635,7 @@ __device__ __noinline__ bool pcg_standard(Grid& g, const SolveArgs& a, const TM*
   TV* p = c.vec(kVp);
   TV* q = c.vec(kVq);
   const int lane = threadIdx.x & 31;
-  // per-thread partial sums stay in the inner type (fp64 work is scarce on this GPU);
+  // per-thread partial sums stay in the inner type (fp64 throughput is scarce on GB300);
   // the warp, block and grid sums are float64
   Acc pb = Acc(0), pz = Acc(0);
   FOR_MY_GROUPS(g, s0, nsl) {
