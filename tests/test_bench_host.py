@@ -75,3 +75,13 @@ def test_two_rank_gloo_max_over_ranks():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [2.0, 2.0]
     assert all(r[2] == 30.0 for r in res)
+
+
+def test_metric_name_follows_the_workload():
+    import synth
+
+    assert bench.metric_for(synth.C2_2D_LARGE) == bench.METRIC
+    for w in (synth.C1_2D_SMALL, synth.C3_3D):
+        m = bench.metric_for(w)
+        assert m != bench.METRIC and w.name in m
+        assert f"{w.unknowns / 1e6:.3g}M unknowns" in m
