@@ -134,3 +134,59 @@ def test_mass_positive_definite_and_stiffness_semidefinite():
     assert np.linalg.eigvalsh(M).min() > 0
     ev = np.linalg.eigvalsh(K)
     assert ev.min() > -1e-12 and np.sum(np.abs(ev) < 1e-10) == 1   # only constants in the kernel
+
+
+@pytest.mark.parametrize("dim,side,lengths", [
+    # parity class (x, y[, z] mod 2, x fastest) -> nonzeros of a row with all its elements
+    (2, 12, [19, 9, 9, 9]),
+    (3, 6, [65, 27, 27, 19, 27, 19, 19, 27]),
+])
+def test_interior_row_lengths_per_lattice_parity_class(dim, side, lengths):
+    # P2 dofs are the half-spacing lattice (Section 2); a row couples the nodes of the
+    # elements around it, so rows with every element present have one length per
+    # parity class of the lattice point: vertices (all even) the longest.  The
+    # structured stencils are one table per class, and a warp over 32 consecutive rows
+    # runs to the longest one among them.
+    mesh = structured_mesh(dim, side, float(side))
+    lens = np.diff(assembly.mass_matrix(mesh).tocsr().indptr)
+    m = 2 * side + 1
+    coords = np.stack(np.unravel_index(np.arange(m ** dim), (m,) * dim, order="F"), axis=1)
+    interior = np.all((coords >= 2) & (coords <= m - 3), axis=1)
+    cls = (coords % 2) @ (2 ** np.arange(dim))
+    for c, want in enumerate(lengths):
+        assert set(lens[interior & (cls == c)].tolist()) == {want}
+    if dim == 2:
+        # along an even lattice line classes 0 and 1 alternate, along an odd one 2 and 3:
+        # a 32-row warp loops to the longer stencil rounded up to the table's multiple of 4
+        def pad(k):
+            return (k + 3) // 4 * 4
+
+        issued = 32 * pad(max(lengths[0], lengths[1])) + 32 * pad(max(lengths[2], lengths[3]))
+        useful = 16 * sum(lengths)
+        assert issued / useful == pytest.approx(1024 / 736)
+
+
+@pytest.mark.parametrize("dim,side,ratio", [(2, 512, 1.403), (3, 64, 1.418)])
+def test_warp_uniform_stencil_loop_padding_on_the_benchmark_meshes(dim, side, ratio):
+    # Gathers a 32-row warp issues when every lane loops to the longest interior stencil
+    # among its rows (rounded up to a multiple of 4), against the gathers the rows need,
+    # on the 2D 512^2 and 3D 64^3 meshes.  Interior: the row's incident-element count is
+    # the largest of its parity class (every element around it exists); the lengths per
+    # class are the ones pinned above.
+    lengths = {2: [19, 9, 9, 9], 3: [65, 27, 27, 19, 27, 19, 19, 27]}[dim]
+    mesh = structured_mesh(dim, side, float(side))
+    m = 2 * side + 1
+    n = m ** dim
+    inc = np.bincount(mesh.elem_dofs.ravel(), minlength=n)
+    coords = np.stack(np.unravel_index(np.arange(n), (m,) * dim, order="F"), axis=1)
+    cls = (coords % 2) @ (2 ** np.arange(dim))
+    interior = np.zeros(n, dtype=bool)
+    for c in range(2 ** dim):
+        sel = cls == c
+        interior[sel] = inc[sel] == inc[sel].max()
+    per_row = np.zeros((n + 31) // 32 * 32, dtype=np.int64)
+    per_row[:n] = np.where(interior, np.asarray(lengths)[cls], 0)
+    per_row = per_row.reshape(-1, 32)
+    nmax = per_row.max(axis=1)
+    issued = int(((nmax + 3) // 4 * 4 * 32)[nmax > 0].sum())
+    assert issued / int(per_row.sum()) == pytest.approx(ratio, abs=1e-3)
