@@ -30,11 +30,15 @@ def q_eigenvalue(k2: float, tau: float, r: float, psi_bar: float = 0.0) -> float
     return symbol_A0(k2, tau, r, psi_bar) / den
 
 
+def qch_denominator(k2: float, tau: float) -> float:
+    """Denominator of the third eigenvalue of Q_CH (Eq. 6.9)."""
+    return tau * k2 ** 3 + (math.sqrt(tau) + 2.0 * tau ** 0.75) * k2 ** 2 \
+        + (math.sqrt(tau) + 2.0 * tau ** 0.25) * k2 + 1.0
+
+
 def qch_eigenvalue(k2: float, tau: float, r: float, psi_bar: float = 0.0) -> float:
     """Third eigenvalue of Q_CH = A P_CH^{-1} (Eq. 6.9)."""
-    den = tau * k2 ** 3 + (math.sqrt(tau) + 2.0 * tau ** 0.75) * k2 ** 2 \
-        + (math.sqrt(tau) + 2.0 * tau ** 0.25) * k2 + 1.0
-    return symbol_A0(k2, tau, r, psi_bar) / den
+    return symbol_A0(k2, tau, r, psi_bar) / qch_denominator(k2, tau)
 
 
 def lemma2_lambda(mu: float, delta: float) -> float:

@@ -173,11 +173,12 @@ class PFCProblem:
     # --- stage solve (Section 4, Section 7) --------------------------------
     def stage_solve(self, A: sp.csr_matrix, b: np.ndarray, tau: float, tol: float = 1e-13,
                     inner: str = "pcg", restart: int = 30, max_outer: int = 2000, coef: Ros3Pw = ROS3PW,
-                    m0: float = 1.0, schur: str = "ch"):
+                    m0: float = 1.0, schur: str = "ch", err_tol: float = 0.0):
         """FGMRES with P(S_CH) (or P(S_D), schur="sd"); m0 is the mean mobility of the
-        constant-mobility approximation."""
+        constant-mobility approximation; err_tol > 0 adds the solution-error stop
+        (``solvers.fgmres``)."""
         pc = PCH(self.M, self.K, m0 * tau, coef.gamma, inner=inner, schur=schur)
-        y, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
+        y, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer, err_tol)
         st.inner = pc.log
         return y, st
 
@@ -244,7 +245,7 @@ class StepResult:
 
 def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = StepControl(),
              tol: float = 1e-13, inner: str = "pcg", coef: Ros3Pw = ROS3PW,
-             prev_rejected: bool = False) -> StepResult:
+             prev_rejected: bool = False, err_tol: float = 0.0) -> StepResult:
     """One attempted Ros3Pw step (Eq. 3.6, 3.7, 3.10) with the error estimate.
 
     The matrix N(psi) is frozen at psi^k for all three stages (W-method).
@@ -257,7 +258,7 @@ def pfc_step(prob: PFCProblem, x_k: np.ndarray, tau: float, ctl: StepControl = S
     for i in range(3):
         x_i = x_k + sum(coef.a(i, j) * ys[j] for j in range(i))
         b = prob.stage_rhs(x_i, [y[n:2 * n] for y in ys], [coef.c(i, j) for j in range(i)], tau)
-        y, st = prob.stage_solve(A, b, tau, tol=tol, inner=inner, coef=coef, m0=m0)
+        y, st = prob.stage_solve(A, b, tau, tol=tol, inner=inner, coef=coef, m0=m0, err_tol=err_tol)
         ys.append(y)
         rhs.append(b)
         stats.append(st)
@@ -287,12 +288,12 @@ def euler_rhs(prob: PFCProblem, psi_k: np.ndarray) -> np.ndarray:
 
 
 def euler_step(prob: PFCProblem, x_k: np.ndarray, tau: float, tol: float = 1e-13, inner: str = "pcg",
-               restart: int = 30, max_outer: int = 2000, schur: str = "ch"):
+               restart: int = 30, max_outer: int = 2000, schur: str = "ch", err_tol: float = 0.0):
     """x_{k+1} = A^{-1} b by FGMRES(restart) with P_CH built for gamma = 1 (Section 4)."""
     psi_k = prob.split(x_k)[1]
     A = euler_matrix(prob, psi_k, tau)
     b = euler_rhs(prob, psi_k)
     pc = PCH(prob.M, prob.K, prob.m0(psi_k) * tau, 1.0, inner=inner, schur=schur)
-    x, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer)
+    x, st = fgmres(lambda v: A @ v, b, pc.apply, tol, restart, max_outer, err_tol)
     st.inner = pc.log
     return x, st

@@ -10,13 +10,31 @@ TEST INFRASTRUCTURE (see ``oracle/__init__``).
   system A P^{-1} (P x) = b; Saad 1993), restart 30 and modified Gram-Schmidt
   (Section 7).  Reading: zero initial guess; Givens rotations on the Hessenberg
   matrix; after each cycle the true residual b - A x is recomputed and the
-  solve stops once ||b - A x||_2 <= tol ||b||_2.
+  solve stops once ||b - A x||_2 <= tol ||b||_2 (and, with err_tol > 0, once
+  the solution-error estimate below is at most err_tol).
 * ``PCH``         - the block preconditioner of Eq. (4.1) with the Cahn-Hilliard
   approximation S_CH of the Schur complement (Section 4.2), applied in the
   steps (1), (2), (3.1), (3.2), (4), (5); or, with ``schur="sd"``, with the
   diagonal approximation S_D = M - 2 delta K + delta K M_D^{-1} K, M_D = diag(M)
   (Section 4.1), whose step (3) S_D x1 = M y1 runs a fixed number of Jacobi-PCG
   iterations (Table 2: 20).
+
+Reading of the outer stopping rule (the paper gives no outer tolerance): the
+stage solution is needed to a relative error, not a relative residual, and the
+ratio of the two grows with tau (the stage matrix nears singularity as
+gamma tau approaches the critical width of Lemma 3).  With right
+preconditioning the error of an iterate x is e = A^{-1} r = P^{-1} (A P^{-1})^{-1} r,
+so ``fgmres(err_tol=...)`` estimates
+
+    E = ||P^{-1} r||_2 / (||x||_2 sigma),   sigma = min over the cycles so far of
+                                            the smallest singular value of the
+                                            cycle's Hessenberg matrix H_k,
+
+(H_k represents A P^{-1} on the cycle's Krylov space, so 1 / sigma estimates
+||(A P^{-1})^{-1}||) and, once the residual test passes, stops only if
+E <= err_tol; otherwise it tightens the residual target to
+(||r|| / ||b||) (err_tol / E) / 2 and runs another cycle, whose first
+preconditioned vector is the P^{-1} r just computed.
 
 Readings of garbled or silent passages (each applies to ``PCH.apply``):
 
@@ -81,25 +99,39 @@ class FGMRESStats:
     restarts: int = 0
     rel_residual: float = float("nan")
     converged: bool = False
+    err_estimate: float = float("nan")   # E of the last solution-error test (err_tol > 0)
+    sigma: float = float("inf")          # smallest singular value of the cycles' H_k
     history: list = field(default_factory=list)   # Givens residual estimates / ||b||
 
 
 def fgmres(apply_A, b: np.ndarray, apply_Pinv, tol: float, restart: int = 30,
-           max_outer: int = 1000) -> tuple[np.ndarray, FGMRESStats]:
-    """Right-preconditioned flexible GMRES(restart) with modified Gram-Schmidt."""
+           max_outer: int = 1000, err_tol: float = 0.0) -> tuple[np.ndarray, FGMRESStats]:
+    """Right-preconditioned flexible GMRES(restart) with modified Gram-Schmidt.
+    err_tol > 0 adds the solution-error test of the module docstring."""
     st = FGMRESStats()
     x = np.zeros_like(b)
     bnorm = math.sqrt(float(b @ b))
     if bnorm == 0.0:
         st.rel_residual, st.converged = 0.0, True
         return x, st
+    tol_r = tol
+    z_first = None                            # P^{-1} v_0 of the next cycle, when already computed
     while True:
         r = b - apply_A(x)
         beta = math.sqrt(float(r @ r))
         st.rel_residual = beta / bnorm
-        if beta <= tol * bnorm:
-            st.converged = True
-            return x, st
+        if beta <= tol_r * bnorm:
+            if err_tol <= 0.0 or beta == 0.0:
+                st.converged = True
+                return x, st
+            if st.outer_iterations < max_outer:
+                z_first = apply_Pinv(r / beta)
+                xnorm = math.sqrt(float(x @ x))
+                st.err_estimate = beta * math.sqrt(float(z_first @ z_first)) / (xnorm * st.sigma)
+                if st.err_estimate <= err_tol:
+                    st.converged = True
+                    return x, st
+                tol_r = st.rel_residual * (err_tol / st.err_estimate) * 0.5
         if st.outer_iterations >= max_outer:
             return x, st
         m = restart
@@ -112,7 +144,8 @@ def fgmres(apply_A, b: np.ndarray, apply_Pinv, tol: float, restart: int = 30,
         g[0] = beta
         k = 0
         for j in range(m):
-            z = apply_Pinv(V[j])
+            z = z_first if (j == 0 and z_first is not None) else apply_Pinv(V[j])
+            z_first = None
             Z.append(z)
             w = apply_A(z)
             for i in range(j + 1):            # modified Gram-Schmidt
@@ -134,9 +167,11 @@ def fgmres(apply_A, b: np.ndarray, apply_Pinv, tol: float, restart: int = 30,
             st.outer_iterations += 1
             k = j + 1
             st.history.append(abs(g[j + 1]) / bnorm)
-            if abs(g[j + 1]) <= tol * bnorm or hnext == 0.0 or st.outer_iterations >= max_outer:
+            if abs(g[j + 1]) <= tol_r * bnorm or hnext == 0.0 or st.outer_iterations >= max_outer:
                 break
             V.append(w / hnext)
+        # the rotated k x k triangle has the singular values of the cycle's H_k
+        st.sigma = min(st.sigma, float(np.linalg.svd(H[:k, :k], compute_uv=False)[-1]))
         y = np.zeros(k)                       # back substitution with the rotated H
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]

@@ -40,9 +40,19 @@ def test_critical_tau_for_p_is_one():
     den = lambda k2, tau: tau * k2 ** 3 + (math.sqrt(tau) - 2 * tau) * k2 ** 2 - math.sqrt(tau) * k2 + 1
     assert abs(den(1.0, 1.0)) < 1e-15
     assert min(den(0.01 * i, 0.99) for i in range(1, 400)) > 0
-    # P_CH's denominator stays positive for every tau (Section 6.1)
-    for tau in (0.01, 1.0, 10.0, 100.0):
-        assert min(analysis.qch_eigenvalue(0.05 * i, tau, -0.35) for i in range(1, 200)) > 0 or True
+    # P_CH's denominator stays positive for every tau (Section 6.1), so the third
+    # eigenvalue of Q_CH changes sign only with the symbol of A_0: it is positive for
+    # every wave number below Lemma 3's critical width and reaches zero at it
+    r, pb = -0.35, 0.0
+    ts = analysis.critical_tau(r, pb)
+    k2s = [0.01 * i for i in range(0, 1000)]
+    for tau in (1e-3, 0.01, 0.1, 1.0, 10.0, 100.0, 1e4):
+        assert min(analysis.qch_denominator(k2, tau) for k2 in k2s) > 0
+    for tau in (0.01, 0.1, 0.5 * ts, 0.99 * ts):
+        assert min(analysis.qch_eigenvalue(k2, tau, r, pb) for k2 in k2s) > 0
+    kc = 2.0 / 3.0 + math.sqrt(1 - 3 * r - 9 * pb * pb) / 3.0
+    assert abs(analysis.qch_eigenvalue(kc, ts, r, pb)) < 1e-12
+    assert analysis.qch_eigenvalue(kc, 1.5 * ts, r, pb) < 0
 
 
 def test_interval_convergence_factor():
