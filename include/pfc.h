@@ -108,6 +108,25 @@ typedef struct {
   int schur_its;      /* fixed PCG iterations of the S_D step (>= 1) */
   int degree;         /* Lagrange degree of V_h (Section 3): 2 (P2, default) or 1 (P1,
                          dofs on the mesh vertices, n = (side + 1)^dim per field) */
+  double err_tol;     /* > 0: a stage solve also stops only once its estimated relative
+                         solution error ||y - y*|| / ||y|| is at most err_tol; 0: the
+                         residual test alone.  The paper fixes no outer tolerance
+                         (Section 7); the stage solution is wanted to a relative error,
+                         and the ratio of error to residual grows with tau as the stage
+                         matrix of Eq. (3.10) nears the singularity of Lemma 3 (four
+                         orders of magnitude at 0.9 tau*).  With right preconditioning
+                         y - y* = P^{-1} (A^R P^{-1})^{-1} r, so once the residual test
+                         passes the solver estimates E = ||P^{-1} r|| / (||y|| sigma),
+                         sigma = the smallest singular value of the Hessenberg matrices
+                         of its restart cycles so far, stops if E <= err_tol and otherwise
+                         tightens its residual target to (||r|| / ||b||)(err_tol / E) / 2.
+                         The ratio E / (||r|| / ||b||) of a context's last tested solve sets
+                         the starting residual target of its next solve (scaled by the
+                         ratio of the widths tau).  Default 1e-9. */
+  double tau_guard;   /* > 0 (PFC2 only): pfc_step caps the next width so that gamma tau <=
+                         tau_guard tau*(r, <psi>), tau* the critical width of Lemma 3 at the
+                         mean density <psi> of the state (conserved by the flow); must be
+                         < 1; 0 (default): no cap beyond tau_max */
 } pfc_options;
 
 typedef struct {
@@ -121,13 +140,26 @@ typedef struct {
   double phase_ms[8];   /* with pfc_set_timing on: block 0's time in [inner SpMV phases,
                            inner vector phases, outer FGMRES phases, PCG set-up phases]
                            (work), then the same four classes of barrier waits */
+  double err_est;       /* the solution-error estimate E of the last test (options.err_tol);
+                           NaN when no test ran */
+  double sigma_min;     /* smallest singular value of the restart cycles' Hessenberg
+                           matrices (estimate of that of A^R P^{-1}); inf when none */
 } pfc_solve_stats;
 
 /* Fills the defaults: r = -0.4, outer_tol = 1e-10, inner_rtol = 1e-3,
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
- * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20, degree = 2. */
+ * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20, degree = 2,
+ * err_tol = 1e-9, tau_guard = 0. */
 void pfc_default_options(pfc_options* opt);
+
+/* Critical time-step width of Lemma 3 (Section 6): the symbol of the PFC2 operator
+ * linearised about the constant density psi_bar has the eigenvalue zero once the
+ * effective width (gamma tau in a Rosenbrock stage) reaches
+ *   tau* = 27 / (2 (sqrt(alpha) - 1)(sqrt(alpha) + 2)^2),  alpha = 1 - 3 r - 9 psi_bar^2.
+ * Returns +infinity when alpha <= 1 (psi_bar^2 >= -r / 3: no critical width).
+ * Host only; no context, no GPU. */
+double pfc_critical_tau(double r, double psi_bar);
 
 /* Mesh, P2 dof map, shared SELL-32 sparsity pattern of all blocks, and the
  * constant M and K (Section 3, the matrices below Eq. 3.4).  dim is 2 or 3,
@@ -177,7 +209,7 @@ pfc_status pfc_stage_solve(pfc_ctx* ctx, const double* b, double* y,
  * e = sum (mhat_j - m_j) dpsi_j.  If err <= 1 the step is accepted and state
  * (3n, device, in/out) is overwritten with x^{k+1}; otherwise state is left
  * unchanged.  *tau (in/out) becomes tau * min(5, max(0.2, 0.9 err^(-1/3))),
- * capped at tau_max; an accepted step that follows a rejected one (on this
+ * capped at tau_max (and by options.tau_guard); an accepted step that follows a rejected one (on this
  * context) does not grow tau (Hairer-Wanner's rule after a rejection).  stats (may be NULL) receives 3 entries.  One host
  * synchronisation per call. */
 pfc_status pfc_step(pfc_ctx* ctx, double* state, double* tau, int* accepted,
@@ -285,8 +317,9 @@ pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3);
  * call's contents; each call overwrites the partials it reads, so nothing needs
  * clearing, but two calls whose kernels overlap on the GPU (different streams, or
  * several host threads) race on it and must be serialised by the caller.
- * Returns PFC_ERR_INVALID for n < 1, n > (2^31 - 1) / 3, null pointers or bad
- * tolerances, PFC_ERR_CUDA if a launch fails. */
+ * Returns PFC_ERR_INVALID for n < 1, n > 715740501 (= (2^31 - 1 - 2^18) / 3: the
+ * kernel's 32-bit index, stepping by 2^18, must not pass 2^31 - 1 on its way past
+ * 3n), null pointers or bad tolerances, PFC_ERR_CUDA if a launch fails. */
 pfc_status pfc_step_combine_static(int64_t n, const double* state, const double* y, double atol, double rtol,
                                    double* state_new, double* err, void* cuda_stream);
 

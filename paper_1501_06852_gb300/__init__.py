@@ -13,7 +13,6 @@ its sources and then loads it; if it cannot be built or loaded the import fails
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from dataclasses import dataclass
 
@@ -42,13 +41,16 @@ class _Options(ctypes.Structure):
                 ("psi_min", ctypes.c_double),
                 ("schur", ctypes.c_int),
                 ("schur_its", ctypes.c_int),
-                ("degree", ctypes.c_int)]
+                ("degree", ctypes.c_int),
+                ("err_tol", ctypes.c_double),
+                ("tau_guard", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("outer_its", ctypes.c_int), ("restarts", ctypes.c_int), ("inner_its", ctypes.c_longlong),
                 ("inner_calls", ctypes.c_int), ("inner_capped", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int), ("phase_ms", ctypes.c_double * 8)]
+                ("rel_residual", ctypes.c_double), ("status", ctypes.c_int), ("phase_ms", ctypes.c_double * 8),
+                ("err_est", ctypes.c_double), ("sigma_min", ctypes.c_double)]
 
 
 def _load():
@@ -84,6 +86,7 @@ def _load():
                              ctypes.POINTER(D)]),
         "pfc_last_error": (ctypes.c_char_p, [P]),
         "pfc_status_string": (ctypes.c_char_p, [I]),
+        "pfc_critical_tau": (D, [D, D]),
         "pfc_destroy": (V, [P]),
     }
     for name, (res, args) in sig.items():
@@ -112,21 +115,18 @@ class SolveStats:
     rel_residual: float
     status: int
     phase_ms: tuple = ()
+    err_est: float = float("nan")
+    sigma_min: float = float("inf")
 
     @classmethod
     def _from(cls, s: _Stats) -> "SolveStats":
         return cls(s.outer_its, s.restarts, s.inner_its, s.inner_calls, s.inner_capped, s.rel_residual, s.status,
-                   tuple(s.phase_ms))
+                   tuple(s.phase_ms), s.err_est, s.sigma_min)
 
 
 def critical_tau(r: float, psi_bar: float) -> float:
-    """Critical time-step width of the linearised operator (Lemma 3):
-    27 / (2 (sqrt(a) - 1)(sqrt(a) + 2)^2) with a = 1 - 3 r - 9 psi_bar^2; inf if a <= 1."""
-    a = 1.0 - 3.0 * r - 9.0 * psi_bar * psi_bar
-    if a <= 1.0:
-        return math.inf
-    s = math.sqrt(a)
-    return 27.0 / (2.0 * (s - 1.0) * (s + 2.0) ** 2)
+    """Critical time-step width of Lemma 3, from the library (pfc_critical_tau); inf when none."""
+    return float(lib.pfc_critical_tau(float(r), float(psi_bar)))
 
 
 def default_options() -> dict:
@@ -204,7 +204,8 @@ class PFCSolver:
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
                  inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
-                 schur: int = 0, schur_its: int = 20, degree: int = 2, stream=None):
+                 schur: int = 0, schur_its: int = 20, degree: int = 2, err_tol: float = 1e-9,
+                 tau_guard: float = 0.0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -226,6 +227,8 @@ class PFCSolver:
         o.schur = schur
         o.schur_its = schur_its
         o.degree = degree
+        o.err_tol = err_tol
+        o.tau_guard = tau_guard
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()

@@ -91,6 +91,8 @@ struct pfc_ctx {
   pfc::DevStats* stats = nullptr;   // 4 slots
   double* step_part = nullptr;
   double* err_scalar = nullptr;
+  double* kappa = nullptr;      // {error / residual ratio, tau} of the last error-tested solve
+
   // pinned host mirrors
   pfc::DevStats* h_stats = nullptr;
   double* h_err = nullptr;
@@ -182,6 +184,8 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.tau_e = c->gamma * c->tau * c->m0;  // PFC1: constant-mobility approximation K_+ ~ M0 K
   a.inv_delta = c->delta > 0 ? 1.0 / c->delta : 0.0;
   a.tol = c->opt.outer_tol;
+  a.err_tol = c->opt.err_tol;
+  a.kappa = c->kappa;
   a.inner_rtol = c->opt.inner_rtol;
   a.restart = c->opt.restart;
   a.max_outer = c->opt.max_outer;
@@ -224,6 +228,37 @@ pfc_status status_from_err(int err) {
   return PFC_OK;
 }
 
+// Lemma 3 (Section 6): the symbol of the linearised PFC2 operator about a constant
+// density psi_bar reaches zero once the effective width gamma tau is at least
+// tau* = 27 / (2 (sqrt(alpha) - 1)(sqrt(alpha) + 2)^2), alpha = 1 - 3 r - 9 psi_bar^2;
+// for alpha <= 1 (psi_bar^2 >= -r / 3) there is no critical width (infinity).
+double critical_tau(double r, double psi_bar) {
+  const double alpha = 1.0 - 3.0 * r - 9.0 * psi_bar * psi_bar;
+  if (!(alpha > 1.0)) return INFINITY;
+  const double sa = std::sqrt(alpha);
+  return 27.0 / (2.0 * (sa - 1.0) * (sa + 2.0) * (sa + 2.0));
+}
+
+// Mean density <psi^k> = (int psi^k) / |Omega| onto c->err_scalar[1] (after the step
+// reduction has consumed c->step_part), for the width guard of pfc_step.
+pfc_status enqueue_mean_psi(pfc_ctx* c) {
+  const int parts = pfc::step_partials();
+  LAUNCH(pfc::launch_dot_partials(c->n_pad, c->wint, c->xk + c->n_pad, c->step_part, parts, c->stream));
+  LAUNCH(pfc::launch_sum_partials(parts, c->step_part, 1.0 / std::pow(c->length, c->dim), c->err_scalar + 1,
+                                  c->stream));
+  return PFC_OK;
+}
+
+bool width_guard_on(const pfc_ctx* c) { return c->opt.tau_guard > 0.0 && c->model == 2; }
+
+// Upper bound of the next step width: tau_max, and with the guard on (PFC2)
+// gamma tau <= tau_guard tau*(r, <psi^k>).
+double width_cap(const pfc_ctx* c, double mean_psi) {
+  double cap = c->opt.tau_max;
+  if (width_guard_on(c)) cap = std::min(cap, c->opt.tau_guard * critical_tau(c->opt.r, mean_psi) / kGamma);
+  return cap;
+}
+
 // Enqueue one persistent-kernel launch; stats go to c->stats[slot].
 pfc_status run_solver(pfc_ctx* c, pfc::SolveArgs a, int prec, int slot) {
   a.stats = c->stats + slot;
@@ -261,6 +296,8 @@ void fill_stats(const pfc::DevStats& d, int err, pfc_solve_stats* s) {
   s->rel_residual = d.rel_residual;
   s->status = status_from_err(err);
   for (int k = 0; k < 8; ++k) s->phase_ms[k] = d.prof_ns[k] * 1e-6;
+  s->err_est = d.err_est;
+  s->sigma_min = d.sigma;
 }
 
 // b^R from the stage value c->xi and (when with_d) d = sum c_ij dpsi_j in c->dvec:
@@ -542,7 +579,11 @@ void pfc_default_options(pfc_options* o) {
   o->schur = 0;
   o->schur_its = 20;
   o->degree = 2;
+  o->err_tol = 1e-9;
+  o->tau_guard = 0.0;
 }
+
+double pfc_critical_tau(double r, double psi_bar) { return critical_tau(r, psi_bar); }
 
 const char* pfc_status_string(int s) {
   switch (s) {
@@ -613,6 +654,10 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if ((c->opt.schur != 0 && c->opt.schur != 1) || c->opt.schur_its < 1)
     return bail(fail(c, PFC_ERR_INVALID, "schur must be 0 (S_CH) or 1 (S_D) and schur_its >= 1"));
   if (c->opt.degree != 1 && c->opt.degree != 2) return bail(fail(c, PFC_ERR_INVALID, "degree must be 1 or 2"));
+  if (!(c->opt.err_tol >= 0.0) || !std::isfinite(c->opt.err_tol))
+    return bail(fail(c, PFC_ERR_INVALID, "err_tol must be finite and >= 0"));
+  if (!(c->opt.tau_guard >= 0.0) || !(c->opt.tau_guard < 1.0))
+    return bail(fail(c, PFC_ERR_INVALID, "tau_guard must be in [0, 1)"));
   c->model = c->opt.model;
   c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
@@ -791,6 +836,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_stats = L.take(sizeof(pfc::DevStats) * 4);
   const size_t o_sp = L.take(sizeof(double) * pfc::step_partials());
   const size_t o_es = L.take(sizeof(double) * 2);
+  const size_t o_kappa = L.take(sizeof(double) * 2);
   size_t o_a10 = 0, o_a11 = 0, o_mob = 0;
   if (c->model == 1) {
     o_a10 = L.take(sizeof(double) * S.nnz_sell);
@@ -865,6 +911,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->stats = (pfc::DevStats*)(A + o_stats);
   c->step_part = (double*)(A + o_sp);
   c->err_scalar = (double*)(A + o_es);
+  c->kappa = (double*)(A + o_kappa);
   c->wint = (double*)(A + o_wint);
   c->dSD = (double*)(A + o_dsd);
   c->fdSD = (float*)(A + o_fdsd);
@@ -1023,9 +1070,13 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   LAUNCH(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
                               c->xnew, c->step_part, pfc::step_partials(), c->stream));
   LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
+  if (width_guard_on(c)) {
+    st = enqueue_mean_psi(c);
+    if (st != PFC_OK) return st;
+  }
   CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   harvest(c);
   int werr = 0;
@@ -1046,7 +1097,7 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
   if (acc && c->last_rejected) fac = std::min(fac, 1.0);  // no growth right after a rejection
   c->last_rejected = !acc;
-  *tau = std::min(*tau * fac, c->opt.tau_max);
+  *tau = std::min(*tau * fac, width_cap(c, c->h_err[1]));
   if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
   return PFC_OK;
 }
@@ -1287,9 +1338,13 @@ pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states
     LAUNCH(pfc::launch_step_combine(np, ck->xk, ck->ys, ck->ys + np3, ck->ys + 2 * np3, kM, e, ck->opt.step_atol,
                                     ck->opt.step_rtol, ck->xnew, ck->step_part, pfc::step_partials(), ck->stream));
     LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), ck->step_part, 1.0 / ck->n, ck->err_scalar, ck->stream));
+    if (width_guard_on(ck)) {
+      st = enqueue_mean_psi(ck);
+      if (st != PFC_OK) return st;
+    }
     CK(cudaMemcpyAsync(ck->h_stats, ck->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, ck->stream));
     CK(cudaMemcpyAsync(ck->h_errw, ck->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, ck->stream));
-    CK(cudaMemcpyAsync(ck->h_err, ck->err_scalar, sizeof(double), cudaMemcpyDeviceToHost, ck->stream));
+    CK(cudaMemcpyAsync(ck->h_err, ck->err_scalar, sizeof(double) * 2, cudaMemcpyDeviceToHost, ck->stream));
   }
   c = ctxs[0];
   CK(cudaStreamSynchronize(c->stream));
@@ -1316,7 +1371,7 @@ pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states
     double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
     if (acc && ck->last_rejected) fac = std::min(fac, 1.0);
     ck->last_rejected = !acc;
-    taus[k] = std::min(taus[k] * fac, ck->opt.tau_max);
+    taus[k] = std::min(taus[k] * fac, width_cap(ck, ck->h_err[1]));
     if (sk != PFC_OK && worst == PFC_OK) worst = sk;
   }
   c = ctxs[0];

@@ -27,6 +27,8 @@ struct DevStats {
   int err;
   int last_its;        // iterations of a single PCG solve (pcg mode)
   long long prof_ns[8];  // block 0: work / barrier-wait time per phase class (when profiling)
+  double err_est;      // last solution-error estimate E (err_tol > 0; NaN when never tested)
+  double sigma;        // smallest singular value of the cycles' Hessenberg matrices (inf: none)
 };
 
 // Arguments of the persistent solver kernel.  Inner arrays are typed by the
@@ -50,6 +52,9 @@ struct SolveArgs {
   const void* dMsK;
   double tau, gamma, inv_gamma, tau_e, inv_delta;
   double tol, inner_rtol;
+  double err_tol;          // > 0: FGMRES also stops only once its solution-error estimate is <= err_tol
+  double* kappa;           // err_tol > 0: {error / residual ratio, tau} of the context's last tested
+                           //   solve (read at the start to set the residual target, written at the end)
   int restart, max_outer, max_inner;
   int mode;                // 0 FGMRES stage solve, 1 one P_CH application, 2 one PCG solve
   int which;               // mode 2: 0 M, 1 M + delta K, 2 M + sqrt(delta) K

@@ -24,8 +24,12 @@ namespace {
 constexpr int kStaticParts = 1024;
 __device__ __align__(256) static double g_step_scratch[kStaticParts];
 
-// Largest n: the combination kernel indexes 3n entries with 32-bit ints.
-constexpr int64_t kStaticMaxN = (int64_t)0x7fffffff / 3;
+// Largest n: the combination kernel walks 3n entries with a 32-bit int index in
+// steps of (its kStaticParts blocks x 256 threads); the last step must not pass
+// INT_MAX, so 3n + kStaticParts * 256 <= 2^31 - 1.
+constexpr int64_t kStaticStride = (int64_t)kStaticParts * 256;
+constexpr int64_t kStaticMaxN = ((int64_t)0x7fffffff - kStaticStride) / 3;
+static_assert(kStaticMaxN == 715740501, "limit stated in pfc.h");
 
 // Ros3Pw weights m and mhat (Table 1); the error vector is sum (mhat_j - m_j) y_j.
 constexpr double kStaticM[3] = {1.63397459621556, 0.294228634059948, 1.07179676972449};

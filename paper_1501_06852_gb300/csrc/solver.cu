@@ -1309,8 +1309,11 @@ __device__ __forceinline__ void block_row(const SolveArgs& a, const double* z, i
   w2 = k_psi + m_om;
 }
 
+constexpr double kNaN = __builtin_nan("");
+constexpr double kInf = __builtin_inf();
+
 __device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts, const InnerCount& cnt, double rel,
-                            double bnorm, int last_its) {
+                            double bnorm, int last_its, double err_est = kNaN, double sigma = kInf) {
   if (g.bid == 0 && threadIdx.x == 0) {
     DevStats st;
     st.outer_its = outer;
@@ -1323,20 +1326,93 @@ __device__ void write_stats(Grid& g, const SolveArgs& a, int outer, int restarts
     st.err = 0;
     st.last_its = last_its;
     for (int k = 0; k < 8; ++k) st.prof_ns[k] = s_prof[k];
+    st.err_est = err_est;
+    st.sigma = sigma;
     *a.stats = st;
   }
 }
 
+// Inverse iterations on R^T R for the solution-error estimate of fgmres.
+constexpr int kSigmaIts = 16;
+
+// Smallest singular value of the k x k upper triangle R (R_il = H[i + l ld], i <= l,
+// k <= 64): inverse iteration on R^T R from the constant vector, kSigmaIts steps,
+// with the Rayleigh quotient x^T (R^T R)^{-1} x as the estimate of 1 / sigma^2
+// (so the result is >= sigma_min and converges to it).  Run by the 32 lanes of
+// one warp together; lane L holds entries L and L + 32, and the triangular solves
+// sweep by columns (one broadcast per row).  Every block computes the same value.
+__device__ double tri_sigma_min(const double* H, int ld, int k) {
+  const int lane = threadIdx.x & 31;
+  for (int i = 0; i < k; ++i)
+    if (!(H[i + i * ld] != 0.0)) return 0.0;
+  const double x_init = 1.0 / sqrt((double)k);
+  double x0 = lane < k ? x_init : 0.0, x1 = lane + 32 < k ? x_init : 0.0;
+  double lam = 0.0;
+  for (int it = 0; it < kSigmaIts; ++it) {
+    double u0 = x0, u1 = x1;
+    // R^T u = x: u_i = x_i / R_ii, then x_l -= R_il u_i for l > i
+    for (int i = 0; i < k; ++i) {
+      const double ui = __shfl_sync(0xffffffffu, (i < 32 ? u0 : u1) / H[i + i * ld], i & 31);
+      if (lane == (i & 31)) {
+        if (i < 32) u0 = ui;
+        else u1 = ui;
+      }
+      if (lane > i && lane < k) u0 = fma(-H[i + lane * ld], ui, u0);
+      if (lane + 32 > i && lane + 32 < k) u1 = fma(-H[i + (lane + 32) * ld], ui, u1);
+    }
+    // R v = u: v_i = u_i / R_ii, then u_l -= R_li v_i for l < i
+    for (int i = k - 1; i >= 0; --i) {
+      const double vi = __shfl_sync(0xffffffffu, (i < 32 ? u0 : u1) / H[i + i * ld], i & 31);
+      if (lane == (i & 31)) {
+        if (i < 32) u0 = vi;
+        else u1 = vi;
+      }
+      if (lane < i) u0 = fma(-H[lane + i * ld], vi, u0);
+      if (lane + 32 < i) u1 = fma(-H[lane + 32 + i * ld], vi, u1);
+    }
+    lam = warp_sum(fma(x0, u0, x1 * u1));
+    const double inv = 1.0 / sqrt(warp_sum(fma(u0, u0, u1 * u1)));
+    x0 = u0 * inv;
+    x1 = u1 * inv;
+  }
+  return lam > 0.0 ? 1.0 / sqrt(lam) : 0.0;
+}
+
+// FGMRES(restart) with modified Gram-Schmidt, right preconditioner P_CH, zero
+// initial guess; the true residual is recomputed in float64 at every restart.
+//
+// Stop rule.  The residual test ||b - A^R y|| <= tol_r ||b|| (tol_r = a.tol) ends a
+// solve when a.err_tol = 0.  With a.err_tol > 0 the solution error must be small
+// too: e = (A^R)^{-1} r = P^{-1} (A^R P^{-1})^{-1} r, so once the residual test passes
+// the kernel estimates
+//     E = ||P^{-1} r|| / (||y|| sigma),
+// sigma = the smallest singular value of the cycles' Hessenberg matrices seen so far
+// (they represent A^R P^{-1} on the Krylov spaces), and stops only if E <= err_tol.
+// Otherwise it tightens tol_r to (||r|| / ||b||)(err_tol / E) / 2 and goes on; the
+// P^{-1} r / ||r|| it computed is the first preconditioned vector of the next cycle,
+// so a failed test wastes nothing.  The ratio E / (||r|| / ||b||) of the last tested
+// solve is kept in a.kappa with its tau; the next solve starts from the residual
+// target that ratio (scaled by tau / tau_kappa) predicts, so that the test usually
+// passes the first time.
 template <class TM, class TV>
 __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   const SolveArgs& a = c.a;
   __shared__ double H[(kMaxRestart + 1) * kMaxRestart];
   __shared__ double gv[kMaxRestart + 1], cs[kMaxRestart], sn[kMaxRestart], yk[kMaxRestart];
   __shared__ int s_k;
+  __shared__ double s_sigma;
   const int np = a.n_pad, n3 = 3 * np, m = a.restart, ld = m + 1;
   const int lane = threadIdx.x & 31;
+  const bool err_test = a.err_tol > 0.0;
   InnerCount cnt;
   Sum4<double> red;
+  double tol_r = a.tol;
+  if (err_test && a.kappa) {
+    const double k0 = a.kappa[0], t0 = a.kappa[1];
+    if (k0 > 0.0 && t0 > 0.0 && isfinite(k0))
+      tol_r = fmin(a.tol, fmax(1e-16, 0.5 * a.err_tol / (k0 * (a.tau / t0))));
+  }
+  if (threadIdx.x == 0) s_sigma = kInf;
   double pb = 0.0;
   FOR_MY_SLICES(g, s) {
     const int row = s * 32 + lane;
@@ -1359,6 +1435,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
   }
   int total = 0, restarts = 0;
   bool first = true;
+  double ynorm = 0.0, err_est = kNaN;
   while (true) {
     // r = b - A^R y  -> V_0 (y = 0 on the first cycle)
     double* V0 = a.V;
@@ -1379,9 +1456,13 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       flag(g, kErrNonfinite);
       return;
     }
-    if (beta <= a.tol * bnorm || total >= a.max_outer) {
-      if (beta > a.tol * bnorm) flag(g, kErrOuterCap);
-      write_stats(g, a, total, restarts, cnt, beta / bnorm, bnorm, 0);
+    const bool res_ok = beta <= tol_r * bnorm;
+    // the error test needs an iterate (not the first pass) and one more P^{-1}
+    bool checking = res_ok && err_test && !first && beta > 0.0 && total < a.max_outer;
+    if (!checking && (res_ok || total >= a.max_outer)) {
+      // a passing residual whose error test is still owed at the cap is not converged
+      if (!res_ok || (err_test && beta > 0.0 && !first)) flag(g, kErrOuterCap);
+      write_stats(g, a, total, restarts, cnt, beta / bnorm, bnorm, 0, err_est, s_sigma);
       return;
     }
     first = false;
@@ -1401,8 +1482,10 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       double* zj = a.Z + (size_t)j * n3;
       double* w = a.V + (size_t)(j + 1) * n3;
       if (!apply_pch(g, c, vj, zj, cnt)) return;
-      // w = A^R z_j, then modified Gram-Schmidt against V_0..V_j
-      double ph = 0.0;
+      // w = A^R z_j, then modified Gram-Schmidt against V_0..V_j; during an error
+      // test also ||z_0||^2 = ||P^{-1} r||^2 / beta^2
+      const bool test_now = checking && j == 0;
+      double ph = 0.0, pz = 0.0;
       FOR_MY_SLICES(g, s) {
         const int row = s * 32 + lane;
         double w0, w1, w2;
@@ -1411,8 +1494,31 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
         w[np + row] = w1;
         w[2 * np + row] = w2;
         ph += w0 * V0[row] + w1 * V0[np + row] + w2 * V0[2 * np + row];
+        if (test_now) {
+          const double z0 = zj[row], z1 = zj[np + row], z2 = zj[2 * np + row];
+          pz += z0 * z0 + z1 * z1 + z2 * z2;
+        }
       }
-      if (!grid_sum<double, 1>(g, ph, 0.0, 0.0, red, kPhOuter)) return;
+      if (test_now) {
+        if (!grid_sum<double, 2>(g, ph, pz, 0.0, red, kPhOuter)) return;
+        err_est = beta * sqrt(red.y) / (ynorm * s_sigma);
+        if (!(err_est > a.err_tol)) {
+          if (!isfinite(err_est)) {
+            flag(g, kErrNonfinite);
+            return;
+          }
+          if (a.kappa && g.bid == 0 && threadIdx.x == 0) {
+            a.kappa[0] = err_est * bnorm / beta;
+            a.kappa[1] = a.tau;
+          }
+          write_stats(g, a, total, restarts, cnt, beta / bnorm, bnorm, 0, err_est, s_sigma);
+          return;
+        }
+        tol_r = fmax(1e-16, 0.5 * (beta / bnorm) * (a.err_tol / err_est));
+        checking = false;
+      } else {
+        if (!grid_sum<double, 1>(g, ph, 0.0, 0.0, red, kPhOuter)) return;
+      }
       double hij = red.x;
       for (int i = 0; i <= j; ++i) {
         if (threadIdx.x == 0) H[i + j * ld] = hij;
@@ -1454,7 +1560,7 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
       __syncthreads();
       total += 1;
       k = j + 1;
-      if (fabs(gv[j + 1]) <= a.tol * bnorm || hnext == 0.0 || total >= a.max_outer) break;
+      if (fabs(gv[j + 1]) <= tol_r * bnorm || hnext == 0.0 || total >= a.max_outer) break;
       const double ih = 1.0 / hnext;
       FOR_MY_SLICES(g, s) {
         const int row = s * 32 + lane;
@@ -1473,6 +1579,13 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
     }
     __syncthreads();
     const int kk = s_k;
+    // warp 0 finds the cycle's smallest singular value (the rotated k x k triangle
+    // has those of the Hessenberg matrix) while the other warps update y
+    if (err_test && threadIdx.x < 32) {
+      const double sg = tri_sigma_min(H, ld, kk);
+      if (threadIdx.x == 0) s_sigma = fmin(s_sigma, sg);
+    }
+    double py = 0.0;
     FOR_MY_SLICES(g, s) {
       const int row = s * 32 + lane;
 #pragma unroll
@@ -1480,10 +1593,16 @@ __device__ void fgmres(Grid& g, Ctx<TM, TV>& c) {
         double acc = a.y[f * np + row];
         for (int i = 0; i < kk; ++i) acc = fma(yk[i], a.Z[(size_t)i * n3 + f * np + row], acc);
         a.y[f * np + row] = acc;
+        py = fma(acc, acc, py);
       }
     }
     restarts += 1;
-    if (!grid_sync(g, kPhOuter)) return;
+    if (err_test) {
+      if (!grid_sum<double, 1>(g, py, 0.0, 0.0, red, kPhOuter)) return;
+      ynorm = sqrt(red.x);
+    } else {
+      if (!grid_sync(g, kPhOuter)) return;
+    }
   }
 }
 

@@ -2,6 +2,7 @@
 include/pfc.h declares, and its host logic (options, status codes, mesh and
 SELL pattern builder, argument checks) behaves as documented.  No GPU calls."""
 import ctypes
+import math
 import os
 import re
 
@@ -38,7 +39,7 @@ def test_default_options(pkg):
     assert o["precision"] == 0 and o["step_atol"] == 1e-3 and o["step_rtol"] == 1e-3
     assert o["pcg_variant"] == 2 and o["inner_operator"] == 1 and o["smem_window"] == 0
     assert o["model"] == 2 and o["psi_min"] == -1.5 and o["schur"] == 0 and o["schur_its"] == 20
-    assert o["degree"] == 2
+    assert o["degree"] == 2 and o["err_tol"] == 1e-9 and o["tau_guard"] == 0.0
 
 
 def test_status_strings(pkg):
@@ -99,9 +100,50 @@ def test_footprint_grows_with_size_and_precision(pkg):
     assert f(2, 512, ctypes.byref(o)) > f(2, 512, None)
 
 
-def test_critical_tau_host_helper(pkg):
-    assert pkg.critical_tau(-0.35, 0.0) == pytest.approx(2.654787212, rel=1e-9)
+def test_critical_tau_export(pkg):
+    """pfc_critical_tau (Lemma 3) against the widths the paper prints and the oracle's closed form."""
+    from oracle import analysis
+    for line in open(os.path.join(ROOT, "tests", "golden", "lemma3_critical_tau.txt")):
+        if line.strip() and not line.startswith("#"):
+            r, pb, printed, digits = (float(v) for v in line.split())
+            got = pkg.lib.pfc_critical_tau(r, pb)
+            assert float(f"{got:.{int(digits)}g}") == pytest.approx(printed, rel=1e-12)
+    for r in (-0.5, -0.4, -0.35, -0.2, -0.05):
+        for pb in (0.0, -0.1, -0.2, -0.3, -0.35, -0.5):
+            want = analysis.critical_tau(r, pb)
+            got = pkg.critical_tau(r, pb)
+            assert got == want if math.isinf(want) else got == pytest.approx(want, rel=1e-14)
     assert pkg.critical_tau(-0.3, -0.35) == float("inf")
+
+
+def test_width_guard_option_checked(pkg):
+    o = pkg._Options()
+    pkg.lib.pfc_default_options(ctypes.byref(o))
+    for bad in (-0.1, 1.0, float("nan")):
+        o.tau_guard = bad
+        h = ctypes.c_void_p()
+        assert pkg.lib.pfc_setup_mesh(ctypes.byref(h), 2, 2, 2.0, ctypes.byref(o), None) == 1
+        assert b"tau_guard" in pkg.lib.pfc_last_error(h)
+        pkg.lib.pfc_destroy(h)
+    o.tau_guard = 0.0
+    for bad in (-1e-9, float("inf"), float("nan")):
+        o.err_tol = bad
+        h = ctypes.c_void_p()
+        assert pkg.lib.pfc_setup_mesh(ctypes.byref(h), 2, 2, 2.0, ctypes.byref(o), None) == 1
+        assert b"err_tol" in pkg.lib.pfc_last_error(h)
+        pkg.lib.pfc_destroy(h)
+
+
+def test_static_step_combination_size_limit(pkg):
+    """pfc_step_combine_static rejects n beyond (2^31 - 1 - 2^18) / 3 before touching the GPU
+    (its kernel's 32-bit index steps by 2^18 past 3n)."""
+    limit = (2 ** 31 - 1 - 2 ** 18) // 3
+    assert limit == 715740501
+    dummy = ctypes.c_void_p(256)   # never dereferenced: the size check comes first
+    f = pkg.lib.pfc_step_combine_static
+    assert f(limit + 1, dummy, dummy, 1e-3, 1e-3, dummy, dummy, None) == 1
+    assert f((2 ** 31 - 1) // 3, dummy, dummy, 1e-3, 1e-3, dummy, dummy, None) == 1
+    assert f(0, dummy, dummy, 1e-3, 1e-3, dummy, dummy, None) == 1
 
 
 def test_no_cuda_means_loud_failure(pkg):

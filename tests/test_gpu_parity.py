@@ -9,6 +9,7 @@ Tolerances:
 * single PCG solves and one preconditioner application with tight inner
   tolerances: <= 1e-9 relative.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -205,7 +206,7 @@ def test_stage_solve_parity(case, precision, variant, inner_op):
     err = np.linalg.norm(y - yref) / np.linalg.norm(yref)
     assert st.status == 0 and st.rel_residual <= 1e-11
     assert err <= 1e-8, (err, st)
-    assert st.outer_its > 0 and st.inner_calls == 5 * st.outer_its
+    assert st.outer_its > 0 and st.inner_calls == 5 * (st.outer_its + 1)  # + the error test
 
 
 @pytest.mark.parametrize("tau", [1.0, 4.0])
@@ -266,14 +267,19 @@ def test_rejected_step_leaves_state():
 
 
 def test_solve_is_deterministic():
+    """With the residual test alone a context keeps no state between solves, so the
+    same solve twice gives the same bits (the error test's learned residual target
+    is per context: tests/test_gpu_error_stop.py compares fresh contexts)."""
     case = CASES[0]
     dim, side, L, r, pm, amp = case
     x, b, _ = oracle_stage(case, 0.1)
-    with pfc.PFCSolver(dim, side, L, r=r, precision="fp32") as s:
+    with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", err_tol=0.0) as s:
         s.assemble(cuda(x), 0.1)
         y1, s1 = s.stage_solve(cuda(b))
         y2, s2 = s.stage_solve(cuda(b))
-        assert torch.equal(y1, y2) and s1 == s2
+        # no error test ran: err_est is NaN in both (NaN != NaN)
+        assert math.isnan(s1.err_est) and math.isnan(s2.err_est)
+        assert torch.equal(y1, y2) and dataclasses.replace(s1, err_est=0.0) == dataclasses.replace(s2, err_est=0.0)
 
 
 def test_edge_cases_zero_nan_and_caps():
@@ -321,8 +327,8 @@ def test_no_growth_right_after_a_rejection_matches_oracle():
     dim, side, L, r, pm, amp = CASES[0]
     prob = problem(dim, side, L, r)
     x0 = prob.consistent_state(synth.initial_psi(dim, side, pm, amp, 1))
-    # at tau = 8 the stage solutions agree to ~1e-6 only (error/residual ratio ~1e5), so the
-    # rejected step's err, and tau_next, agree to ~1e-3
+    # at tau = 8 the oracle's stage solutions (residual 1e-13 alone) agree with the exact ones to
+    # ~1e-8 only (error/residual ratio ~1e5), so the rejected step's err, and tau_next, agree to ~1e-3
     with pfc.PFCSolver(dim, side, L, r=r, outer_tol=1e-12) as s:
         st = cuda(x0)
         acc1, _, tau1, _ = s.step(st, 8.0)

@@ -1,0 +1,108 @@
+"""Parity with the oracle at sizes where the persistent kernel's full-size code paths run.
+
+With the cooperative grid of 152 blocks x 32 warps, meshes of a few thousand rows
+give every warp at most one 32-row slice.  These cases give warps several slices
+(2D 512^2: about 7 per warp; 2D 256^2 and 3D 32^3: about 1.7), so they exercise
+the cost-balanced contiguous slice ranges, the slot bounds of slices past a
+warp's first read from registers, and the block's row-info window in shared
+memory.  Tolerances as in test_gpu_parity: operators entrywise <= 1e-12 (|A| |x|),
+stage solutions <= 1e-8 relative against the oracle's FGMRES run to an estimated
+solution error of 1e-11 (oracle/solvers.py).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle.mesh import structured_mesh
+from oracle.rosenbrock import PFCProblem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1501_06852_gb300 as pfc  # noqa: E402
+
+CASES = {
+    "2d-s256-h0.5": (2, 256, 128.0, -0.4, -0.3, 0.1),
+    "3d-s32": (3, 32, 32.0, -0.3, -0.35, 0.05),
+}
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        dim, side, L, r, pm, amp = CASES[name]
+        prob = PFCProblem(structured_mesh(dim, side, L), r)
+        n = prob.n
+        # mu and omega seeded, psi the seeded noise of the workloads (no consistency needed
+        # for a single stage system)
+        x = np.concatenate([synth.random_vector(n, 101), synth.initial_psi(dim, side, pm, amp, 1),
+                            synth.random_vector(n, 201)])
+        _cache[name] = (prob, x)
+    return _cache[name]
+
+
+def cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def assert_close_scaled(got, want, scale, tol=1e-12):
+    err = np.abs(got - want)
+    assert np.all(err <= tol * (scale + 1e-300) + tol * 1e-3 * np.abs(want).max()), (err / (scale + 1e-300)).max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_operators_match_oracle_at_size(name):
+    dim, side, L, r = CASES[name][:4]
+    prob, x = setup(name)
+    n = prob.n
+    tau = 0.1
+    with pfc.PFCSolver(dim, side, L, r=r) as s:
+        s.assemble(cuda(x), tau)
+        v = synth.random_vector(n, 5)
+        for op, A in ((pfc.OP_M, prob.M), (pfc.OP_K, prob.K), (pfc.OP_A01, prob.a01(x[n:2 * n]))):
+            assert_close_scaled(host(s.apply(op, cuda(v))), A @ v, abs(A) @ np.abs(v))
+        AR = prob.stage_matrix(x[n:2 * n], tau)
+        v3 = synth.random_vector(3 * n, 6)
+        assert_close_scaled(host(s.apply(pfc.OP_AR, cuda(v3))), AR @ v3, abs(AR) @ np.abs(v3))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stage_solve_matches_oracle_at_size(name):
+    dim, side, L, r = CASES[name][:4]
+    prob, x = setup(name)
+    n = prob.n
+    tau = 0.1
+    A = prob.stage_matrix(x[n:2 * n], tau)
+    b = prob.stage_rhs(x, [], [], tau)
+    yref, ost = prob.stage_solve(A, b, tau, tol=1e-12, err_tol=1e-11)
+    assert ost.converged
+    for precision in ("fp32", "fp64"):
+        with pfc.PFCSolver(dim, side, L, r=r, precision=precision) as s:
+            s.assemble(cuda(x), tau)
+            y, st = s.stage_solve(cuda(b))
+            err = np.linalg.norm(host(y) - yref) / np.linalg.norm(yref)
+        assert st.status == 0 and err <= 1e-8, (precision, err, st)
+
+
+def test_block_operator_matches_oracle_at_benchmark_size():
+    """A^R z entrywise on the 2D 512^2 mesh (3,151,875 unknowns) of the benchmark."""
+    w = synth.C2_2D_LARGE
+    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r)
+    n = prob.n
+    x = np.concatenate([synth.random_vector(n, 301), synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed),
+                        synth.random_vector(n, 302)])
+    tau = 6.7
+    AR = prob.stage_matrix(x[n:2 * n], tau)
+    v3 = synth.random_vector(3 * n, 303)
+    with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision="fp32") as s:
+        s.assemble(cuda(x), tau)
+        got = host(s.apply(pfc.OP_AR, cuda(v3)))
+    assert_close_scaled(got, AR @ v3, abs(AR) @ np.abs(v3))
