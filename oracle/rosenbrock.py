@@ -183,17 +183,31 @@ class PFCProblem:
         return y, st
 
     # --- initial state ----------------------------------------------------
-    def consistent_state(self, psi0: np.ndarray, tol: float = 1e-14) -> np.ndarray:
+    def consistent_state(self, psi0: np.ndarray, tol: float = 1e-14, solver: str = "lu") -> np.ndarray:
         """(mu0, psi0, omega0) with M omega0 = -K psi0 and
         M mu0 = l(psi0^3) + (1+r) M psi0 - 2 K psi0 - K omega0 (Eq. 2.4 in weak form).
         Reading: the paper does not say how mu and omega start; this makes the
-        algebraic rows of the DAE hold at t = 0."""
+        algebraic rows of the DAE hold at t = 0.  solver: "lu" (sparse LU of M) or
+        "pcg" (Jacobi-PCG to a relative residual tol; M is well conditioned, so this
+        is the cheap route on large meshes)."""
         import scipy.sparse.linalg as spla
-        lu = spla.splu(self.M.tocsc())
-        om = lu.solve(-(self.K @ psi0))
+        if solver == "lu":
+            lu = spla.splu(self.M.tocsc())
+            solve = lu.solve
+        elif solver == "pcg":
+            from .solvers import pcg_jacobi
+
+            def solve(rhs):
+                res = pcg_jacobi(self.M, rhs, tol, 10000)
+                if not res.converged:
+                    raise RuntimeError("consistent_state: PCG with M did not converge")
+                return res.x
+        else:
+            raise ValueError("solver must be 'lu' or 'pcg'")
+        om = solve(-(self.K @ psi0))
         rhs = assembly.load_cubed(self.mesh, psi0, self.ref) + (1.0 + self.r) * (self.M @ psi0) \
             - 2.0 * (self.K @ psi0) - self.K @ om
-        mu = lu.solve(rhs)
+        mu = solve(rhs)
         return np.concatenate([mu, psi0, om])
 
     # --- diagnostics ------------------------------------------------------

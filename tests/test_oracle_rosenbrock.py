@@ -116,6 +116,19 @@ def test_consistent_start_zeroes_algebraic_rows(small_pfc):
     assert abs(b[n:2 * n].sum()) < 1e-12 * scale
 
 
+def test_consistent_start_by_pcg_matches_lu():
+    """The PCG route of the consistent start (used on the benchmark mesh, where the LU
+    of M is slow) gives the LU route's state, and so zeroes the algebraic rows too."""
+    prob = PFCProblem(structured_mesh(2, 12, 6.0), -0.4)
+    psi0 = synth.initial_psi(2, 12, -0.3, 0.1, 7)
+    x_lu = prob.consistent_state(psi0)
+    x_cg = prob.consistent_state(psi0, tol=1e-15, solver="pcg")
+    assert np.linalg.norm(x_cg - x_lu) <= 1e-13 * np.linalg.norm(x_lu)
+    n = prob.n
+    b = prob.stage_rhs(x_cg, [], [], 0.1)
+    assert np.linalg.norm(b[:n]) < 1e-12 * np.linalg.norm(b[n:2 * n])
+
+
 def test_mass_conservation_and_energy(small_pfc):
     prob, x = small_pfc
     m0 = prob.mass(x)
