@@ -57,7 +57,12 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--precision", choices=["fp32", "fp16"], default="fp32", help="inner precision of the mixed form")
-    p.add_argument("--outer-tol", type=float, default=1e-11)
+    p.add_argument("--outer-tol", type=float, default=1e-10,
+                   help="starting relative-residual target of the stage solves")
+    p.add_argument("--err-tol", type=float, default=5e-9,
+                   help="stage solves stop once their estimated relative solution error is below this "
+                        "(the library's error test, which overestimates the error by 1.1-2.7x on the "
+                        "oracle's pins; 0 = residual test alone).  5e-9 keeps the metric's 1e-8")
     p.add_argument("--workload", choices=["c2", "c1", "c3", "c4", "c5", "c0"], default="c2",
                    help="c2 (default) the 2D 512^2 metric; c1/c3 other single instances; c4 256 batched "
                         "instances; c5 the serving stream; c0 the paper's ~66k-unknown Euler solver tables")
@@ -77,7 +82,6 @@ def parse_args(argv=None):
     p.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-outer", type=int, default=2, help="FGMRES iterations in the CPU baseline sample")
     p.add_argument("--pcg-sweep", action="store_true",
                    help="per-iteration time of fixed-length inner PCG solves (M + sqrt(delta) K) against "
                         "problem size, PCG form and blocks per SM; one JSON line per configuration")
@@ -105,13 +109,12 @@ def batched(args):
     t0 = time.perf_counter()
     solvers, states, taus = [], [], []
     for w in wls:
-        cap = tau_cap(w)
         s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol,
-                          tau_max=cap)
+                          err_tol=args.err_tol, tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD)
         solvers.append(s)
         states.append(s.init_state(torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp,
                                                                       w.seed)).cuda()))
-        taus.append(min(w.tau0, cap))
+        taus.append(min(w.tau0, tau_cap(w)))
     setup_s = time.perf_counter() - t0
     # a stage solve that hits the iteration cap rejects that instance's step (its tau
     # shrinks); it is counted, not raised
@@ -203,7 +206,8 @@ def euler_tables(args):
         psi0 = torch.from_numpy(synth.initial_psi(w.dim, side, w.psi_mean, w.amp, w.seed, degree=deg)).cuda()
         for precision in ("fp64", args.precision):
             for tol in (w.outer_tol, 1e-6):
-                with pfc.PFCSolver(w.dim, side, w.length, r=w.r, precision=precision, outer_tol=tol,
+                # residual test alone, as the paper's tolerance (its outer iteration counts)
+                with pfc.PFCSolver(w.dim, side, w.length, r=w.r, precision=precision, outer_tol=tol, err_tol=0.0,
                                    model=args.model, schur=1 if args.schur == "sd" else 0, degree=deg) as s:
                     x0 = s.init_state(psi0)
                     s.set_timing(True)
@@ -298,16 +302,19 @@ def pcg_sweep(args):
 
 
 # Step-width limit where Lemma 3 gives no critical step width (the paper's adaptive
-# runs reach tau of about 18, Section 7).
+# runs reach tau of about 18, Section 7), and the library's Lemma-3 guard: after each
+# step gamma tau <= TAU_GUARD tau*(r, <psi>) (options.tau_guard).
 TAU_MAX_UNGUARDED = 20.0
+TAU_GUARD = 0.9
 
 
 def tau_cap(w: synth.Workload) -> float:
-    """Step-width guard from Lemma 3: gamma * tau stays below 0.9 tau*(r, psi_mean)."""
+    """The width limit the library's guard gives at the workload's nominal mean density
+    (the library uses the state's own mean, within 1e-4 of it), for labels and start widths."""
     from paper_1501_06852_gb300 import critical_tau
 
     ts = critical_tau(w.r, w.psi_mean)
-    return TAU_MAX_UNGUARDED if math.isinf(ts) else min(TAU_MAX_UNGUARDED, 0.9 * ts / GAMMA)
+    return TAU_MAX_UNGUARDED if math.isinf(ts) else min(TAU_MAX_UNGUARDED, TAU_GUARD * ts / GAMMA)
 
 
 # ----------------------------------------------------------------------------- bytes
@@ -443,7 +450,8 @@ def aggregate_value(per_rank_solves: int, world: int, t_max_s: float) -> float:
 
 # ----------------------------------------------------------------------------- native
 def run_steps(s, state, tau, steps, cap, torch):
-    """K adaptive steps; returns (elapsed ms from CUDA events, per-step ms, stats, tau)."""
+    """K adaptive steps; returns (elapsed ms from CUDA events, per-step ms, stats, tau).
+    The library caps the widths it returns (tau_max, tau_guard); cap is unused."""
     stream = s.stream
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -457,8 +465,9 @@ def run_steps(s, state, tau, steps, cap, torch):
         all_stats.extend(st)
         accepted += int(acc)
         traj.append([round(tau, 4), int(acc), round(err, 4), max(x.outer_its for x in st),
-                     round(sum(x.inner_its for x in st) / max(1, sum(x.outer_its for x in st)), 1)])
-        tau = min(tau_next, cap)
+                     round(sum(x.inner_its for x in st) / max(1, sum(x.outer_its for x in st)), 1),
+                     float(f"{max(x.err_est for x in st):.3g}")])
+        tau = tau_next
     ev1.record(stream)
     torch.cuda.synchronize()
     per_step = [marks[k].elapsed_time(marks[k + 1]) for k in range(steps)]
@@ -488,8 +497,8 @@ def native(args, world, rank, local, pg):
 
     def make(precision):
         return pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=args.outer_tol,
-                             model=args.model, schur=1 if args.schur == "sd" else 0,
-                             tau_max=cap)
+                             err_tol=args.err_tol, model=args.model, schur=1 if args.schur == "sd" else 0,
+                             tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD)
 
     out = {}
     hbm = FALLBACK_HBM_GBS
@@ -564,7 +573,14 @@ def native(args, world, rank, local, pg):
         },
         "step_ms": {"p50": pct(per_step, 50), "p99": pct(per_step, 99), "mean": statistics.mean(per_step)},
         "accepted_steps": accepted,
-        "trajectory": {"columns": ["tau", "accepted", "err", "max_outer_its", "inner_its_per_outer"],
+        # rejected attempts are timed stage solves like the others; this says how much of the
+        # timed region they take (the controller grows tau by up to 5x, to the Lemma-3 guard)
+        "rejected_attempts": {
+            "count": sum(1 for t in run_steps.last_trajectory if not t[1]),
+            "share_of_time": sum(ms for ms, t in zip(per_step, run_steps.last_trajectory) if not t[1])
+            / max(sum(per_step), 1e-30)},
+        "trajectory": {"columns": ["tau", "accepted", "err", "max_outer_its", "inner_its_per_outer",
+                                   "max_err_est"],
                        "mixed": run_steps.last_trajectory},
         "solver": {
             "outer_its_mean": statistics.mean(st.outer_its for st in stats),
@@ -623,7 +639,7 @@ def native(args, world, rank, local, pg):
             back.copy_(dstate, non_blocking=True)
             torch.cuda.synchronize()
             host, back = back, host
-            tau = min(tau_next, cap)
+            tau = tau_next
         t_e2e = time.perf_counter() - t0
         dist_barrier(pg, dev)
         t_e2e = dist_max(pg, t_e2e, dev)
@@ -635,33 +651,125 @@ def native(args, world, rank, local, pg):
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(w: synth.Workload, outer: int, model: int = 2):
-    """Times the oracle on a bounded sample of one stage solve: assembly of A^R and b
-    plus ``outer`` FGMRES iterations (P_CH with Jacobi-PCG inner solves)."""
-    import numpy as np
-
-    from oracle.mesh import structured_mesh
-    from oracle.rosenbrock import ROS3PW, PFCProblem
-    from oracle.solvers import PCH, fgmres
-
-    t0 = time.perf_counter()
-    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=model)
-    t_setup = time.perf_counter() - t0
-    n = prob.n
-    psi = synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)
-    x = np.concatenate([synth.random_vector(n, 101) * 0.0, psi, synth.random_vector(n, 201) * 0.0])
-    t0 = time.perf_counter()
-    A = prob.stage_matrix(psi, w.tau0, mu_k=x[:n])
-    b = prob.stage_rhs(x, [], [], w.tau0)
-    t_fixed = time.perf_counter() - t0
-    pc = PCH(prob.M, prob.K, prob.m0(psi) * w.tau0, ROS3PW.gamma)
-    t0 = time.perf_counter()
-    fgmres(lambda v: A @ v, b, pc.apply, 1e-30, 30, outer)
-    t_outer = (time.perf_counter() - t0) / outer
-    return t_setup, t_fixed, t_outer
+# Stage systems of the headline workload checked against the oracle: the first stage
+# of the first step (tau0 from the seeded consistent start) and the first stage from
+# the same start at the largest width the trajectory can attempt (the Lemma-3 guard).
+# The oracle's FGMRES solves them to an estimated relative error of ACC_ORACLE_ERR
+# (its error test, oracle/solvers.py); the GPU forms run with the benchmark's options.
+ACC_ORACLE_ERR = {"first": 1e-11, "widest": 1e-9}
 
 
-def oracle_accuracy_small(precision: str, outer_tol: float, model: int = 2):
+def oracle_stage_worker(wname: str, tau: float, err_tol: float, model: int, out_path: str, q):
+    """Process body (spawned before any GPU work): one whole oracle stage solve of the
+    workload's first stage at width tau from the seeded consistent start.  Puts
+    {seconds: ..., outer_its: ...} on q and the solution in out_path (.npy)."""
+    try:
+        import numpy as np
+
+        from oracle.mesh import structured_mesh
+        from oracle.rosenbrock import PFCProblem
+
+        w = {x.name: x for x in (synth.C1_2D_SMALL, synth.C2_2D_LARGE, synth.C3_3D)}[wname]
+        t0 = time.perf_counter()
+        prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=model)
+        x0 = prob.consistent_state(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed), tol=1e-15,
+                                   solver="pcg")
+        t_setup = time.perf_counter() - t0
+        n = prob.n
+        t0 = time.perf_counter()
+        A = prob.stage_matrix(x0[n:2 * n], tau, mu_k=x0[:n])
+        b = prob.stage_rhs(x0, [], [], tau)
+        y, st = prob.stage_solve(A, b, tau, tol=1e-12, err_tol=err_tol, m0=prob.m0(x0[n:2 * n]),
+                                 max_outer=3000)
+        t_solve = time.perf_counter() - t0
+        np.save(out_path, y)
+        q.put({"tau": tau, "seconds": t_solve, "setup_seconds": t_setup, "outer_its": st.outer_iterations,
+               "converged": bool(st.converged), "err_estimate": st.err_estimate, "rel_residual": st.rel_residual})
+    except Exception as e:  # reported, never raised into the benchmark
+        q.put({"tau": tau, "error": repr(e)[:300]})
+
+
+class one_thread_children:
+    """Processes started inside this block run numpy/BLAS on one thread (the oracle's
+    workers are one core each; several BLAS thread pools per core thrash)."""
+    VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.VARS}
+        for k in self.VARS:
+            os.environ[k] = "1"
+
+    def __exit__(self, *exc):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+class OracleChecks:
+    """Whole oracle stage solves of the workload run in spawned processes (one core
+    each) while the GPU measures; their solutions are the accuracy reference of the
+    bench line and their times the CPU baseline."""
+
+    def __init__(self, w: synth.Workload, widths: dict, model: int):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.dir = tempfile.mkdtemp(prefix="pfc_oracle_")
+        self.w, self.widths = w, widths
+        self.jobs = {}
+        for key, tau in widths.items():
+            q = ctx.Queue()
+            path = os.path.join(self.dir, f"{key}.npy")
+            p = ctx.Process(target=oracle_stage_worker, args=(w.name, tau, ACC_ORACLE_ERR[key], model, path, q),
+                            daemon=True)
+            with one_thread_children():
+                p.start()
+            self.jobs[key] = (p, q, path)
+
+    def collect(self, timeout_s: float) -> dict:
+        import numpy as np
+
+        res = {}
+        deadline = time.perf_counter() + timeout_s
+        for key, (p, q, path) in self.jobs.items():
+            try:
+                info = q.get(timeout=max(1.0, deadline - time.perf_counter()))
+            except Exception:
+                info = {"tau": self.widths[key], "error": f"oracle solve unfinished after {timeout_s:.0f} s"}
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+            if "error" not in info:
+                info["y"] = np.load(path)
+                os.unlink(path)
+            res[key] = info
+        try:
+            os.rmdir(self.dir)
+        except OSError:
+            pass
+        return res
+
+
+def gpu_first_stage(w: synth.Workload, precision: str, tau: float, args):
+    """The GPU's solution of the workload's first stage at width tau from its own
+    consistent start of the same seeded psi0 (lexicographic order, host array)."""
+    import torch
+
+    import paper_1501_06852_gb300 as pfc
+
+    psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
+    with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=args.outer_tol,
+                       err_tol=args.err_tol, model=args.model, max_outer=3000) as s:
+        x0 = s.init_state(psi0)
+        s.assemble(x0, tau)
+        b = s.stage_rhs(0, x0)
+        y, st = s.stage_solve(b)
+        return y.cpu().numpy(), st
+
+
+def oracle_accuracy_small(precision: str, outer_tol: float, err_tol: float, model: int = 2):
     """Stage solutions of the small 2D workload: GPU (both forms) against the oracle at 1e-13."""
     import numpy as np
     import torch
@@ -676,7 +784,8 @@ def oracle_accuracy_small(precision: str, outer_tol: float, model: int = 2):
     ref = pfc_step(prob, x0, w.tau0, StepControl(), tol=1e-13)
     errs = {}
     for prec in (precision, "fp64"):
-        with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=outer_tol, model=model) as s:
+        with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=outer_tol, err_tol=err_tol,
+                           model=model) as s:
             xs = torch.from_numpy(x0).cuda()
             s.assemble(xs, w.tau0)
             worst = 0.0
@@ -689,60 +798,103 @@ def oracle_accuracy_small(precision: str, outer_tol: float, model: int = 2):
     return errs
 
 
-def reference(args, world, rank):
-    """Times the FP64 CPU oracle on the host cores on bounded samples of the same workload.
+def reference_worker(wname: str, tau: float, count: int, model: int, outer_tol: float, err_tol: float, start_evt, q):
+    """Process body of the reference arm: set-up (mesh, M, K, consistent start; the
+    warm-up, untimed), then, once start_evt is set, `count` whole oracle stage solves
+    of the workload's first stage at width tau.  Puts per-solve seconds on q."""
+    try:
+        from oracle.mesh import structured_mesh
+        from oracle.rosenbrock import PFCProblem
 
-    Set-up (mesh, M, K) is not timed.  The per-solve fixed cost (assembly of A^R
-    and b) is timed once; every benchmark step is one FGMRES iteration of the
-    oracle's stage solve (P_CH with Jacobi-PCG inner solves, A^R SpMV, MGS), and
-    a stage solve is scaled to OUTER_ITS_PER_SOLVE iterations."""
+        w = {x.name: x for x in (synth.C1_2D_SMALL, synth.C2_2D_LARGE, synth.C3_3D)}[wname]
+        prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=model)
+        x0 = prob.consistent_state(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed), tol=1e-15,
+                                   solver="pcg")
+        n = prob.n
+        q.put(("ready", None))
+        start_evt.wait()
+        for _ in range(count):
+            t0 = time.perf_counter()
+            A = prob.stage_matrix(x0[n:2 * n], tau, mu_k=x0[:n])
+            b = prob.stage_rhs(x0, [], [], tau)
+            _, st = prob.stage_solve(A, b, tau, tol=outer_tol, err_tol=err_tol, m0=prob.m0(x0[n:2 * n]),
+                                     max_outer=3000)
+            q.put(("solve", (time.perf_counter() - t0, st.outer_iterations)))
+    except Exception as e:
+        q.put(("error", repr(e)[:300]))
+
+
+def reference(args, world, rank):
+    """The FP64 CPU oracle, as it stands, on the host cores: whole stage solves.
+
+    Each benchmark step is one whole oracle stage solve (assembly of A^R and b,
+    FGMRES(30) + P_CH with Jacobi-PCG inner solves, to the GPU arm's residual target
+    and estimated solution error, --outer-tol and --err-tol) of the workload's
+    first stage at tau0 from the seeded consistent start.  The K steps are dealt to
+    P = min(K, host cores - 1) spawned processes that run at the same time (one
+    core each; scipy's sparse products and numpy's vector calls run on one thread
+    at these sizes), so `value` is the all-cores throughput; the W warm-up steps are
+    each process's set-up (mesh, M, K, consistent start).  The widest widths of the
+    trajectory take up to ten times as many iterations as tau0, so this flatters
+    the CPU."""
     if rank != 0:
         return None
-    import numpy as np
-
-    from oracle.mesh import structured_mesh
-    from oracle.rosenbrock import ROS3PW, PFCProblem
-    from oracle.solvers import PCH, fgmres
+    import multiprocessing as mp
 
     w = workload(args.workload)
-    outer_per_solve = OUTER_ITS_PER_SOLVE.get(w.name, 30.0)
+    K = max(1, args.steps)
+    P = max(1, min(K, (os.cpu_count() or 2) - 1))
+    counts = [K // P + (1 if i < K % P else 0) for i in range(P)]
+    ctx = mp.get_context("spawn")
+    start_evt = ctx.Event()
+    q = ctx.Queue()
     t_start = time.perf_counter()
-    prob = PFCProblem(structured_mesh(w.dim, w.side, w.length), w.r, model=args.model)
-    n = prob.n
-    psi = synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)
-    x = np.concatenate([np.zeros(n), psi, np.zeros(n)])
+    procs = [ctx.Process(target=reference_worker,
+                         args=(w.name, w.tau0, c, args.model, args.outer_tol, args.err_tol, start_evt, q), daemon=True)
+             for c in counts]
+    with one_thread_children():
+        for p in procs:
+            p.start()
+    ready, errors, solves = 0, [], []
     t0 = time.perf_counter()
-    A = prob.stage_matrix(psi, w.tau0, mu_k=x[:n])
-    b = prob.stage_rhs(x, [], [], w.tau0)
-    t_fixed = time.perf_counter() - t0
-    pc = PCH(prob.M, prob.K, prob.m0(psi) * w.tau0, ROS3PW.gamma)
-    v = b / np.linalg.norm(b)
-    samples = []
-    for k in range(args.warmup + args.steps):
+    try:
+        while ready + len(errors) < P:
+            kind, val = q.get(timeout=1800)
+            if kind == "ready":
+                ready += 1
+            elif kind == "error":
+                errors.append(val)
         t0 = time.perf_counter()
-        fgmres(lambda u: A @ u, v, pc.apply, 1e-30, 30, 1)
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            samples.append(dt)
-    per_solve = t_fixed + outer_per_solve * statistics.mean(samples)
-    value = 1.0 / per_solve
-    total = time.perf_counter() - t_start
-    return {"metric": metric_for(w), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 3e3 * per_solve, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{w.name} (same workload, metric and unit as the native arm)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step = 1 FGMRES iteration of the oracle stage solve "
-                                       f"(mean {statistics.mean(samples):.2f} s); per solve = A^R/b assembly "
-                                       f"({t_fixed:.1f} s) + {outer_per_solve:g} iterations; {total:.0f} s total"},
+        start_evt.set()
+        while len(solves) < K and not errors:
+            kind, val = q.get(timeout=3600)
+            if kind == "solve":
+                solves.append(val)
+            elif kind == "error":
+                errors.append(val)
+    except Exception as e:  # queue timeout
+        errors.append(repr(e)[:200])
+    wall = time.perf_counter() - t0
+    for p in procs:
+        p.join(timeout=10)
+        if p.is_alive():
+            p.terminate()
+    if errors or not solves:
+        return {"impl": "reference", "unavailable": f"oracle worker failed: {errors[:1]}"}
+    value = len(solves) / wall
+    per = statistics.mean(t for t, _ in solves)
+    its = statistics.mean(i for _, i in solves)
+    sample = (f"{len(solves)} whole oracle stage solves (first stage at tau0={w.tau0}, {its:.0f} FGMRES its each) "
+              f"in {P} parallel processes, one core each: {wall:.0f} s wall, {per:.1f} s per solve on one core "
+              f"({1.0 / per:.4f} stage solves/s single-core); set-up {t0 - t_start:.0f} s untimed")
+    return {"metric": metric_for(w), "value": value, "unit": UNIT, "n_gpus": world, "steps": len(solves),
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / len(solves), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{w.name} (same workload, metric and unit as the native arm; first stage "
+                                   f"at tau0 only)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample,
+                             "single_core_value": 1.0 / per},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-
-
-# mean FGMRES iterations per stage solve of the float64 GPU run of the same
-# workload, tolerance and step trajectory (same algorithm as the oracle): the
-# scale of the reference arm's per-iteration samples (2D 512^2: 68 measured over
-# the 20-step adaptive run; the others: 30, the first-step count).
-OUTER_ITS_PER_SOLVE = {"2d-s512-L256": 68.0, "2d-s32-L32": 30.0, "3d-s64-L64": 30.0}
 
 
 def profile_case(args):
@@ -821,25 +973,57 @@ def main(argv=None):
         if rank == 0 and res is not None:
             print(json.dumps(res), flush=True)
         return 0
+    w = workload(args.workload)
+    checks = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.name != synth.C3_3D.name:
+        # spawned before the first GPU call; they run on host cores while the GPU measures
+        checks = OracleChecks(w, {"first": w.tau0, "widest": tau_cap(w)}, args.model)
     out, stats, n, nnz = native(args, world, rank, local, pg)
     if rank == 0:
-        outer_mean = out.pop("_fp64_outer_mean", None) or out["solver"]["outer_its_mean"]
+        out.pop("_fp64_outer_mean", None)
+        if checks is not None:
+            import numpy as np
+
+            ref = checks.collect(timeout_s=1800.0)
+            acc = {"workload": f"{w.name}: first stage of the first step (tau0) and first stage at the widest "
+                               f"width the Lemma-3 guard allows, from the seeded consistent start; "
+                               f"max rel L2 error of the GPU stage solution against the oracle's",
+                   "oracle_err_tol": ACC_ORACLE_ERR}
+            worst = 0.0
+            for key, info in ref.items():
+                row = {"tau": info["tau"]}
+                if "error" in info:
+                    row["error"] = info["error"]
+                    worst = float("nan")
+                else:
+                    row["oracle_outer_its"] = info["outer_its"]
+                    row["oracle_err_estimate"] = info["err_estimate"]
+                    for prec in (args.precision, "fp64"):
+                        y, st = gpu_first_stage(w, prec, info["tau"], args)
+                        e = float(np.linalg.norm(y - info["y"]) / np.linalg.norm(info["y"]))
+                        row[prec] = {"rel_err": e, "outer_its": st.outer_its, "err_est": st.err_est}
+                        worst = max(worst, e) if worst == worst else worst
+                acc[key] = row
+            acc["max_rel_err"] = worst
+            out["accuracy_vs_oracle"] = acc
+            done = [v for v in ref.values() if "error" not in v]
+            if done:
+                per = statistics.mean(v["seconds"] for v in done)
+                out["cpu_baseline"] = {
+                    "value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": "whole oracle stage solves (numpy/scipy FP64, one core each, run in parallel "
+                              "processes): " + "; ".join(
+                                  f"tau={v['tau']:.3g}: {v['outer_its']} FGMRES its, {v['seconds']:.1f} s"
+                                  for v in done)
+                              + " (mean per solve; mesh, M, K and consistent start not timed)"}
         if world == 1 and not args.no_cpu_baseline:
-            w = workload(args.workload)
-            t_setup, t_fixed, t_outer = oracle_sample(w, args.cpu_outer, args.model)
-            per = t_fixed + t_outer * outer_mean
-            out["cpu_baseline"] = {
-                "value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"oracle (numpy/scipy, 1 thread) on the same workload: A^R + b assembly "
-                          f"({t_fixed:.1f} s) and {args.cpu_outer} FGMRES iterations ({t_outer:.1f} s each) of the "
-                          f"first stage solve, scaled to {outer_mean:.1f} iterations/solve (GPU fp64 mean); "
-                          f"mesh/M/K set-up {t_setup:.1f} s not counted"}
             try:
-                out["accuracy_vs_oracle"] = {
+                out["accuracy_vs_oracle_small"] = {
                     "workload": "2d-s32-L32 (4225 dofs/field): max rel L2 error of the 3 stage solutions of one step",
-                    **{k: v for k, v in oracle_accuracy_small(args.precision, args.outer_tol, args.model).items()}}
+                    **{k: v for k, v in oracle_accuracy_small(args.precision, args.outer_tol, args.err_tol,
+                                                              args.model).items()}}
             except Exception as e:  # keep the benchmark line even if the check cannot run
-                out["accuracy_vs_oracle"] = {"error": str(e)[:200]}
+                out["accuracy_vs_oracle_small"] = {"error": str(e)[:200]}
         print(json.dumps(out), flush=True)
     if pg is not None:
         pg.destroy_process_group()
