@@ -76,8 +76,8 @@ def parse_args(argv=None):
     p.add_argument("--degree", type=int, choices=[2, 1], default=2,
                    help="c0: Lagrange degree, 2 (P2) or 1 (P1 on the same domains with twice the cells per "
                         "axis, hence the same unknowns; the paper's Tables 3-4 list both)")
-    p.add_argument("--requests", type=int, default=300, help="c5: number of requests")
-    p.add_argument("--rate", type=float, default=3.0, help="c5: Poisson arrival rate (requests/s)")
+    p.add_argument("--requests", type=int, default=2000, help="c5: number of requests")
+    p.add_argument("--rate", type=float, default=8.0, help="c5: Poisson arrival rate (requests/s)")
     p.add_argument("--instances", type=int, default=256, help="c4: number of instances")
     p.add_argument("--no-fp64", action="store_true", help="skip the float64 comparison run")
     p.add_argument("--no-e2e", action="store_true")
@@ -88,6 +88,11 @@ def parse_args(argv=None):
     p.add_argument("--profile-case", action="store_true",
                    help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
                         "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
+    p.add_argument("--profile-side", type=int, default=0,
+                   help="profiler case: mesh side in place of the workload's (same spacing h and parameters)")
+    p.add_argument("--profile-restart", type=int, default=30,
+                   help="profiler case: FGMRES restart length (its one iteration needs 2; smaller bases "
+                        "keep a capture's device memory small)")
     p.add_argument("--phases", action="store_true",
                    help="phase split of one whole stage solve (first stage at tau = 4 after a warm-up solve): "
                         "the kernel's own clock in block 0 for inner SpMV, inner vector, outer FGMRES and PCG "
@@ -100,52 +105,66 @@ def workload(name: str) -> synth.Workload:
 
 
 def batched(args):
-    """c4: independent 2D instances of uneven size advanced by batched steps."""
+    """c4: independent 2D instances of uneven size advanced by batched steps, with the
+    library's default solver configuration and with the autotuner's per size class."""
     import torch
 
     import paper_1501_06852_gb300 as pfc
+    from paper_1501_06852_gb300 import autotune
 
     wls = synth.batched_instances(args.instances)
+
+    def run(config_of):
+        solvers, states, taus = [], [], []
+        for w in wls:
+            s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol,
+                              err_tol=args.err_tol, tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD, **config_of(w))
+            solvers.append(s)
+            states.append(s.init_state(torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp,
+                                                                          w.seed)).cuda()))
+            taus.append(w.tau0)
+        # a stage solve that hits the iteration cap rejects that instance's step (its tau
+        # shrinks); it is counted, not raised
+        for _ in range(args.warmup):
+            _, _, taus, _ = pfc.batch_step(solvers, states, taus, check=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        per, accepted, capped = [], 0, 0
+        ev0.record()
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            acc, errs, taus, stats = pfc.batch_step(solvers, states, taus, check=False)
+            per.append(1e3 * (time.perf_counter() - t))
+            accepted += sum(acc)
+            capped += sum(1 for st3 in stats for x in st3 if x.status != 0)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        for s in solvers:
+            s.close()
+        return ms, per, accepted, capped
+
     t0 = time.perf_counter()
-    solvers, states, taus = [], [], []
-    for w in wls:
-        s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol,
-                          err_tol=args.err_tol, tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD)
-        solvers.append(s)
-        states.append(s.init_state(torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp,
-                                                                      w.seed)).cuda()))
-        taus.append(min(w.tau0, tau_cap(w)))
-    setup_s = time.perf_counter() - t0
-    # a stage solve that hits the iteration cap rejects that instance's step (its tau
-    # shrinks); it is counted, not raised
-    for _ in range(args.warmup):
-        _, _, taus, _ = pfc.batch_step(solvers, states, taus, check=False)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    per = []
-    accepted = capped = 0
-    ev0.record()
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        acc, errs, taus, stats = pfc.batch_step(solvers, states, taus, check=False)
-        per.append(1e3 * (time.perf_counter() - t))
-        accepted += sum(acc)
-        capped += sum(1 for st3 in stats for x in st3 if x.status != 0)
-    ev1.record()
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    rows = sum(s.n for s in solvers)
-    for s in solvers:
-        s.close()
-    return {"metric": "PFC stage solves/s, batched independent instances", "value": 3 * len(wls) * args.steps / (ms / 1e3),
+    classes = sorted({(w.dim, autotune.size_class(w.side)) for w in wls})
+    tuned = {c: autotune.tuned(c[0], c[1], float(c[1]), args.precision) for c in classes}
+    tune_s = time.perf_counter() - t0
+    ms_def, _, _, _ = run(lambda w: {})
+    ms, per, accepted, capped = run(lambda w: tuned[(w.dim, autotune.size_class(w.side))])
+    rows = sum((2 * w.side + 1) ** w.dim for w in wls)
+    setup_s = tune_s
+    out = {"metric": "PFC stage solves/s, batched independent instances", "value": 3 * len(wls) * args.steps / (ms / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": f"{len(wls)} 2D instances, side log-uniform [16,256] (h=1), r~U(-0.5,-0.2), "
                                    f"psi_mean~U(-0.4,-0.2), amp 0.1, seeds 1000+b; {rows} dofs/field in total",
                        "launch": "one persistent cooperative launch per stage for all instances (segmented grid)"},
-            "step_ms": {"p50": pct(per, 50), "p99": pct(per, 99)}, "setup_s": setup_s,
+            "step_ms": {"p50": pct(per, 50), "p99": pct(per, 99)}, "autotune_s": setup_s,
             "accepted_steps": accepted, "stage_solves_not_converged": capped}
+    out["autotune"] = {"tuned_per_size_class": {f"{d}d-side{c}": cfg for (d, c), cfg in tuned.items()},
+                       "default_value": 3 * len(wls) * args.steps / (ms_def / 1e3),
+                       "gain_over_default": ms_def / ms}
+    return out
 
 
 def serve(args):
@@ -156,9 +175,11 @@ def serve(args):
 
     reqs = synth.serving_stream(args.requests, args.rate)
     free, total = torch.cuda.mem_get_info()
-    srv = serving.Server(budget_bytes=int(0.6 * free), precision=args.precision, outer_tol=1e-10,
+    srv = serving.Server(budget_bytes=int(0.6 * free), precision=args.precision, outer_tol=args.outer_tol,
+                         err_tol=args.err_tol, autotune=True,
                          initial_psi=lambda w: synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed))
     try:
+        srv.prepare(reqs)
         rep = srv.run(reqs)
     finally:
         srv.close()
@@ -903,8 +924,14 @@ def profile_case(args):
     import paper_1501_06852_gb300 as pfc
 
     w = workload(args.workload)
+    if args.profile_side > 0:
+        import dataclasses
+
+        w = dataclasses.replace(w, name=f"{w.name}-side{args.profile_side}", side=args.profile_side,
+                                length=w.length * args.profile_side / w.side)
     psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
-    s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol, max_outer=1)
+    s = pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=args.precision, outer_tol=args.outer_tol, max_outer=1,
+                      restart=max(2, args.profile_restart))
     x = s.init_state(psi0)
     s.assemble(x, w.tau0)
     b = s.stage_rhs(0, x)

@@ -127,6 +127,12 @@ typedef struct {
                          tau_guard tau*(r, <psi>), tau* the critical width of Lemma 3 at the
                          mean density <psi> of the state (conserved by the flow); must be
                          < 1; 0 (default): no cap beyond tau_max */
+  int grid_blocks;    /* > 0: the persistent solver of this context always runs on exactly
+                         min(grid_blocks, its 32-row slices, co-resident blocks) blocks, alone
+                         and in every batched launch, so its row partition and reduction
+                         order, hence its results bit for bit, do not depend on what else
+                         is in a batch (serving); 0 (default): alone it takes every
+                         co-resident block, in a batch a share proportional to its rows */
 } pfc_options;
 
 typedef struct {
@@ -150,7 +156,7 @@ typedef struct {
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
  * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20, degree = 2,
- * err_tol = 1e-9, tau_guard = 0. */
+ * err_tol = 1e-9, tau_guard = 0, grid_blocks = 0. */
 void pfc_default_options(pfc_options* opt);
 
 /* Critical time-step width of Lemma 3 (Section 6): the symbol of the PFC2 operator
@@ -271,6 +277,35 @@ pfc_status pfc_batch_stage_solve(pfc_ctx* const* ctxs, int count, const double* 
 pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states, double* taus, int* accepted,
                           double* errs, pfc_solve_stats* stats);
 
+/* A step in three stage launches, for continuous batching (not in the paper: its runs
+ * advance one simulation).  A server can then start a newly arrived simulation's
+ * step in the same launch that solves the second or third stage of others.
+ *
+ * pfc_step_begin: assembly at state (3n, device; read here and not kept) for width
+ * tau, as in pfc_step; enqueued, no synchronisation.  The context's stage becomes 0.
+ *
+ * pfc_batch_stage_advance: every context (each after pfc_step_begin, stage 0..2;
+ * same device, stream and inner precision; each once) forms its current stage's
+ * value x_i and right-hand side b_i^R (Eq. 3.10) and all of them solve their stage
+ * systems in one batched persistent launch (more launches when they exceed one
+ * co-resident grid); each context's stage then advances by one.  Contexts with
+ * options.grid_blocks > 0 keep their own block count and get the same bits as
+ * pfc_step.  One host synchronisation per call.  PFC_ERR_INVALID if a context has
+ * no begun step or has solved all three stages.
+ *
+ * pfc_step_finish: after the third stage, the step combination, error estimate,
+ * acceptance and next width exactly as pfc_step (same arguments, same state
+ * update, stats receives 3 entries); the context's stage becomes -1.
+ *
+ * pfc_step_stage: the context's stage: -1 no begun step, 0..2 the next stage to
+ * solve, 3 ready for pfc_step_finish.  Every other step, assembly or solve call
+ * abandons a begun step. */
+pfc_status pfc_step_begin(pfc_ctx* ctx, const double* state, double tau);
+pfc_status pfc_batch_stage_advance(pfc_ctx* const* ctxs, int count);
+pfc_status pfc_step_finish(pfc_ctx* ctx, double* state, double* tau, int* accepted, double* err,
+                           pfc_solve_stats* stats);
+int pfc_step_stage(const pfc_ctx* ctx);
+
 /* Failure-detection self-test: launches a PCG whose grid barriers wait for one
  * block more than the grid holds, so every wait runs out after limit_seconds
  * (0 < limit <= 10).  The kernel sets its timeout bit and returns; the context
@@ -291,6 +326,22 @@ pfc_status pfc_counters(const pfc_ctx* ctx, long long* kernel_launches, long lon
 /* Host-only inspection of the mesh/pattern builder (no GPU needed):
  * out4 = {n, nnz of one block, stored SELL slots, elements}. */
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
+
+/* Row-block partition of one instance over nparts devices (host only, no GPU).
+ * The paper's parallel runs distribute the rows of the stage system over MPI
+ * processes in contiguous blocks, with a halo exchange per matrix-vector product
+ * and a global sum per inner product (PETSc, Section 7).  This is the plan such a
+ * multi-device solve uses here: each field's lexicographic rows (same cut in
+ * mu, psi and omega) are split into nparts strips of whole lattice lines (2D) or
+ * planes (3D), balanced by nonzeros; a strip's columns reach at most `degree`
+ * lines beyond it, so it exchanges ghost values with its two neighbours only.
+ * row_begin (nparts + 1): first row of each part and n; halo (2 nparts): ghost
+ * rows below and above part k (in [2k], [2k + 1]); part_nnz (nparts): nonzeros of
+ * one block in part k.  PFC_ERR_INVALID for bad sizes or when a part would hold
+ * fewer than `degree` lines.  This build runs one device per instance; the plan is
+ * exercised by a multi-process CPU test of the partitioned solve. */
+pfc_status pfc_host_partition(int dim, int side, double length, int degree, int nparts, int64_t* row_begin,
+                              int64_t* halo, int64_t* part_nnz);
 
 /* Host-only inspection of the structured stencils (no GPU needed):
  * out3 = {rows that use the stencil, nonzeros of the rows that keep their

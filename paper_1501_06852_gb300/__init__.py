@@ -20,7 +20,7 @@ from . import build as _build
 from .build import LIB as _LIB_PATH
 
 __all__ = ["PFCSolver", "PFCError", "SolveStats", "lib", "critical_tau", "ROS3PW_GAMMA",
-           "batch_stage_solve", "batch_step",
+           "batch_stage_solve", "batch_step", "batch_stage_advance",
            "OP_M", "OP_K", "OP_A01", "OP_AR", "OP_PCH", "PRECISIONS"]
 
 OP_M, OP_K, OP_A01, OP_AR, OP_PCH = 0, 1, 2, 3, 4
@@ -43,7 +43,8 @@ class _Options(ctypes.Structure):
                 ("schur_its", ctypes.c_int),
                 ("degree", ctypes.c_int),
                 ("err_tol", ctypes.c_double),
-                ("tau_guard", ctypes.c_double)]
+                ("tau_guard", ctypes.c_double),
+                ("grid_blocks", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -76,11 +77,18 @@ def _load():
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_host_partition": (I, [I, I, D, I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)]),
         "pfc_batch_stage_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P),
                                       ctypes.POINTER(_Stats)]),
         "pfc_batch_step": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(D), ctypes.POINTER(I),
                                ctypes.POINTER(D), ctypes.POINTER(_Stats)]),
         "pfc_set_timing": (I, [P, I]),
+        "pfc_step_begin": (I, [P, P, D]),
+        "pfc_batch_stage_advance": (I, [ctypes.POINTER(P), I]),
+        "pfc_step_finish": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(I), ctypes.POINTER(D),
+                                ctypes.POINTER(_Stats)]),
+        "pfc_step_stage": (I, [P]),
         "pfc_step_combine_static": (I, [ctypes.c_int64, P, P, D, D, P, P, P]),
         "pfc_counters": (I, [P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(D)]),
@@ -183,6 +191,28 @@ def batch_step(solvers, states, taus, check: bool = True):
     return [bool(a) for a in acc], list(errs), list(tt), out
 
 
+def batch_stage_advance(solvers):
+    """One batched launch solving every solver's next stage of its begun step
+    (pfc_batch_stage_advance); each solver's stage advances by one."""
+    if not solvers:
+        raise ValueError("no solvers")
+    st = lib.pfc_batch_stage_advance(_handles(solvers), len(solvers))
+    if st != 0:
+        raise PFCError(st, lib.pfc_last_error(solvers[0]._h).decode())
+
+
+def host_partition(dim: int, side: int, length: float, nparts: int, degree: int = 2) -> dict:
+    """Row-block (strip) partition of one instance over nparts devices (pfc_host_partition):
+    {"begin": row offsets (nparts + 1), "halo": [(below, above)] * nparts, "nnz": per part}."""
+    b = (ctypes.c_int64 * (nparts + 1))()
+    h = (ctypes.c_int64 * (2 * nparts))()
+    z = (ctypes.c_int64 * nparts)()
+    st = lib.pfc_host_partition(dim, side, float(length), degree, nparts, b, h, z)
+    if st != 0:
+        raise PFCError(st, "host_partition")
+    return {"begin": list(b), "halo": [(h[2 * k], h[2 * k + 1]) for k in range(nparts)], "nnz": list(z)}
+
+
 def host_stencil(dim: int, side: int, length: float = 1.0) -> dict:
     """Stencil sizes from the host builder (no GPU needed)."""
     out = (ctypes.c_int64 * 3)()
@@ -205,7 +235,7 @@ class PFCSolver:
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
                  inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
                  schur: int = 0, schur_its: int = 20, degree: int = 2, err_tol: float = 1e-9,
-                 tau_guard: float = 0.0, stream=None):
+                 tau_guard: float = 0.0, grid_blocks: int = 0, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -229,6 +259,7 @@ class PFCSolver:
         o.degree = degree
         o.err_tol = err_tol
         o.tau_guard = tau_guard
+        o.grid_blocks = grid_blocks
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()
@@ -292,6 +323,28 @@ class PFCSolver:
         stats = (_Stats * 3)()
         st = lib.pfc_step(self._h, self._vec(state, 3 * self.n, "state"), ctypes.byref(t), ctypes.byref(acc),
                           ctypes.byref(err), stats)
+        if check:
+            self._check(st)
+        return bool(acc.value), err.value, t.value, [SolveStats._from(s) for s in stats]
+
+    def step_begin(self, state, tau: float):
+        """Assembly for a stage-wise step (pfc_step_begin); the stages are solved by
+        batch_stage_advance and the step completed by step_finish."""
+        self._check(lib.pfc_step_begin(self._h, self._vec(state, 3 * self.n, "state"), float(tau)))
+
+    @property
+    def stage(self) -> int:
+        """-1 no begun step, 0..2 next stage, 3 ready for step_finish (pfc_step_stage)."""
+        return int(lib.pfc_step_stage(self._h))
+
+    def step_finish(self, state, tau: float, check: bool = True):
+        """Completes a stage-wise step like step(): returns (accepted, err, tau_next, stats)."""
+        t = ctypes.c_double(tau)
+        acc = ctypes.c_int(0)
+        err = ctypes.c_double(0.0)
+        stats = (_Stats * 3)()
+        st = lib.pfc_step_finish(self._h, self._vec(state, 3 * self.n, "state"), ctypes.byref(t), ctypes.byref(acc),
+                                 ctypes.byref(err), stats)
         if check:
             self._check(st)
         return bool(acc.value), err.value, t.value, [SolveStats._from(s) for s in stats]

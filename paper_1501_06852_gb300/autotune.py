@@ -4,8 +4,10 @@ For a problem class (dimension, side, inner precision) it times the inner solve
 of each candidate configuration on the device and keeps the fastest:
 
 * ``inner_operator``: assembled SELL-32 values and indices, or structured stencils;
-* ``pcg_variant``: textbook, pipelined or Chronopoulos-Gear Jacobi-PCG;
-* ``blocks_per_sm``: one or two resident blocks of the cooperative grid per SM.
+* ``pcg_variant``: textbook, pipelined or Chronopoulos-Gear Jacobi-PCG.
+
+(The persistent kernel runs 1024-thread blocks, one per SM, so the grid's
+residency is not a candidate.)
 
 The timing unit is a fixed-iteration PCG solve with M + sqrt(delta) K, the matrix of
 the preconditioner's most frequent inner solves (steps 3.1 and 3.2), through
@@ -15,11 +17,14 @@ not excluded here: FGMRES absorbs it at the price of outer iterations, which thi
 per-iteration timing does not see; ``pcg_variant`` candidates are therefore
 limited to the forms that keep the outer iteration count (textbook and
 Chronopoulos-Gear in float32/float16; all three in float64).
-Results are cached per process.
+Results are cached per process.  ``tuned`` gives the configuration of a size
+class (the mesh side rounded to a power of two at the same spacing), so that a
+batch or a server with many sizes tunes a handful of classes, not every size.
 """
 from __future__ import annotations
 
 import itertools
+import math
 import time
 
 _CACHE: dict = {}
@@ -27,8 +32,19 @@ _CACHE: dict = {}
 
 def candidates(precision: str):
     variants = (0, 1, 3) if precision == "fp64" else (0, 3)
-    return [dict(inner_operator=io, pcg_variant=v, blocks_per_sm=b)
-            for io, v, b in itertools.product((0, 1), variants, (1, 2))]
+    return [dict(inner_operator=io, pcg_variant=v) for io, v in itertools.product((0, 1), variants)]
+
+
+def size_class(side: int) -> int:
+    """The power of two nearest to side (in log scale), between 8 and 512."""
+    return int(min(512, max(8, 2 ** round(math.log2(max(side, 1))))))
+
+
+def tuned(dim: int, side: int, length: float, precision: str = "fp32", **kw) -> dict:
+    """Tuned options of the size class of (dim, side): the fastest configuration
+    timed on the class's representative mesh at the same spacing."""
+    rep = size_class(side)
+    return tune(dim, rep, length * rep / side, precision, **kw)["config"]
 
 
 def tune(dim: int, side: int, length: float, precision: str = "fp32", iters: int = 60, reps: int = 2,

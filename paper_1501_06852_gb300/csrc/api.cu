@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
 
 #include "device.cuh"
@@ -99,6 +100,8 @@ struct pfc_ctx {
   int* h_errw = nullptr;
   bool assembled = false;
   bool last_rejected = false;   // the previous pfc_step attempt was rejected
+  int step_stage = -1;          // stage-wise step (pfc_step_begin): next stage 0..2, 3 = ready to finish
+  bool fixed_grid = false;      // options.grid_blocks > 0: the solver always uses G blocks
   double tau = 0.0, delta = 0.0;
   double gamma = kGamma;        // scaling of the (1,1) block: Ros3Pw gamma, or 1 for the Euler system
   // PFC1 (model 1): second block row A10 = tau K_+(psi_k), A11 = M / gamma + tau F(mu_k),
@@ -370,6 +373,50 @@ pfc_status check_ctx(pfc_ctx* c) {
   return PFC_OK;
 }
 
+// The end of a step attempt after its three stage solves (Eq. 3.6, 3.7):
+// x^{k+1} and the embedded error estimate, one synchronisation, accept/reject,
+// the next width.  Shared by pfc_step and pfc_step_finish.
+pfc_status finish_step(pfc_ctx* c, double* state, double* tau, int* accepted, double* err, pfc_solve_stats* stats) {
+  const int np = c->n_pad;
+  const size_t np3 = 3 * (size_t)np;
+  pfc_status st = PFC_OK;
+  double e[3];
+  for (int j = 0; j < 3; ++j) e[j] = kMhat[j] - kM[j];
+  LAUNCH(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
+                              c->xnew, c->step_part, pfc::step_partials(), c->stream));
+  LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
+  if (width_guard_on(c)) {
+    st = enqueue_mean_psi(c);
+    if (st != PFC_OK) return st;
+  }
+  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  harvest(c);
+  int werr = 0;
+  for (int i = 0; i < 3; ++i) {
+    fill_stats(c->h_stats[i], c->h_errw[i], stats ? stats + i : nullptr);
+    werr |= c->h_errw[i];
+  }
+  const double ev = c->h_err[0];
+  if (err) *err = ev;
+  st = status_from_err(werr);
+  if (st == PFC_ERR_TIMEOUT || st == PFC_ERR_NONFINITE || !std::isfinite(ev)) {
+    if (accepted) *accepted = 0;
+    return fail(c, st == PFC_OK ? PFC_ERR_NONFINITE : st, "step failed in a stage solve");
+  }
+  const bool acc = ev <= 1.0 && st == PFC_OK;
+  if (accepted) *accepted = acc ? 1 : 0;
+  if (acc) LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
+  double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
+  if (acc && c->last_rejected) fac = std::min(fac, 1.0);  // no growth right after a rejection
+  c->last_rejected = !acc;
+  *tau = std::min(*tau * fac, width_cap(c, c->h_err[1]));
+  if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
+  return PFC_OK;
+}
+
 // ---------------------------------------------------------------- batches
 // Device and pinned staging buffers of batched launches (per device, grown on demand).
 struct BatchSpace {
@@ -441,6 +488,24 @@ void plan_segments(pfc_ctx* const* ctxs, int count, int max_blocks, std::vector<
                    std::vector<std::pair<int, int>>& waves) {
   Gs.assign(count, 1);
   waves.clear();
+  bool fixed = true;
+  for (int k = 0; k < count; ++k) fixed = fixed && ctxs[k]->fixed_grid;
+  if (fixed) {
+    // every instance keeps its own block count (its partition, hence its results, do not
+    // depend on the rest of the batch); waves fill the co-resident grid in order
+    int lo = 0, used = 0;
+    for (int k = 0; k < count; ++k) {
+      Gs[k] = std::min(ctxs[k]->G, max_blocks);
+      if (k > lo && used + Gs[k] > max_blocks) {
+        waves.emplace_back(lo, k);
+        lo = k;
+        used = 0;
+      }
+      used += Gs[k];
+    }
+    waves.emplace_back(lo, count);
+    return;
+  }
   for (int lo = 0; lo < count; lo += max_blocks) {
     const int hi = std::min(count, lo + max_blocks);
     long long rows = 0;
@@ -468,14 +533,23 @@ void plan_segments(pfc_ctx* const* ctxs, int count, int max_blocks, std::vector<
   }
 }
 
-// Enqueues the batched FGMRES solves of stage `slot` for every instance: b = ctx->bv,
-// y = ys + slot * 3 n_pad (or tmp3 for slot 3), stats and error word in `slot`.
-pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, BatchSpace* space, size_t region) {
+// Enqueues the batched FGMRES solves for every instance: b = ctx->bv, y = ys + slot * 3 n_pad
+// (or tmp3 when to_tmp), stats and error word in `slot`, with slot = slots[k] of the
+// instance (its own stage) or the common `slot` when slots is null.
+pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, BatchSpace* space, size_t region,
+                     const int* slots = nullptr) {
   // Instances are taken largest first, so that when they need several waves each wave
   // holds instances of similar size (a wave lasts as long as its largest solve).  All
   // outputs are per context, so the order changes nothing else.
-  std::vector<pfc_ctx*> order(ctxs_in, ctxs_in + count);
-  std::stable_sort(order.begin(), order.end(), [](const pfc_ctx* x, const pfc_ctx* y) { return x->n_pad > y->n_pad; });
+  std::vector<int> idx(count);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return ctxs_in[x]->n_pad > ctxs_in[y]->n_pad; });
+  std::vector<pfc_ctx*> order(count);
+  std::vector<int> slot_of(count);
+  for (int k = 0; k < count; ++k) {
+    order[k] = ctxs_in[idx[k]];
+    slot_of[k] = slots ? slots[idx[k]] : slot;
+  }
   pfc_ctx* const* ctxs = order.data();
   pfc_ctx* c0 = ctxs[0];      // stream, device and precision are shared by all
   pfc_ctx* c = ctxs_in[0];    // errors are reported on the caller's first context
@@ -508,16 +582,17 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
       pfc::SolveArgs a = base_args(ck, ck->prec);
       a.win_cap = 0;  // segments of different instances: no shared-memory window
       a.mode = 0;
+      const int sk = slot_of[wv.first + i];
       a.b = ck->bv;
-      a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)slot * 3 * ck->n_pad;
+      a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)sk * 3 * ck->n_pad;
       a.blk = ck->blk_b;
-      a.stats = ck->stats + slot;
-      a.err = ck->errw + slot;
+      a.stats = ck->stats + sk;
+      a.err = ck->errw + sk;
       hargs[i] = a;
       hseg[i + 1] = hseg[i] + Gs[wv.first + i];
       CK(cudaMemsetAsync(ck->arrive, 0, sizeof(unsigned) * (4 + (size_t)ck->G), ck->stream));
-      CK(cudaMemsetAsync(ck->errw + slot, 0, sizeof(int), ck->stream));
-      CK(cudaMemsetAsync(ck->stats + slot, 0, sizeof(pfc::DevStats), ck->stream));
+      CK(cudaMemsetAsync(ck->errw + sk, 0, sizeof(int), ck->stream));
+      CK(cudaMemsetAsync(ck->stats + sk, 0, sizeof(pfc::DevStats), ck->stream));
     }
     c = ctxs_in[0];
     const size_t bytes = sizeof(pfc::SolveArgs) * n + sizeof(int) * (n + 1);
@@ -581,6 +656,7 @@ void pfc_default_options(pfc_options* o) {
   o->degree = 2;
   o->err_tol = 1e-9;
   o->tau_guard = 0.0;
+  o->grid_blocks = 0;
 }
 
 double pfc_critical_tau(double r, double psi_bar) { return critical_tau(r, psi_bar); }
@@ -658,6 +734,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "err_tol must be finite and >= 0"));
   if (!(c->opt.tau_guard >= 0.0) || !(c->opt.tau_guard < 1.0))
     return bail(fail(c, PFC_ERR_INVALID, "tau_guard must be in [0, 1)"));
+  if (c->opt.grid_blocks < 0) return bail(fail(c, PFC_ERR_INVALID, "grid_blocks must be >= 0"));
   c->model = c->opt.model;
   c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
@@ -714,6 +791,10 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (c->opt.blocks_per_sm > 0) bps = std::min(bps, c->opt.blocks_per_sm);
   if (bps < 1) return bail(fail(c, PFC_ERR_CUDA, "solver kernel does not fit on an SM"));
   c->G = std::max(1, std::min(std::min(sms * bps, c->nslices), pfc::solve_threads()));
+  if (c->opt.grid_blocks > 0) {
+    c->G = std::min(c->G, c->opt.grid_blocks);
+    c->fixed_grid = true;
+  }
   // Slice ranges: blocks and, inside each block, warps get contiguous runs of
   // slices of equal cost, cost(slice) = 32 * (width + 10) ~ bytes of one SpMV
   // row plus the vector traffic of the inner iteration.  With structured stencils
@@ -934,8 +1015,6 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
       if (cudaEventCreate(&c->ev[k][j]) != cudaSuccess) return bail(fail(c, PFC_ERR_CUDA, "cudaEventCreate failed"));
 
   // ---- uploads ----
-  std::vector<int> perm_pad(S.n_pad, 0);
-  std::copy(S.perm.begin(), S.perm.end(), perm_pad.begin());
 #define UP(dst, vec) CK_SETUP(cudaMemcpy(dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice))
 #define CK_SETUP(call)                                                                         \
   do {                                                                                         \
@@ -946,7 +1025,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   UP(c->slice_ptr, S.slice_ptr);
   UP(c->cols, S.cols);
   UP(c->diag, S.diag_pos);
-  UP(c->perm, perm_pad);
+  UP(c->perm, S.perm);
   UP(c->elem, S.elem_int);
   UP(c->cptr, S.contrib_ptr);
   if (!S.contrib_idx.empty()) UP(c->cidx, S.contrib_idx);
@@ -1000,6 +1079,7 @@ pfc_status pfc_assemble(pfc_ctx* c, const double* state, double tau) {
   pfc_status st = check_ctx(c);
   if (st != PFC_OK) return st;
   if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "state must be non-null and tau > 0");
+  c->step_stage = -1;
   LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, state, c->xk, c->stream));
   return assemble_internal(c, tau);
 }
@@ -1026,16 +1106,28 @@ pfc_status pfc_stage_solve(pfc_ctx* c, const double* b, double* y, pfc_solve_sta
   if (!c->assembled) return fail(c, PFC_ERR_INVALID, "pfc_assemble must come first");
   if (!b || !y) return fail(c, PFC_ERR_INVALID, "null vector");
   LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, b, c->bv, c->stream));
-  pfc::SolveArgs a = base_args(c, c->prec);
-  a.mode = 0;
-  a.b = c->bv;
-  a.y = c->tmp3;
-  st = run_solver(c, a, c->prec, 0);
+  std::unique_lock<std::mutex> lk(g_batch_mutex, std::defer_lock);
+  if (c->fixed_grid) {
+    // fixed block count: the batched kernel, as in every batch (same bits alone and batched)
+    lk.lock();
+    BatchSpace* space = nullptr;
+    st = batch_space(c, batch_region_bytes(1), space);
+    if (st != PFC_OK) return st;
+    pfc_ctx* one[1] = {c};
+    st = run_batch(one, 1, 0, true, space, 0);
+  } else {
+    pfc::SolveArgs a = base_args(c, c->prec);
+    a.mode = 0;
+    a.b = c->bv;
+    a.y = c->tmp3;
+    st = run_solver(c, a, c->prec, 0);
+  }
   if (st != PFC_OK) return st;
   LAUNCH(pfc::launch_scatter_out(c->n, c->n_pad, 3, c->perm, c->tmp3, y, c->stream));
   CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (lk.owns_lock()) lk.unlock();
   harvest(c);
   fill_stats(c->h_stats[0], c->h_errw[0], stats);
   st = status_from_err(c->h_errw[0]);
@@ -1049,9 +1141,31 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
   if (!state || !tau || !(*tau > 0.0) || !std::isfinite(*tau)) return fail(c, PFC_ERR_INVALID, "bad step arguments");
   const int np = c->n_pad;
   const size_t np3 = 3 * (size_t)np;
+  c->step_stage = -1;
   LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
   st = assemble_internal(c, *tau);
   if (st != PFC_OK) return st;
+  if (c->fixed_grid) {
+    // a context with a fixed block count solves through the batched kernel (as a batch
+    // of one), the kernel every batched launch runs, so its results are the same bits
+    // alone and in a batch
+    std::lock_guard<std::mutex> lk(g_batch_mutex);
+    BatchSpace* space = nullptr;
+    const size_t region = batch_region_bytes(1);
+    st = batch_space(c, 3 * region, space);
+    if (st != PFC_OK) return st;
+    pfc_ctx* one[1] = {c};
+    for (int i = 0; i < 3; ++i) {
+      LAUNCH(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1],
+                                       c->xi, c->dvec, c->stream));
+      st = rhs_at_stage(c, i > 0);
+      if (st != PFC_OK) return st;
+      st = run_batch(one, 1, i, false, space, (size_t)i * region);
+      if (st != PFC_OK) return st;
+    }
+    // the staged launch arguments are read before this synchronisation returns
+    return finish_step(c, state, tau, accepted, err, stats);
+  }
   for (int i = 0; i < 3; ++i) {
     LAUNCH(pfc::launch_stage_combine(np, c->xk, c->ys, c->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1], c->xi,
                                  c->dvec, c->stream));
@@ -1065,47 +1179,70 @@ pfc_status pfc_step(pfc_ctx* c, double* state, double* tau, int* accepted, doubl
     st = run_solver(c, a, c->prec, i);
     if (st != PFC_OK) return st;
   }
-  double e[3];
-  for (int j = 0; j < 3; ++j) e[j] = kMhat[j] - kM[j];
-  LAUNCH(pfc::launch_step_combine(np, c->xk, c->ys, c->ys + np3, c->ys + 2 * np3, kM, e, c->opt.step_atol, c->opt.step_rtol,
-                              c->xnew, c->step_part, pfc::step_partials(), c->stream));
-  LAUNCH(pfc::launch_reduce_partials(pfc::step_partials(), c->step_part, 1.0 / c->n, c->err_scalar, c->stream));
-  if (width_guard_on(c)) {
-    st = enqueue_mean_psi(c);
+  return finish_step(c, state, tau, accepted, err, stats);
+}
+
+pfc_status pfc_step_begin(pfc_ctx* c, const double* state, double tau) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "bad step arguments");
+  c->step_stage = -1;
+  LAUNCH(pfc::launch_gather_in(c->n, c->n_pad, 3, c->perm, state, c->xk, c->stream));
+  st = assemble_internal(c, tau);
+  if (st != PFC_OK) return st;
+  c->step_stage = 0;
+  return PFC_OK;
+}
+
+int pfc_step_stage(const pfc_ctx* c) { return c ? c->step_stage : -1; }
+
+pfc_status pfc_batch_stage_advance(pfc_ctx* const* ctxs, int count) {
+  pfc_status st = check_batch(ctxs, count);
+  if (st != PFC_OK) return st;
+  pfc_ctx* c = ctxs[0];
+  for (int k = 0; k < count; ++k)
+    if (ctxs[k]->step_stage < 0 || ctxs[k]->step_stage > 2)
+      return fail(c, PFC_ERR_INVALID, "every context needs a begun step with a stage left (pfc_step_begin)");
+  std::lock_guard<std::mutex> lk(g_batch_mutex);
+  BatchSpace* space = nullptr;
+  st = batch_space(c, batch_region_bytes(count), space);
+  if (st != PFC_OK) return st;
+  std::vector<int> slots(count);
+  for (int k = 0; k < count; ++k) {
+    pfc_ctx* ck = ctxs[k];
+    c = ck;
+    const int i = ck->step_stage, np = ck->n_pad;
+    const size_t np3 = 3 * (size_t)np;
+    slots[k] = i;
+    LAUNCH(pfc::launch_stage_combine(np, ck->xk, ck->ys, ck->ys + np3, i, kA[i][0], kA[i][1], kC[i][0], kC[i][1],
+                                     ck->xi, ck->dvec, ck->stream));
+    st = rhs_at_stage(ck, i > 0);
     if (st != PFC_OK) return st;
   }
-  CK(cudaMemcpyAsync(c->h_stats, c->stats, sizeof(pfc::DevStats) * 3, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_errw, c->errw, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_err, c->err_scalar, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+  c = ctxs[0];
+  st = run_batch(ctxs, count, 0, false, space, 0, slots.data());
+  if (st != PFC_OK) return st;
+  for (int k = 0; k < count; ++k) ctxs[k]->step_stage += 1;
+  // the launch's arguments were staged in pinned memory that the next call reuses
   CK(cudaStreamSynchronize(c->stream));
-  harvest(c);
-  int werr = 0;
-  for (int i = 0; i < 3; ++i) {
-    fill_stats(c->h_stats[i], c->h_errw[i], stats ? stats + i : nullptr);
-    werr |= c->h_errw[i];
-  }
-  const double ev = c->h_err[0];
-  if (err) *err = ev;
-  st = status_from_err(werr);
-  if (st == PFC_ERR_TIMEOUT || st == PFC_ERR_NONFINITE || !std::isfinite(ev)) {
-    if (accepted) *accepted = 0;
-    return fail(c, st == PFC_OK ? PFC_ERR_NONFINITE : st, "step failed in a stage solve");
-  }
-  const bool acc = ev <= 1.0 && st == PFC_OK;
-  if (accepted) *accepted = acc ? 1 : 0;
-  if (acc) LAUNCH(pfc::launch_scatter_out(c->n, np, 3, c->perm, c->xnew, state, c->stream));
-  double fac = ev == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(ev, -1.0 / 3.0)));
-  if (acc && c->last_rejected) fac = std::min(fac, 1.0);  // no growth right after a rejection
-  c->last_rejected = !acc;
-  *tau = std::min(*tau * fac, width_cap(c, c->h_err[1]));
-  if (st != PFC_OK) return fail(c, st, "a stage solve did not converge");
   return PFC_OK;
+}
+
+pfc_status pfc_step_finish(pfc_ctx* c, double* state, double* tau, int* accepted, double* err,
+                           pfc_solve_stats* stats) {
+  pfc_status st = check_ctx(c);
+  if (st != PFC_OK) return st;
+  if (!state || !tau || !(*tau > 0.0) || !std::isfinite(*tau)) return fail(c, PFC_ERR_INVALID, "bad step arguments");
+  if (c->step_stage != 3) return fail(c, PFC_ERR_INVALID, "the step's three stages have not been solved");
+  c->step_stage = -1;
+  return finish_step(c, state, tau, accepted, err, stats);
 }
 
 pfc_status pfc_euler_step(pfc_ctx* c, double* state, double tau, pfc_solve_stats* stats) {
   pfc_status st = check_ctx(c);
   if (st != PFC_OK) return st;
   if (!state || !(tau > 0.0) || !std::isfinite(tau)) return fail(c, PFC_ERR_INVALID, "bad euler step arguments");
+  c->step_stage = -1;
   const int np = c->n_pad;
   LAUNCH(pfc::launch_gather_in(c->n, np, 3, c->perm, state, c->xk, c->stream));
   // A of Eq. (3.4): the stage matrix with gamma = 1, A01 = -(1+r) M + N(psi_k) + 2 K
@@ -1308,6 +1445,7 @@ pfc_status pfc_batch_step(pfc_ctx* const* ctxs, int count, double* const* states
   for (int k = 0; k < count; ++k) {
     pfc_ctx* ck = ctxs[k];
     c = ck;
+    ck->step_stage = -1;
     LAUNCH(pfc::launch_gather_in(ck->n, ck->n_pad, 3, ck->perm, states[k], ck->xk, ck->stream));
     st = assemble_internal(ck, taus[k]);
     if (st != PFC_OK) return st;
@@ -1400,16 +1538,12 @@ pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3) {
   std::string err;
   if (!pfc::build_setup(dim, side, length, S, err, 1)) return PFC_ERR_INVALID;
   int64_t interior = 0, bnnz = 0;
-  for (int p = 0; p < S.n; ++p) {
-    if (S.rowinfo[p] & 8) {
-      ++interior;
-    } else {
-      bnnz += 0;  // counted below from the row's stored slots
-    }
-  }
-  // nonzeros of the rows that keep their assembled values (true row lengths)
-  for (int p = 0; p < S.n; ++p) {
-    if (S.rowinfo[p] & 8) continue;
+  for (int p = 0; p < S.n_pad; ++p)
+    if (S.rowinfo[p] & 8) ++interior;
+  // nonzeros of the rows that keep their assembled values (true row lengths; rows
+  // that hold no dof have none)
+  for (int p = 0; p < S.n_pad; ++p) {
+    if ((S.rowinfo[p] & 8) || S.perm[p] < 0) continue;
     const int s = p / pfc::kSellC, lane = p % pfc::kSellC, base = S.slice_ptr[s] + lane;
     const int w = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / pfc::kSellC;
     for (int j = 0; j < w; ++j)
@@ -1418,6 +1552,18 @@ pfc_status pfc_host_stencil(int dim, int side, double length, int64_t* out3) {
   out3[0] = interior;
   out3[1] = bnnz;
   out3[2] = (int64_t)S.st_off.size();
+  return PFC_OK;
+}
+
+pfc_status pfc_host_partition(int dim, int side, double length, int degree, int nparts, int64_t* row_begin,
+                              int64_t* halo, int64_t* part_nnz) {
+  if (!row_begin || !halo || !part_nnz || nparts < 1) return PFC_ERR_INVALID;
+  std::vector<int64_t> b, h, z;
+  std::string err;
+  if (!pfc::build_partition(dim, side, length, degree, nparts, b, h, z, err)) return PFC_ERR_INVALID;
+  std::copy(b.begin(), b.end(), row_begin);
+  std::copy(h.begin(), h.end(), halo);
+  std::copy(z.begin(), z.end(), part_nnz);
   return PFC_OK;
 }
 

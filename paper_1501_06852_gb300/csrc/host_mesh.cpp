@@ -9,13 +9,15 @@
 // midpoint of its end points.  P1 dofs (degree 1) are the vertices themselves.
 //
 // Device layout.  All blocks of the stage matrix (M, K, A01 and the inner
-// matrices) share one sparsity pattern, stored once as SELL-32-sigma: rows are
-// sorted by length (descending) inside windows of kSellSigma lexicographic rows,
-// grouped in slices of 32 rows, and each slice is stored column-major with the
-// width of its longest row.  The sorted row order IS the internal dof order of
-// every device vector, so a SpMV writes y[row] coalesced and a vector update
-// touches 32 consecutive rows per warp.  Padding slots point at their own row
-// with value 0.
+// matrices) share one sparsity pattern, stored once as SELL-32-sigma: slices of
+// 32 rows, each stored column-major with the width of its longest row.  The row
+// order IS the internal dof order of every device vector, so a SpMV writes y[row]
+// coalesced and a vector update touches 32 consecutive rows per warp.  Without
+// structured stencils rows are sorted by length (descending) inside windows of
+// kSellSigma lexicographic rows; with them (sigma = 1) the P2 rows are numbered
+// line by line with each line split by x parity (line_layout) and P1 rows
+// lexicographically.  Padding rows hold no dof; padding slots point at their own
+// row with value 0.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -26,10 +28,44 @@
 #include <omp.h>
 #endif
 
+// 1: P2 rows with structured stencils in the line-split order (line_layout); 0: lexicographic
+#ifndef PFC_LINE_LAYOUT
+#define PFC_LINE_LAYOUT 1
+#endif
+
 namespace pfc {
 
 void element_path(int dim, int t, int verts[4][3]);
 void local_edge(int dim, int e, int& a, int& b);
+
+// Row order of the P2 lattice with structured stencils.  Lattice points (a, b, c),
+// 0 <= a, b, c <= 2 side, are numbered line by line (x lines, lexicographic in
+// (b, c)), and inside each line the points with even a (on the vertices' x
+// positions) come first, then those with odd a:
+//     row(a, b, c) = ((c lat + b) lat) + (a even ? a / 2 : side + 1 + a / 2).
+// Every line keeps its lat = 2 side + 1 rows, so a neighbour at a fixed lattice
+// offset from a point of type t (the coordinate parities) is at a fixed row offset
+// again: the interior stencil of a type is one list of row offsets.  In plain
+// lexicographic order consecutive rows of a line alternate between the vertex-x and
+// edge-x types, whose stencils have 19 and 9 entries (2D) or 65 and 19-27 (3D), and a
+// warp's loop runs to the longer one for all 32 lanes; here a warp's 32 rows have
+// one type except near the middle and the ends of a line.  Rows stay in their
+// lattice line, so the stencil reads of a block keep the locality of the
+// lexicographic order (numbering the parity classes one after another instead
+// spread a block's reads over four or eight distant regions and lost more in L1
+// hits than it saved in loop iterations).
+void line_layout(int dim, int side, HostSetup& S) {
+  const int64_t lat = 2 * (int64_t)side + 1, half = side + 1;
+  S.n_pad = (int)((S.n + kSellC - 1) / kSellC * kSellC);
+  S.perm.assign(S.n_pad, -1);
+  for (int64_t i = 0; i < S.n; ++i) {
+    const int64_t a = i % lat, line = i / lat;
+    const int64_t p = line * lat + ((a & 1) ? half + (a >> 1) : (a >> 1));
+    S.perm[p] = (int)i;
+    S.iperm[i] = (int)p;
+  }
+  (void)dim;
+}
 
 bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma, int degree) {
   if (dim != 2 && dim != 3) {
@@ -124,23 +160,31 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   S.nnz = 0;
   for (int i = 0; i < n; ++i) S.nnz += len[i];
 
-  // --- SELL-32-sigma ordering -------------------------------------------------
-  S.perm.resize(n);
-  std::iota(S.perm.begin(), S.perm.end(), 0);
-  for (int w0 = 0; w0 < n; w0 += S.sigma) {
-    int w1 = std::min(n, w0 + S.sigma);
-    std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
+  // --- internal row order ------------------------------------------------------
+  // perm: internal row -> lexicographic dof, -1 for rows that hold no dof (padding).
+  // With structured stencils on P2 (sigma == 1) each lattice line is split by the
+  // parity of x (see line_layout); otherwise SELL-32-sigma: rows sorted by length
+  // inside windows of sigma lexicographic rows.  Padding rows at the end.
+  S.iperm.assign(n, -1);
+  if (S.sigma == 1 && degree == 2 && PFC_LINE_LAYOUT) {
+    line_layout(dim, side, S);
+  } else {
+    S.n_pad = (n + kSellC - 1) / kSellC * kSellC;
+    S.perm.assign(S.n_pad, -1);
+    std::iota(S.perm.begin(), S.perm.begin() + n, 0);
+    for (int w0 = 0; w0 < n; w0 += S.sigma) {
+      int w1 = std::min(n, w0 + S.sigma);
+      std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
+    }
+    for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
   }
-  S.iperm.resize(n);
-  for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
-  S.nslices = (n + kSellC - 1) / kSellC;
-  S.n_pad = S.nslices * kSellC;
+  S.nslices = S.n_pad / kSellC;
   S.slice_ptr.assign(S.nslices + 1, 0);
   for (int s = 0; s < S.nslices; ++s) {
     int w = 0;
     for (int l = 0; l < kSellC; ++l) {
-      int p = s * kSellC + l;
-      if (p < n) w = std::max(w, len[S.perm[p]]);
+      const int i = S.perm[s * kSellC + l];
+      if (i >= 0) w = std::max(w, len[i]);
     }
     S.slice_ptr[s + 1] = S.slice_ptr[s] + w * kSellC;
   }
@@ -177,11 +221,11 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
       int s = p / kSellC, lane = p % kSellC;
       int base = S.slice_ptr[s] + lane;
       int w = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / kSellC;
-      if (p >= n) {
+      const int i = S.perm[p];
+      if (i < 0) {
         for (int j = 0; j < w; ++j) S.cols[base + j * kSellC] = p;
         continue;
       }
-      int i = S.perm[p];
       row_cols(i, buf);
       for (int j = 0; j < w; ++j) S.cols[base + j * kSellC] = j < (int)buf.size() ? buf[j] : p;
       for (int j = 0; j < (int)buf.size(); ++j)
@@ -204,10 +248,11 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   {
     std::vector<int> buf;
 #pragma omp for schedule(static)
-    for (int p = 0; p < n; ++p) {
+    for (int p = 0; p < S.n_pad; ++p) {
+      const int i = S.perm[p];
+      if (i < 0) continue;
       int s = p / kSellC, lane = p % kSellC;
       int base = S.slice_ptr[s] + lane;
-      int i = S.perm[p];
       row_cols(i, buf);
       std::vector<int> next(buf.size(), 0);
       for (int q = inc_ptr[i]; q < inc_ptr[i + 1]; ++q) {
@@ -226,16 +271,20 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   // --- dof gather map for element load vectors ---------------------------------
   S.dof_ptr.assign(S.n_pad + 1, 0);
   for (int p = 0; p < S.n_pad; ++p) {
-    int c = p < n ? inc_ptr[S.perm[p] + 1] - inc_ptr[S.perm[p]] : 0;
+    const int i = S.perm[p];
+    int c = i >= 0 ? inc_ptr[i + 1] - inc_ptr[i] : 0;
     S.dof_ptr[p + 1] = S.dof_ptr[p] + c;
   }
   S.dof_idx.resize(S.dof_ptr[S.n_pad]);
-  for (int p = 0; p < n; ++p) {
-    int i = S.perm[p];
-    std::copy(inc.begin() + inc_ptr[i], inc.begin() + inc_ptr[i + 1], S.dof_idx.begin() + S.dof_ptr[p]);
+  for (int p = 0; p < S.n_pad; ++p) {
+    const int i = S.perm[p];
+    if (i >= 0) std::copy(inc.begin() + inc_ptr[i], inc.begin() + inc_ptr[i + 1], S.dof_idx.begin() + S.dof_ptr[p]);
   }
 
-  // --- structured stencils of M and K (lexicographic internal order only) ------
+  // --- structured stencils of M and K (sigma == 1: lexicographic or line order) ---
+  // Row p's columns are p + offset; in both orders the offsets of an interior row
+  // (all incident elements present) depend only on its dof type t (the lattice
+  // coordinate parities), so every type has one stencil.
   S.ntypes_dof = 1 << dim;
   S.rowinfo.assign(S.n_pad, 0);
   if (S.sigma == 1) {
@@ -261,8 +310,9 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
     for (int t = 0; t < S.ntypes_dof; ++t) {
       const int i = rep[t];
       if (i >= 0) {
-        row_cols(i, buf);  // internal == lexicographic here
-        const int s_ = i / kSellC, lane = i % kSellC, base = S.slice_ptr[s_] + lane;
+        row_cols(i, buf);
+        const int p = S.iperm[i];
+        const int s_ = p / kSellC, lane = p % kSellC, base = S.slice_ptr[s_] + lane;
         for (int j = 0; j < (int)buf.size(); ++j) {
           const int slot = base + j * kSellC;
           double m = 0.0, k = 0.0;
@@ -271,7 +321,7 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
             m += R.mass[(size_t)et * R.npairs + pr];
             k += R.stiff[(size_t)et * R.npairs + pr];
           }
-          S.st_off.push_back(buf[j] - i);
+          S.st_off.push_back(buf[j] - p);
           S.st_wM.push_back(m);
           S.st_wK.push_back(k);
         }
@@ -284,16 +334,18 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
     {
       std::vector<int> rb;
 #pragma omp for schedule(static)
-      for (int i = 0; i < n; ++i) {
+      for (int p = 0; p < S.n_pad; ++p) {
+        const int i = S.perm[p];
+        if (i < 0) continue;
         const int t = dof_type(i);
         bool interior = (inc_ptr[i + 1] - inc_ptr[i]) == maxinc[t];
         if (interior) {
           row_cols(i, rb);
           const int k0 = S.st_start[t], len = S.st_start[t + 1] - k0;
           interior = (int)rb.size() == len;
-          for (int j = 0; interior && j < len; ++j) interior = rb[j] - i == S.st_off[k0 + j];
+          for (int j = 0; interior && j < len; ++j) interior = rb[j] - p == S.st_off[k0 + j];
         }
-        S.rowinfo[i] = (unsigned char)(t | (interior ? 8 : 0));
+        S.rowinfo[p] = (unsigned char)(t | (interior ? 8 : 0));
       }
     }
   }
@@ -317,6 +369,83 @@ size_t footprint_estimate(int dim, int side, int restart, int precision, int deg
   b += n * 8 * 12;                          // inner vectors, diagonals
   if (model == 1) b += nnz * 8 * 2 + E * np * 8 * 2;  // PFC1: A10, A11 and the wider element buffer
   return (size_t)(b * 1.05) + (64u << 20);
+}
+
+}  // namespace pfc
+
+namespace pfc {
+
+// Strip partition of one instance for a row-block solve over several devices (the
+// paper's PETSc/MPI runs partition the rows in contiguous blocks, Section 7).  With
+// lexicographic numbering a contiguous block of rows made of whole lattice lines
+// (2D) or planes (3D) is a strip (slab) of the domain, and a row's columns reach at
+// most `degree` lines (planes) up or down, so a part exchanges ghost values with its
+// two neighbours only, provided every part holds at least `degree` lines.  Parts are
+// cut at line boundaries so that their nonzeros are as equal as the lines allow.
+bool build_partition(int dim, int side, double length, int degree, int nparts, std::vector<int64_t>& begin,
+                     std::vector<int64_t>& halo, std::vector<int64_t>& part_nnz, std::string& err) {
+  HostSetup S;
+  if (!build_setup(dim, side, length, S, err, kSellSigma, degree)) return false;
+  const int64_t lat = S.lat, n = S.n;
+  const int64_t line = dim == 2 ? lat : lat * lat;   // rows per line (2D) / plane (3D)
+  const int64_t nlines = n / line;
+  if (nparts < 1 || (int64_t)nparts * degree > nlines) {
+    err = "every part needs at least `degree` lattice lines: nparts must be in 1.." + std::to_string(nlines / degree);
+    return false;
+  }
+  // per lexicographic row: true nonzeros and the lowest / highest column
+  std::vector<int64_t> rnnz(n, 0), cmin(n, n), cmax(n, -1);
+  for (int p = 0; p < S.n_pad; ++p) {
+    const int i = S.perm[p];
+    if (i < 0) continue;
+    const int s = p / kSellC, lane = p % kSellC, base = S.slice_ptr[s] + lane;
+    const int w = (S.slice_ptr[s + 1] - S.slice_ptr[s]) / kSellC;
+    for (int j = 0; j < w; ++j) {
+      const int slot = base + j * kSellC;
+      if (S.contrib_ptr[slot + 1] == S.contrib_ptr[slot]) continue;   // padding slot
+      const int64_t col = S.perm[S.cols[slot]];
+      rnnz[i] += 1;
+      cmin[i] = std::min(cmin[i], col);
+      cmax[i] = std::max(cmax[i], col);
+    }
+  }
+  std::vector<int64_t> lnnz(nlines + 1, 0);   // prefix sums of nonzeros by line
+  for (int64_t l = 0; l < nlines; ++l) {
+    int64_t t = 0;
+    for (int64_t i = l * line; i < (l + 1) * line; ++i) t += rnnz[i];
+    lnnz[l + 1] = lnnz[l] + t;
+  }
+  // cut points: the line where the nonzero prefix reaches k / nparts of the total,
+  // kept at least `degree` lines apart
+  std::vector<int64_t> cut(nparts + 1, 0);
+  cut[nparts] = nlines;
+  for (int k = 1; k < nparts; ++k) {
+    const int64_t target = lnnz[nlines] * k / nparts;
+    int64_t l = (int64_t)(std::lower_bound(lnnz.begin(), lnnz.end(), target) - lnnz.begin());
+    l = std::max(l, cut[k - 1] + degree);
+    l = std::min(l, nlines - (int64_t)(nparts - k) * degree);
+    cut[k] = l;
+  }
+  begin.assign(nparts + 1, 0);
+  halo.assign(2 * (size_t)nparts, 0);
+  part_nnz.assign(nparts, 0);
+  for (int k = 0; k <= nparts; ++k) begin[k] = cut[k] * line;
+  for (int k = 0; k < nparts; ++k) {
+    int64_t lo = n, hi = -1;
+    for (int64_t i = begin[k]; i < begin[k + 1]; ++i) {
+      lo = std::min(lo, cmin[i]);
+      hi = std::max(hi, cmax[i]);
+    }
+    halo[2 * k] = begin[k] - lo;             // ghost rows below the part
+    halo[2 * k + 1] = hi + 1 - begin[k + 1]; // ghost rows above it
+    part_nnz[k] = lnnz[cut[k + 1]] - lnnz[cut[k]];
+    // ghosts come from the neighbouring parts only
+    if ((k > 0 && lo < begin[k - 1]) || (k + 1 < nparts && hi >= begin[k + 2])) {
+      err = "a part's columns reach past its neighbours";
+      return false;
+    }
+  }
+  return true;
 }
 
 }  // namespace pfc

@@ -34,15 +34,15 @@ struct HostSetup {
   double length = 0.0, h = 0.0;
   int lat = 0;                    // degree * side + 1 lattice points per axis
   int n = 0;                      // dofs per field
-  int n_pad = 0;                  // n rounded up to a multiple of kSellC
+  int n_pad = 0;                  // internal rows (a multiple of kSellC, >= n)
   int nslices = 0;
   int64_t nnz = 0;                // true nonzeros of one block
   int64_t nnz_sell = 0;           // stored slots (with padding)
   int E = 0;                      // elements
   int nl = 0;                     // local nodes per element
   int ntypes = 0;                 // element types per cell (2 or 6)
-  std::vector<int> perm;          // internal row -> lexicographic dof (size n)
-  std::vector<int> iperm;         // lexicographic dof -> internal row
+  std::vector<int> perm;          // internal row -> lexicographic dof (size n_pad; -1: no dof)
+  std::vector<int> iperm;         // lexicographic dof -> internal row (size n)
   std::vector<int> slice_ptr;     // nslices + 1 (slot offsets)
   std::vector<int> cols;          // nnz_sell internal column indices (padding: the row itself)
   std::vector<int> diag_pos;      // n_pad (-1 for padding rows)
@@ -53,7 +53,8 @@ struct HostSetup {
   std::vector<int> dof_idx;       // l * E + e for each element incident to a row
   RefTensors ref;
   // Structured stencils of the constant matrices (only with sigma == 1, where the
-  // internal order is lexicographic): dof type t = lattice-coordinate parities;
+  // internal order is lexicographic (P1) or line by line split by x parity (P2, line_layout)):
+  // dof type t = lattice-coordinate parities;
   // every row whose incident elements all exist ("interior") has the stencil of
   // its type: M_i,i+off[k] = st_wM[k], K_i,i+off[k] = st_wK[k], k in
   // [st_start[t], st_start[t+1]).
@@ -68,6 +69,12 @@ struct HostSetup {
 bool build_reference(int dim, double h, RefTensors& out, std::string& err, int degree = 2);
 bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err, int sigma = kSellSigma,
                  int degree = 2);
+
+// Strip partition of the lexicographic rows over nparts devices (row-block solve):
+// begin (nparts + 1 row offsets), halo (ghost rows below / above each part), the
+// nonzeros of one block held by each part.
+bool build_partition(int dim, int side, double length, int degree, int nparts, std::vector<int64_t>& begin,
+                     std::vector<int64_t>& halo, std::vector<int64_t>& part_nnz, std::string& err);
 
 // Bytes of device memory a context of this size holds (estimate used for admission).
 size_t footprint_estimate(int dim, int side, int restart, int precision, int degree = 2, int model = 2);

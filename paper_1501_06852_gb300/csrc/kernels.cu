@@ -562,7 +562,8 @@ __global__ void k_gather_in(int n, int n_pad, int nf, const int* __restrict__ pe
   const long long tot = (long long)nf * n_pad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
     const int f = (int)(i / n_pad), p = (int)(i - (long long)f * n_pad);
-    internal[i] = p < n ? lex[(size_t)f * n + perm[p]] : 0.0;
+    const int q = perm[p];   // -1: a row that holds no dof
+    internal[i] = q >= 0 ? lex[(size_t)f * n + q] : 0.0;
   }
 }
 
@@ -571,7 +572,8 @@ __global__ void k_scatter_out(int n, int n_pad, int nf, const int* __restrict__ 
   const long long tot = (long long)nf * n_pad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
     const int f = (int)(i / n_pad), p = (int)(i - (long long)f * n_pad);
-    if (p < n) lex[(size_t)f * n + perm[p]] = internal[i];
+    const int q = perm[p];
+    if (q >= 0) lex[(size_t)f * n + q] = internal[i];
   }
 }
 

@@ -6,5 +6,9 @@ def test_candidates_keep_outer_iteration_safe_forms():
     c32 = autotune.candidates("fp32")
     assert all(c["pcg_variant"] in (0, 3) for c in c32)          # no pipelined form in float32
     assert {c["inner_operator"] for c in c32} == {0, 1}
-    assert {c["blocks_per_sm"] for c in c32} == {1, 2}
     assert {c["pcg_variant"] for c in autotune.candidates("fp64")} == {0, 1, 3}
+
+
+def test_size_classes_are_powers_of_two():
+    assert [autotune.size_class(s) for s in (1, 16, 22, 23, 45, 46, 181, 182, 256, 700)] == \
+        [8, 16, 16, 32, 32, 64, 128, 256, 256, 512]
