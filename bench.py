@@ -88,6 +88,9 @@ def parse_args(argv=None):
     p.add_argument("--profile-case", action="store_true",
                    help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
                         "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
+    p.add_argument("--pcg-variant", type=int, choices=[0, 1, 2, 3], default=2,
+                   help="inner CG form (options.pcg_variant): 2 automatic (default), 0 textbook, 1 pipelined, "
+                        "3 Chronopoulos-Gear")
     p.add_argument("--profile-side", type=int, default=0,
                    help="profiler case: mesh side in place of the workload's (same spacing h and parameters)")
     p.add_argument("--profile-restart", type=int, default=30,
@@ -519,7 +522,7 @@ def native(args, world, rank, local, pg):
     def make(precision):
         return pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=args.outer_tol,
                              err_tol=args.err_tol, model=args.model, schur=1 if args.schur == "sd" else 0,
-                             tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD)
+                             tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD, pcg_variant=args.pcg_variant)
 
     out = {}
     hbm = FALLBACK_HBM_GBS
@@ -537,7 +540,7 @@ def native(args, world, rank, local, pg):
     nnz = pfc.host_pattern(w.dim, w.side, w.length)["nnz"]
     inner_nnz = pfc.host_stencil(w.dim, w.side, w.length)["boundary_nnz"]   # stencil inner operators
     # the automatic PCG form of the library: Chronopoulos-Gear for float32/float16 inner solves
-    variant = 1 if args.precision == "fp64" else 3
+    variant = args.pcg_variant if args.pcg_variant != 2 else (1 if args.precision == "fp64" else 3)
     state0 = s.init_state(psi0)
     state = state0.clone()
     tau = w.tau0
@@ -955,7 +958,8 @@ def phases(args):
     psi0 = torch.from_numpy(synth.initial_psi(w.dim, w.side, w.psi_mean, w.amp, w.seed)).cuda()
     res = {"phases": w.name, "tau": 4.0}
     for prec in (args.precision, "fp64"):
-        with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=args.outer_tol) as s:
+        with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=args.outer_tol,
+                           err_tol=args.err_tol, pcg_variant=args.pcg_variant) as s:
             x = s.init_state(psi0)
             s.assemble(x, 4.0)
             b = s.stage_rhs(0, x)

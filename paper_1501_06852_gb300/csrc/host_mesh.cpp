@@ -14,10 +14,9 @@
 // order IS the internal dof order of every device vector, so a SpMV writes y[row]
 // coalesced and a vector update touches 32 consecutive rows per warp.  Without
 // structured stencils rows are sorted by length (descending) inside windows of
-// kSellSigma lexicographic rows; with them (sigma = 1) the P2 rows are numbered
-// line by line with each line split by x parity (line_layout) and P1 rows
-// lexicographically.  Padding rows hold no dof; padding slots point at their own
-// row with value 0.
+// kSellSigma lexicographic rows; with them (sigma = 1) the order is lexicographic.
+// Padding rows at the end hold no dof; padding slots point at their own row with
+// value 0.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -28,44 +27,10 @@
 #include <omp.h>
 #endif
 
-// 1: P2 rows with structured stencils in the line-split order (line_layout); 0: lexicographic
-#ifndef PFC_LINE_LAYOUT
-#define PFC_LINE_LAYOUT 1
-#endif
-
 namespace pfc {
 
 void element_path(int dim, int t, int verts[4][3]);
 void local_edge(int dim, int e, int& a, int& b);
-
-// Row order of the P2 lattice with structured stencils.  Lattice points (a, b, c),
-// 0 <= a, b, c <= 2 side, are numbered line by line (x lines, lexicographic in
-// (b, c)), and inside each line the points with even a (on the vertices' x
-// positions) come first, then those with odd a:
-//     row(a, b, c) = ((c lat + b) lat) + (a even ? a / 2 : side + 1 + a / 2).
-// Every line keeps its lat = 2 side + 1 rows, so a neighbour at a fixed lattice
-// offset from a point of type t (the coordinate parities) is at a fixed row offset
-// again: the interior stencil of a type is one list of row offsets.  In plain
-// lexicographic order consecutive rows of a line alternate between the vertex-x and
-// edge-x types, whose stencils have 19 and 9 entries (2D) or 65 and 19-27 (3D), and a
-// warp's loop runs to the longer one for all 32 lanes; here a warp's 32 rows have
-// one type except near the middle and the ends of a line.  Rows stay in their
-// lattice line, so the stencil reads of a block keep the locality of the
-// lexicographic order (numbering the parity classes one after another instead
-// spread a block's reads over four or eight distant regions and lost more in L1
-// hits than it saved in loop iterations).
-void line_layout(int dim, int side, HostSetup& S) {
-  const int64_t lat = 2 * (int64_t)side + 1, half = side + 1;
-  S.n_pad = (int)((S.n + kSellC - 1) / kSellC * kSellC);
-  S.perm.assign(S.n_pad, -1);
-  for (int64_t i = 0; i < S.n; ++i) {
-    const int64_t a = i % lat, line = i / lat;
-    const int64_t p = line * lat + ((a & 1) ? half + (a >> 1) : (a >> 1));
-    S.perm[p] = (int)i;
-    S.iperm[i] = (int)p;
-  }
-  (void)dim;
-}
 
 bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma, int degree) {
   if (dim != 2 && dim != 3) {
@@ -161,23 +126,18 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   for (int i = 0; i < n; ++i) S.nnz += len[i];
 
   // --- internal row order ------------------------------------------------------
-  // perm: internal row -> lexicographic dof, -1 for rows that hold no dof (padding).
-  // With structured stencils on P2 (sigma == 1) each lattice line is split by the
-  // parity of x (see line_layout); otherwise SELL-32-sigma: rows sorted by length
-  // inside windows of sigma lexicographic rows.  Padding rows at the end.
+  // perm: internal row -> lexicographic dof, -1 for the padding rows at the end.
+  // SELL-32-sigma: rows sorted by length inside windows of sigma lexicographic rows
+  // (sigma = 1 with structured stencils: lexicographic).
   S.iperm.assign(n, -1);
-  if (S.sigma == 1 && degree == 2 && PFC_LINE_LAYOUT) {
-    line_layout(dim, side, S);
-  } else {
-    S.n_pad = (n + kSellC - 1) / kSellC * kSellC;
-    S.perm.assign(S.n_pad, -1);
-    std::iota(S.perm.begin(), S.perm.begin() + n, 0);
-    for (int w0 = 0; w0 < n; w0 += S.sigma) {
-      int w1 = std::min(n, w0 + S.sigma);
-      std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
-    }
-    for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
+  S.n_pad = (n + kSellC - 1) / kSellC * kSellC;
+  S.perm.assign(S.n_pad, -1);
+  std::iota(S.perm.begin(), S.perm.begin() + n, 0);
+  for (int w0 = 0; w0 < n; w0 += S.sigma) {
+    int w1 = std::min(n, w0 + S.sigma);
+    std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
   }
+  for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
   S.nslices = S.n_pad / kSellC;
   S.slice_ptr.assign(S.nslices + 1, 0);
   for (int s = 0; s < S.nslices; ++s) {
@@ -281,10 +241,10 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
     if (i >= 0) std::copy(inc.begin() + inc_ptr[i], inc.begin() + inc_ptr[i + 1], S.dof_idx.begin() + S.dof_ptr[p]);
   }
 
-  // --- structured stencils of M and K (sigma == 1: lexicographic or line order) ---
-  // Row p's columns are p + offset; in both orders the offsets of an interior row
-  // (all incident elements present) depend only on its dof type t (the lattice
-  // coordinate parities), so every type has one stencil.
+  // --- structured stencils of M and K (sigma == 1: lexicographic order) -----------
+  // Row p's columns are p + offset; the offsets of an interior row (all incident
+  // elements present) depend only on its dof type t (the lattice coordinate
+  // parities), so every type has one stencil.
   S.ntypes_dof = 1 << dim;
   S.rowinfo.assign(S.n_pad, 0);
   if (S.sigma == 1) {

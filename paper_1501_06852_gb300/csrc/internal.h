@@ -53,7 +53,7 @@ struct HostSetup {
   std::vector<int> dof_idx;       // l * E + e for each element incident to a row
   RefTensors ref;
   // Structured stencils of the constant matrices (only with sigma == 1, where the
-  // internal order is lexicographic (P1) or line by line split by x parity (P2, line_layout)):
+  // internal order is lexicographic):
   // dof type t = lattice-coordinate parities;
   // every row whose incident elements all exist ("interior") has the stencil of
   // its type: M_i,i+off[k] = st_wM[k], K_i,i+off[k] = st_wK[k], k in

@@ -73,7 +73,8 @@ namespace {
 #ifndef PFC_ST_UNROLL
 #define PFC_ST_UNROLL 4
 #endif
-static_assert(PFC_ST_UNROLL >= 1 && PFC_ST_UNROLL <= 32, "PFC_ST_UNROLL: stencil entries per unrolled round");
+// the stencil tables are padded to a multiple of 4 entries per type
+static_assert(4 % PFC_ST_UNROLL == 0, "PFC_ST_UNROLL must divide 4");
 
 constexpr int kThreads = PFC_SOLVER_THREADS;
 constexpr int kWarps = kThreads / 32;
@@ -545,15 +546,9 @@ __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, in
   Acc acc[kGroup];
 #pragma unroll
   for (int uu = 0; uu < kGroup; ++uu) acc[uu] = Acc(0);
-  // whole rounds of PFC_ST_UNROLL entries, then one predicated round for the rest
-  // (nmax is the same in all lanes): a warp whose rows share one type (the usual
-  // case with the line-split row order) reads exactly its type's entries, in as
-  // many dependent rounds as a padded loop would take
-  const int nmain = nmax - nmax % PFC_ST_UNROLL;
   if (from_win) {
     // the interior rows' reach lies inside the window (see stage_window)
-    int k = 0;
-    for (; k < nmain; k += PFC_ST_UNROLL) {
+    for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
 #pragma unroll
       for (int j = 0; j < PFC_ST_UNROLL; ++j) {
 #pragma unroll
@@ -563,39 +558,14 @@ __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, in
         }
       }
     }
-    if (k < nmax) {
-#pragma unroll
-      for (int j = 0; j < PFC_ST_UNROLL; ++j) {
-        if (k + j < nmax) {
-#pragma unroll
-          for (int uu = 0; uu < kGroup; ++uu) {
-            const StEntry<Acc> e = tab[base[uu] + k + j];
-            acc[uu] = fma(e.w, (Acc)s_win[rowc[uu] - g.win_lo + e.off], acc[uu]);
-          }
-        }
-      }
-    }
   } else {
-    int k = 0;
-    for (; k < nmain; k += PFC_ST_UNROLL) {
+    for (int k = 0; k < nmax; k += PFC_ST_UNROLL) {
 #pragma unroll
       for (int j = 0; j < PFC_ST_UNROLL; ++j) {
 #pragma unroll
         for (int uu = 0; uu < kGroup; ++uu) {
           const StEntry<Acc> e = tab[base[uu] + k + j];
           acc[uu] = fma(e.w, (Acc)x[rowc[uu] + e.off], acc[uu]);
-        }
-      }
-    }
-    if (k < nmax) {
-#pragma unroll
-      for (int j = 0; j < PFC_ST_UNROLL; ++j) {
-        if (k + j < nmax) {
-#pragma unroll
-          for (int uu = 0; uu < kGroup; ++uu) {
-            const StEntry<Acc> e = tab[base[uu] + k + j];
-            acc[uu] = fma(e.w, (Acc)x[rowc[uu] + e.off], acc[uu]);
-          }
         }
       }
     }
