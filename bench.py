@@ -88,6 +88,8 @@ def parse_args(argv=None):
     p.add_argument("--profile-case", action="store_true",
                    help="profiler case: consistent start (2 PCG launches of solve_kernel), then one stage "
                         "solve capped at one FGMRES iteration (the 3rd solve_kernel launch); no timing output")
+    p.add_argument("--smem-window", type=int, choices=[0, 1, 2], default=None,
+                   help="options.smem_window (default: the library's)")
     p.add_argument("--pcg-variant", type=int, choices=[0, 1, 2, 3], default=2,
                    help="inner CG form (options.pcg_variant): 2 automatic (default), 0 textbook, 1 pipelined, "
                         "3 Chronopoulos-Gear")
@@ -101,6 +103,10 @@ def parse_args(argv=None):
                         "the kernel's own clock in block 0 for inner SpMV, inner vector, outer FGMRES and PCG "
                         "set-up phases and the waits at the grid barriers that end them")
     return p.parse_args(argv)
+
+
+def win_kw(args) -> dict:
+    return {} if args.smem_window is None else {"smem_window": args.smem_window}
 
 
 def workload(name: str) -> synth.Workload:
@@ -522,7 +528,8 @@ def native(args, world, rank, local, pg):
     def make(precision):
         return pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=precision, outer_tol=args.outer_tol,
                              err_tol=args.err_tol, model=args.model, schur=1 if args.schur == "sd" else 0,
-                             tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD, pcg_variant=args.pcg_variant)
+                             tau_max=TAU_MAX_UNGUARDED, tau_guard=TAU_GUARD, pcg_variant=args.pcg_variant,
+                             **win_kw(args))
 
     out = {}
     hbm = FALLBACK_HBM_GBS
@@ -959,7 +966,7 @@ def phases(args):
     res = {"phases": w.name, "tau": 4.0}
     for prec in (args.precision, "fp64"):
         with pfc.PFCSolver(w.dim, w.side, w.length, r=w.r, precision=prec, outer_tol=args.outer_tol,
-                           err_tol=args.err_tol, pcg_variant=args.pcg_variant) as s:
+                           err_tol=args.err_tol, pcg_variant=args.pcg_variant, **win_kw(args)) as s:
             x = s.init_state(psi0)
             s.assemble(x, 4.0)
             b = s.stage_rhs(0, x)

@@ -82,12 +82,21 @@ typedef struct {
                          elements all exist has the same entries as every other row of its
                          dof type, so those rows read neither values nor indices (the
                          other rows keep their assembled values) */
-  int smem_window;    /* 1: with structured stencils and float32/float16 inner solves, each
-                         block of the persistent kernel copies the rows of the SpMV source
-                         vector its rows reach (its own rows plus the stencil reach on both
-                         sides) into shared memory once per product, when that window fits
-                         without lowering the grid's residency; 0: stencil reads go to
-                         global memory.  Same results bit for bit either way. */
+  int smem_window;    /* with structured stencils and float32/float16 inner solves, where the
+                         inner SpMV reads its source vector:
+                         0: global memory, each warp gathering for its own slices;
+                         1: each block copies the rows its rows reach (its own rows plus the
+                         stencil reach on both sides) into shared memory once per product,
+                         when that window fits without lowering the grid's residency; same
+                         results bit for bit as 0;
+                         2: each block walks its rows in chunks of 1024, one row per thread,
+                         and the chunk's source window (its lattice lines and two more on
+                         each side; in 3D that band in the five planes around it) is
+                         bulk-copied into one of two shared-memory buffers (cp.async.bulk
+                         completing on an mbarrier) while the previous chunk is computed;
+                         the Chronopoulos-Gear inner solves use it (the per-row sums are
+                         the same, the partial inner products are added in another order).
+                         Chunks that cross a 3D plane boundary read global memory. */
   int model;          /* 2: PFC2, the H^-1 gradient flow of Eq. (2.2) (mobility 1);
                          1: PFC1, the Wasserstein flow of Eq. (2.3) with mobility
                          psi^+ = psi - psi_min: the second block row of the stage

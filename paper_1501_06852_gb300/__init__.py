@@ -233,7 +233,7 @@ class PFCSolver:
                  outer_tol: float = 1e-10, inner_rtol: float = 1e-3, restart: int = 30, max_outer: int = 600,
                  max_inner: int = 1000, step_atol: float = 1e-3, step_rtol: float = 1e-3,
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
-                 inner_operator: int = 1, smem_window: int = 0, model: int = 2, psi_min: float = -1.5,
+                 inner_operator: int = 1, smem_window: int | None = None, model: int = 2, psi_min: float = -1.5,
                  schur: int = 0, schur_its: int = 20, degree: int = 2, err_tol: float = 1e-9,
                  tau_guard: float = 0.0, grid_blocks: int = 0, stream=None):
         import torch
@@ -251,7 +251,8 @@ class PFCSolver:
         o.step_atol, o.step_rtol, o.tau_max, o.blocks_per_sm = step_atol, step_rtol, tau_max, blocks_per_sm
         o.pcg_variant = pcg_variant
         o.inner_operator = inner_operator
-        o.smem_window = smem_window
+        if smem_window is not None:        # else the library's default (pfc_default_options)
+            o.smem_window = smem_window
         o.model = model
         o.psi_min = psi_min
         o.schur = schur

@@ -18,7 +18,7 @@ per-iteration timing does not see; ``pcg_variant`` candidates are therefore
 limited to the forms that keep the outer iteration count (textbook and
 Chronopoulos-Gear in float32/float16; all three in float64).
 Results are cached per process.  ``tuned`` gives the configuration of a size
-class (the mesh side rounded to a power of two at the same spacing), so that a
+class (the mesh side rounded down to a power of two, at the same spacing), so that a
 batch or a server with many sizes tunes a handful of classes, not every size.
 """
 from __future__ import annotations
@@ -36,8 +36,9 @@ def candidates(precision: str):
 
 
 def size_class(side: int) -> int:
-    """The power of two nearest to side (in log scale), between 8 and 512."""
-    return int(min(512, max(8, 2 ** round(math.log2(max(side, 1))))))
+    """The largest power of two not above side, between 8 and 512 (the class is timed on
+    a mesh no larger than any of its members)."""
+    return int(min(512, max(8, 2 ** math.floor(math.log2(max(side, 1))))))
 
 
 def tuned(dim: int, side: int, length: float, precision: str = "fp32", **kw) -> dict:

@@ -73,6 +73,7 @@ struct pfc_ctx {
   int st_types = 0;
   int st_halo = 0;              // largest |stencil offset|
   int win_cap = 0;              // floats of the shared-memory SpMV window (0: off)
+  int tma = 0, tma_lat = 0, tma_plane = 0, tma_S = 0, tma_cap = 0;   // chunked windows (smem_window 2)
   double *mass_tab = nullptr, *stiff_tab = nullptr;
   // float64 matrices
   double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
@@ -214,6 +215,11 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.st_types = c->st_types;
   a.st_halo = c->st_halo;
   a.win_cap = c->win_cap;
+  a.tma = c->tma;
+  a.lat = c->tma_lat;
+  a.plane = c->tma_plane;
+  a.tma_S = c->tma_S;
+  a.tma_cap = c->tma_cap;
   const double cK[4] = {0.0, 1.0, c->delta, std::sqrt(c->delta)};
   const double cM[4] = {1.0, 0.0, 1.0, 1.0};
   for (int k = 0; k < 4; ++k) {
@@ -581,6 +587,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
       c = ck;
       pfc::SolveArgs a = base_args(ck, ck->prec);
       a.win_cap = 0;  // segments of different instances: no shared-memory window
+      a.tma = 0;
       a.mode = 0;
       const int sk = slot_of[wv.first + i];
       a.b = ck->bv;
@@ -723,8 +730,8 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     return bail(fail(c, PFC_ERR_INVALID, "pcg_variant must be 0, 1, 2 or 3"));
   if (c->opt.inner_operator < 0 || c->opt.inner_operator > 1)
     return bail(fail(c, PFC_ERR_INVALID, "inner_operator must be 0 or 1"));
-  if (c->opt.smem_window < 0 || c->opt.smem_window > 1)
-    return bail(fail(c, PFC_ERR_INVALID, "smem_window must be 0 or 1"));
+  if (c->opt.smem_window < 0 || c->opt.smem_window > 2)
+    return bail(fail(c, PFC_ERR_INVALID, "smem_window must be 0, 1 or 2"));
   if ((c->opt.model != 1 && c->opt.model != 2) || !std::isfinite(c->opt.psi_min))
     return bail(fail(c, PFC_ERR_INVALID, "model must be 1 (PFC1) or 2 (PFC2) and psi_min finite"));
   if ((c->opt.schur != 0 && c->opt.schur != 1) || c->opt.schur_its < 1)
@@ -860,6 +867,41 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
         occ_w >= need)
       c->win_cap = winmax;
     cudaGetLastError();
+  }
+
+  // Chunked windows (smem_window 2, float inner vectors): every block walks its rows
+  // in chunks of one row per thread, and the source window of a chunk (its lattice
+  // lines +- 2, in 3D in the five planes around it) is bulk-copied into one of two
+  // shared-memory buffers.  Sizes: a chunk spans at most maxlines lines; 3D plane
+  // segments sit S apart with S = plane (mod 4), so that each copy starts 16-byte
+  // aligned.  Used only if two buffers keep the grid's residency.
+  if (stencil && c->prec != 0 && c->opt.smem_window == 2) {
+    const int chunk = pfc::solve_threads();
+    const long long lat = (long long)c->opt.degree * side + 1;
+    const long long plane = dim == 3 ? lat * lat : 0;
+    if (dim == 2 || plane >= chunk) {
+      const long long maxlines = (chunk - 1) / lat + 2;
+      const long long span = (maxlines + 4) * lat + 8;
+      long long S = 0, cap = 0;
+      if (dim == 2) {
+        cap = (span + 8 + 3) & ~3LL;
+      } else {
+        S = span + 4;
+        while (((S - plane) % 4 + 4) % 4 != 0) ++S;
+        cap = (5 * S + 8 + 3) & ~3LL;
+      }
+      const size_t dyn = 2 * (size_t)cap * sizeof(float);
+      const int need = (c->G + sms - 1) / sms;
+      int occ_t = 0;
+      if (pfc::solve_occupancy(c->prec, &occ_t, dyn) == cudaSuccess && occ_t >= need) {
+        c->tma = 1;
+        c->tma_lat = (int)lat;
+        c->tma_plane = (int)plane;
+        c->tma_S = (int)S;
+        c->tma_cap = (int)cap;
+      }
+      cudaGetLastError();
+    }
   }
 
   // ---- device layout (one allocation) ----

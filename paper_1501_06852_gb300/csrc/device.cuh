@@ -87,6 +87,13 @@ struct SolveArgs {
                            //   the SpMV source vector (float inner vectors only); 0: no window
   double op_cK[4];         // inner operator op = M, K, M + delta K, M + sqrt(delta) K:
   double op_cM[4];         //   weights op_cM[op] * wM + op_cK[op] * wK
+  // chunked stencil SpMV with bulk-copied source windows (float inner vectors, structured
+  // stencils, lexicographic rows; see spmv_chunks in solver.cu)
+  int tma;                 // 1: on
+  int lat;                 // lattice points per axis
+  int plane;               // rows per lattice plane (3D: lat^2); 0 in 2D (one window segment)
+  int tma_S;               // 3D: shared-memory stride between plane segments (S = plane mod 4)
+  int tma_cap;             // floats of one window buffer (two buffers in dynamic shared memory)
 };
 
 // A batched launch: instance k (arguments inst[k], in device memory) owns the

@@ -580,6 +580,198 @@ __device__ __forceinline__ void inner_rows(const Grid& g, const SolveArgs& a, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Chunked stencil SpMV with bulk-copied source windows (float inner vectors).
+//
+// The block walks its rows in chunks of kChunk consecutive rows, one row per thread.
+// Before a chunk is computed, one thread bulk-copies the chunk's source window -
+// every lattice line its interior rows' stencils can reach: the chunk's lines and two
+// more on each side (2D: one contiguous segment; 3D: that band of lines in each of the
+// five planes around the chunk's plane) - from global into shared memory with
+// cp.async.bulk, completing on an mbarrier.  Two buffers alternate, so the copy of
+// chunk k + 2 runs while chunk k + 1 is computed.  The stencil then reads shared
+// memory only: a chunk's 1024 rows share one window, where separate warps each
+// gathered their own lines through L1 (in 3D a warp's 32 rows reach ~25 lines of five
+// planes, and the reuse of those lines by later slices falls outside L1).
+//
+// Window index.  With g0 the first copied element and S the stride between plane
+// segments (S = plane mod 4, so every segment starts 16-byte aligned), element e of
+// plane p sits at  e - g0 - (p - p_lo)(plane - S);  a stencil entry with row offset
+// off = dx + lat dy + plane dz therefore sits at a fixed distance
+// sdelta = off - dz (plane - S) from its row's own index (2D: plane = 0, sdelta = off).
+// Interior rows reach at most two lines (planes) away, inside the window.  A chunk
+// whose rows cross a plane boundary, or whose window would not fit, reads global
+// memory as before.
+constexpr int kChunk = kThreads;
+
+__shared__ __align__(8) unsigned long long s_mbar[2];
+__shared__ int s_sdelta[kMaxStencil];   // window offset of each stencil table entry
+__shared__ int s_sd_lo[9], s_sd_hi[9];  // smallest and largest window offset of each dof type
+__shared__ unsigned s_tma_uses[2];      // copies issued into each buffer (mbarrier phases)
+
+struct ChunkWin {
+  int ok;            // the window is staged (else the chunk reads global memory)
+  int ncopy;
+  int parity;        // mbarrier phase parity of this use of the buffer
+  int p_lo;
+  long long g0;
+  long long src[5];  // first element of each copy (multiple of 4)
+  int cnt[5];        // elements of each copy (multiple of 4)
+  int dst[5];        // first element of each copy in the buffer (multiple of 4)
+};
+__shared__ ChunkWin s_cw[2];
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// global -> shared bulk copy (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Window of the chunk of rows [ra, rb) (see above).  ok = 0 when it cannot be staged.
+__device__ __noinline__ ChunkWin chunk_window(const SolveArgs& a, int ra, int rb) {
+  ChunkWin w{};
+  w.ok = 0;
+  const int lat = a.lat;
+  if (a.plane == 0) {
+    const int ys = max(0, ra / lat - 2), ye = min(lat, (rb - 1) / lat + 3);
+    const long long as = ((long long)ys * lat) & ~3LL;
+    long long ae = ((long long)ye * lat + 3) & ~3LL;
+    if (ae > a.n_pad) ae = a.n_pad;
+    if (ae - as > a.tma_cap || ae <= as) return w;
+    w.ncopy = 1;
+    w.src[0] = as;
+    w.cnt[0] = (int)(ae - as);
+    w.dst[0] = 0;
+    w.g0 = as;
+    w.p_lo = 0;
+    w.ok = 1;
+    return w;
+  }
+  const int plane = a.plane;
+  const int c = ra / plane;
+  if ((rb - 1) / plane != c) return w;
+  const int ys = max(0, (ra - c * plane) / lat - 2), ye = min(lat, (rb - 1 - c * plane) / lat + 3);
+  const int plo = max(0, c - 2), phi = min(lat - 1, c + 2);
+  const long long g0 = ((long long)plo * plane + (long long)ys * lat) & ~3LL;
+  int prev_end = 0;
+  for (int p = plo; p <= phi; ++p) {
+    const long long as = ((long long)p * plane + (long long)ys * lat) & ~3LL;
+    long long ae = ((long long)p * plane + (long long)ye * lat + 3) & ~3LL;
+    if (ae > a.n_pad) ae = a.n_pad;
+    const long long d = as - g0 - (long long)(p - plo) * (plane - a.tma_S);
+    if (d < prev_end || (d & 3) || ae <= as || d + (ae - as) > a.tma_cap) return w;
+    const int k = p - plo;
+    w.src[k] = as;
+    w.cnt[k] = (int)(ae - as);
+    w.dst[k] = (int)d;
+    prev_end = (int)(d + (ae - as));
+  }
+  w.ncopy = phi - plo + 1;
+  w.g0 = g0;
+  w.p_lo = plo;
+  w.ok = 1;
+  return w;
+}
+
+// Thread 0: plans chunk ck of [R0, R1) into buffer b and issues its copies.
+__device__ __noinline__ void issue_chunk(const SolveArgs& a, const float* x, float* buf, int b, int ck, int R0,
+                                         int R1) {
+  const int ra = R0 + ck * kChunk, rb = min(R1, ra + kChunk);
+  ChunkWin w = chunk_window(a, ra, rb);
+  if (w.ok) {
+    unsigned bytes = 0;
+    bool aligned = true;
+    for (int k = 0; k < w.ncopy; ++k) {
+      bytes += (unsigned)w.cnt[k] * 4u;
+      aligned = aligned && ((((unsigned long long)(x + w.src[k])) & 15ull) == 0) &&
+                ((smem_u32(buf + w.dst[k]) & 15u) == 0) && ((w.cnt[k] & 3) == 0);
+    }
+    if (!aligned) w.ok = 0;
+    if (w.ok) {
+      w.parity = (int)(s_tma_uses[b] & 1u);
+      s_tma_uses[b] += 1;
+      mbar_expect_tx(&s_mbar[b], bytes);
+      for (int k = 0; k < w.ncopy; ++k) bulk_g2s(buf + w.dst[k], x + w.src[k], (unsigned)w.cnt[k] * 4u, &s_mbar[b]);
+    }
+  }
+  s_cw[b] = w;
+}
+
+// Bounded wait for buffer b's copies (phase parity).  false: gave up (timeout bit set).
+__device__ bool wait_chunk(Grid& g, int b, int parity) {
+  unsigned spins = 0;
+  unsigned long long t0 = 0;
+  while (!mbar_try_wait(&s_mbar[b], (unsigned)parity)) {
+    if ((++spins & 255u) == 0u) {
+      const unsigned long long t = global_ns();
+      if (t0 == 0) {
+        t0 = t;
+      } else if (t - t0 > g.limit_ns) {
+        atomicOr(g.err, kErrTimeout);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// One row of the chunked SpMV: interior rows from the staged window (or global memory),
+// the others from their assembled SELL row.
+template <class TM>
+__device__ __forceinline__ float chunk_row(const Grid& g, const SolveArgs& a, int op, const TM* __restrict__ vals,
+                                           const float* x, const ChunkWin& w, const float* buf, int row) {
+  const unsigned info = row_info(g, a, row);
+  float acc = 0.f;
+  if (info & 8u) {
+    const int t = info & 7u;
+    const int k0 = s_st_start[t], k1 = k0 + s_st_cnt[t];
+    const StEntry<float>* tab = reinterpret_cast<const StEntry<float>*>(s_st_raw) + op * kMaxStencil;
+    int widx = (int)(row - w.g0);
+    if (a.plane) widx -= (row / a.plane - w.p_lo) * (a.plane - a.tma_S);
+    // the window holds every interior row's reach by construction; a row whose reach
+    // would leave it reads global memory instead
+    if (w.ok && widx + s_sd_lo[t] >= 0 && widx + s_sd_hi[t] < a.tma_cap) {
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) acc = fma(tab[k].w, buf[widx + s_sdelta[k]], acc);
+    } else {
+#pragma unroll 4
+      for (int k = k0; k < k1; ++k) {
+        const StEntry<float> e = tab[k];
+        acc = fma(e.w, x[row + e.off], acc);
+      }
+    }
+  } else {
+    const int sl = row >> 5;
+    acc = sell_row_wide_impl<float>(make_int2(__ldg(a.slice_ptr + sl), __ldg(a.slice_ptr + sl + 1)), a.cols, vals, x,
+                                    row & 31);
+  }
+  return acc;
+}
+
 struct InnerCount {
   long long its = 0;
   int calls = 0;
@@ -1046,12 +1238,77 @@ __device__ __noinline__ bool pcg_pipelined(Grid& g, const SolveArgs& a, const TM
   return true;
 }
 
+// w = A u with the partial sums (r, u) and (w, u), over this block's rows in chunks of
+// kChunk rows whose source windows are bulk-copied into shared memory (see
+// chunk_window).  All threads of the block call it; false if a wait gave up.
+template <class TM>
+__device__ __forceinline__ bool spmv_chunks_cg(Grid& g, const SolveArgs& a, int op, const TM* AV, const float* u,
+                                               const float* r, float* w, float& pg, float& pd) {
+  const int R0 = g.b_lo * 32, R1 = g.b_hi * 32;
+  const int nch = (R1 - R0 + kChunk - 1) / kChunk;
+  if (threadIdx.x == 0) {
+    // u was written through the generic proxy by every block before the last grid
+    // barrier; order those writes before this thread's bulk (async-proxy) reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    for (int ck = 0; ck < 2 && ck < nch; ++ck) issue_chunk(a, u, s_win + ck * a.tma_cap, ck, ck, R0, R1);
+  }
+  __syncthreads();
+  bool ok = true;
+  for (int ck = 0; ck < nch; ++ck) {
+    const int b = ck & 1;
+    const ChunkWin& cw = s_cw[b];
+    if (cw.ok && ok) ok = wait_chunk(g, b, cw.parity);
+    const int row = R0 + ck * kChunk + (int)threadIdx.x;
+    if (ok && row < R1) {
+      const float acc = chunk_row<TM>(g, a, op, AV, u, cw, s_win + b * a.tma_cap, row);
+      w[row] = acc;
+      const float uo = u[row], ro = r[row];
+      pg = fma(ro, uo, pg);
+      pd = fma(acc, uo, pd);
+    }
+    // every thread is done with buffer b (and with s_cw[b]); a wait that gave up stops
+    // the whole block, which issues no further copies
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (threadIdx.x == 0 && ok && ck + 2 < nch) issue_chunk(a, u, s_win + b * a.tma_cap, b, ck + 2, R0, R1);
+  }
+  return ok;
+}
+
+// w = A u and the partial sums (r, u), (w, u) of one Chronopoulos-Gear phase: the
+// chunked path with staged windows (kChunked, float vectors), else each warp over its
+// own slices.
+template <class TM, class TV, bool kChunked>
+__device__ __forceinline__ bool spmv_cg(Grid& g, const SolveArgs& a, int op, const TM* AV, const TV* u, const TV* r,
+                                        TV* w, typename AccOf<TV>::type& pg, typename AccOf<TV>::type& pd) {
+  using Acc = typename AccOf<TV>::type;
+  if constexpr (kChunked && sizeof(TV) == 4) {
+    return spmv_chunks_cg<TM>(g, a, op, AV, u, r, w, pg, pd);
+  }
+  const int lane = threadIdx.x & 31;
+  if (g.staged) stage_window(g, u);
+  FOR_MY_GROUPS(g, s0, nsl) {
+    Acc wa[kGroup];
+    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int row = (s0 + uu) * 32 + lane;
+        const Acc uo = (Acc)u[row], ro = (Acc)r[row];
+        w[row] = (TV)wa[uu];
+        pg = fma(ro, uo, pg);
+        pd = fma(wa[uu], uo, pd);
+      }
+    }
+  }
+  return true;
+}
+
 // Chronopoulos-Gear Jacobi-PCG (Chronopoulos & Gear, J. Comput. Appl. Math. 25,
 // 1989): the same iterates as pcg_standard in exact arithmetic with two phases
 // per iteration.  It carries w = A u (u = D r) and s = A p as recurrences:
 //   phase 1: p = u + b p, s = w + b s, x += a p, r -= a s, u = D r, partial (r, r)
 //   phase 2: w = A u, partials (r, u), (w, u);  b = g'/g, a = g' / (d - b g'/a)
-template <class TM, class TV>
+template <class TM, class TV, bool kChunked>
 __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, int op, const TV* DI, TV* x,
                                     RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   Ctx<TM, TV> c(a);
@@ -1092,21 +1349,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
   const Acc thr = (Acc)(rtol * rtol * bb);
   // w = A u, partials (r, u), (w, u)
   Acc pg = Acc(0), pd = Acc(0);
-  if (g.staged) stage_window(g, u);
-  FOR_MY_GROUPS(g, s0, nsl) {
-    Acc wa[kGroup];
-    inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
-#pragma unroll
-    for (int uu = 0; uu < kGroup; ++uu) {
-      if (uu < nsl) {
-        const int row = (s0 + uu) * 32 + lane;
-        const Acc uo = (Acc)u[row], ro = (Acc)r[row];
-        w[row] = (TV)wa[uu];
-        pg = fma(ro, uo, pg);
-        pd = fma(wa[uu], uo, pd);
-      }
-    }
-  }
+  if (!spmv_cg<TM, TV, kChunked>(g, a, op, AV, u, r, w, pg, pd)) return false;
   if (!grid_sum<Acc, 2>(g, pg, pd, Acc(0), red, kPhSpmv)) return false;
   Acc gam = (Acc)red.x, del = (Acc)red.y;
   if (!(del > Acc(0))) {
@@ -1168,21 +1411,7 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
     // phase 2: w = A u and the two inner products
     pg = Acc(0);
     pd = Acc(0);
-    if (g.staged) stage_window(g, u);
-    FOR_MY_GROUPS(g, s0, nsl) {
-      Acc wa[kGroup];
-      inner_rows<Acc>(g, a, op, AV, u, s0, nsl, lane, wa, g.staged);
-#pragma unroll
-      for (int uu = 0; uu < kGroup; ++uu) {
-        if (uu < nsl) {
-          const int row = (s0 + uu) * 32 + lane;
-          const Acc uo = (Acc)u[row], ro = (Acc)r[row];
-          w[row] = (TV)wa[uu];
-          pg = fma(ro, uo, pg);
-          pd = fma(wa[uu], uo, pd);
-        }
-      }
-    }
+    if (!spmv_cg<TM, TV, kChunked>(g, a, op, AV, u, r, w, pg, pd)) return false;
     if (!grid_sum<Acc>(g, pg, pd, g.nbsync ? prr : Acc(0), red, kPhSpmv)) return false;
     if (g.nbsync) {
       its = it;
@@ -1215,7 +1444,12 @@ template <class TM, class TV>
 __device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, int op, const TV* DI, TV* x,
                                     RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
-  if (c.a.pcg_variant == 3) return pcg_cg<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
+  if (c.a.pcg_variant == 3) {
+    if constexpr (sizeof(TV) == 4) {
+      if (c.a.tma) return pcg_cg<TM, TV, true>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
+    }
+    return pcg_cg<TM, TV, false>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
+  }
   return pcg_standard<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
 }
 
@@ -1677,6 +1911,16 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
         wm = __ldg(a.st_wM + src);
         wk = __ldg(a.st_wK + src);
       }
+      if (a.tma) {
+        // staged window offset of the entry: off - dz (plane - S), dz its plane offset
+        int sd = off;
+        if (a.plane) {
+          const int half = a.plane / 2;
+          const int dz = off >= 0 ? (off + half) / a.plane : -((-off + half) / a.plane);
+          sd = off - dz * (a.plane - a.tma_S);
+        }
+        s_sdelta[k] = sd;
+      }
 #pragma unroll
       for (int op = 0; op < 4; ++op) {
         StEntry<Acc> e{};
@@ -1689,6 +1933,25 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
       const int t = threadIdx.x;
       s_st_start[t] = t * L;
       s_st_cnt[t] = t < a.st_types ? __ldg(a.st_start + t + 1) - __ldg(a.st_start + t) : 0;
+    }
+    if (a.tma) {
+      __syncthreads();   // s_sdelta complete
+      if ((int)threadIdx.x < a.st_types) {
+        const int t = threadIdx.x;
+        int lo = 0, hi = 0;
+        for (int k = t * L; k < t * L + (__ldg(a.st_start + t + 1) - __ldg(a.st_start + t)); ++k) {
+          lo = min(lo, s_sdelta[k]);
+          hi = max(hi, s_sdelta[k]);
+        }
+        s_sd_lo[t] = lo;
+        s_sd_hi[t] = hi;
+      }
+    }
+    if (a.tma && threadIdx.x == 0) {
+      mbar_init(&s_mbar[0], 1);
+      mbar_init(&s_mbar[1], 1);
+      s_tma_uses[0] = s_tma_uses[1] = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // this block's row-info bytes, 16 at a time (the row ranges start at multiples of 32)
     const int nrow = (g.b_hi - g.b_lo) * 32;
@@ -1777,7 +2040,8 @@ cudaError_t solve_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem) {
 cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t stream) {
   SolveArgs local = args;
   void* params[] = {&local};
-  const size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
+  size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
+  if (prec != 0 && args.tma) dyn = 2 * (size_t)args.tma_cap * sizeof(float);
   cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, dyn, stream);

@@ -10,5 +10,5 @@ def test_candidates_keep_outer_iteration_safe_forms():
 
 
 def test_size_classes_are_powers_of_two():
-    assert [autotune.size_class(s) for s in (1, 16, 22, 23, 45, 46, 181, 182, 256, 700)] == \
-        [8, 16, 16, 32, 32, 64, 128, 256, 256, 512]
+    assert [autotune.size_class(s) for s in (1, 16, 22, 31, 32, 48, 63, 255, 256, 700)] == \
+        [8, 16, 16, 16, 32, 32, 32, 128, 256, 512]
