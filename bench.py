@@ -362,8 +362,12 @@ def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, v
                            S + 19 n sv (pipelined: SpMV; 9 recurrences read and written, D)
                            S + 15 n sv (Chronopoulos-Gear: u, p, w, s, x, r, D read and p, s, x,
                                         r, u written; SpMV gathers u, reads r, writes w)
-      PCG set-up (x5 per P_CH): 4 n sv (textbook), S + 14 n sv (pipelined, incl. w = A u) or
+                           11 n sv (Chronopoulos-Gear on the cell kernels, variant 4: p, w, s, r,
+                                        D, x read and p, s, r, x, w written; u stays in shared
+                                        memory, every row's stencil too)
+      PCG set-up (x5 per P_CH): 4 n sv (textbook), S + 14 n sv (pipelined, incl. w = A u),
                            S + 9 n sv (Chronopoulos-Gear: x, r, u, s, p written, D read, w = A u)
+                           or 7 n sv (cell kernels: x, r, s, p written, r, D read, w written)
       P_CH application:    4 (S + n sv) right-hand-side SpMVs + 24 n (v reads) + 4 n sv + 24 n (steps 4, 5)
       outer iteration j:   28 N + 192 n + 96 j n  (A^R SpMV with 3 value streams, MGS, scaling)
       restart cycle:       28 N + 96 n + 24 n (k + 2) (true residual, basis scaling, y update)
@@ -372,6 +376,8 @@ def stage_solve_bytes(st, n: int, nnz: int, precision: str, restart: int = 30, v
     S = (nnz if inner_nnz is None else inner_nnz) * (sM + 4)
     it = S + {1: 19, 3: 15}.get(variant, 13) * n * sv
     setup = {1: S + 14 * n * sv, 3: S + 9 * n * sv}.get(variant, 4 * n * sv)
+    if variant == 4:
+        it, setup = 11 * n * sv, 7 * n * sv
     b = st.inner_its * it
     b += st.outer_its * (4 * (S + n * sv) + 24 * n + 4 * n * sv + 24 * n + 5 * setup)
     left = st.outer_its
@@ -548,6 +554,8 @@ def native(args, world, rank, local, pg):
     inner_nnz = pfc.host_stencil(w.dim, w.side, w.length)["boundary_nnz"]   # stencil inner operators
     # the automatic PCG form of the library: Chronopoulos-Gear for float32/float16 inner solves
     variant = args.pcg_variant if args.pcg_variant != 2 else (1 if args.precision == "fp64" else 3)
+    if s.cell_kernels:
+        variant = 4
     state0 = s.init_state(psi0)
     state = state0.clone()
     tau = w.tau0
@@ -595,9 +603,14 @@ def native(args, world, rank, local, pg):
             "workload": f"{w.name}: {w.dim}D [0,{w.length:g}]^{w.dim}, side {w.side}, P2, {n} dofs/field, "
                         f"{3 * n} unknowns, r={w.r}, psi={w.psi_mean}+{w.amp}U(-1,1) seed {w.seed}, "
                         f"tau0={w.tau0}, adaptive Ros3Pw (Lemma-3 guard tau<={cap:.3g})",
-            "precision": f"{args.precision} inner Jacobi-PCG (Chronopoulos-Gear form), fp64 outer FGMRES(30)/Arnoldi/step control",
+            "precision": f"{args.precision} inner Jacobi-PCG (Chronopoulos-Gear form"
+                         + (", cell kernels: one grid barrier per iteration" if variant == 4 else "")
+                         + "), fp64 outer FGMRES(30)/Arnoldi/step control",
             "model": "PFC2 (H^-1 flow)" if args.model == 2 else "PFC1 (mobility psi + 1.5)",
-            "inner_operator": "structured stencils for M, K, M+dK, M+sqrt(d)K (boundary rows assembled SELL-32)",
+            "inner_operator": "structured stencils for M, K, M+dK, M+sqrt(d)K ("
+                              + ("2x2-cell rows; rows off the interior stencil use their class stencil from "
+                                 "shared memory in the inner solves" if variant == 4 else
+                                 "boundary rows assembled SELL-32") + ")",
             "outer_tol": args.outer_tol, "inner_rtol": 1e-3,
             "l2": "inputs larger than L2: matrices + Krylov bases ~3 GB per instance vs 129 MB L2",
             "parallelism": f"{world} independent replica(s), one per GPU",

@@ -142,6 +142,16 @@ typedef struct {
                          order, hence its results bit for bit, do not depend on what else
                          is in a batch (serving); 0 (default): alone it takes every
                          co-resident block, in a batch a share proportional to its rows */
+  int cells;          /* 2D P2 with structured stencils (inner_operator 1): 1 (default)
+                         numbers the rows by 2 x 2 lattice cells (the four dofs of a cell
+                         are consecutive rows, so a vector moves a cell per 16-byte
+                         access), and the float32/float16 Chronopoulos-Gear inner solves
+                         run one grid barrier per iteration: every block keeps u on its
+                         cells and on the cells its stencils reach in shared memory,
+                         recomputing the halo from its neighbours' r, s, w rather than
+                         waiting for them (same iterates in exact arithmetic); 0: the
+                         lexicographic order.  Ignored elsewhere (3D, P1, assembled
+                         inner matrices). */
 } pfc_options;
 
 typedef struct {
@@ -165,7 +175,7 @@ typedef struct {
  * restart = 30, max_outer = 600, max_inner = 1000, precision = FP64,
  * step_atol = step_rtol = 1e-3, tau_max = 1e9, blocks_per_sm = 0, pcg_variant = 2, inner_operator = 1,
  * smem_window = 0, model = 2, psi_min = -1.5, schur = 0, schur_its = 20, degree = 2,
- * err_tol = 1e-9, tau_guard = 0, grid_blocks = 0. */
+ * err_tol = 1e-9, tau_guard = 0, grid_blocks = 0, cells = 1. */
 void pfc_default_options(pfc_options* opt);
 
 /* Critical time-step width of Lemma 3 (Section 6): the symbol of the PFC2 operator
@@ -351,6 +361,22 @@ pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
  * exercised by a multi-process CPU test of the partitioned solve. */
 pfc_status pfc_host_partition(int dim, int side, double length, int degree, int nparts, int64_t* row_begin,
                               int64_t* halo, int64_t* part_nnz);
+
+/* Host-only inspection of the 2D P2 cell-major order (no GPU needed; options.cells):
+ * out4 = {row classes (distinct row stencils; the first four are the interior
+ * stencils of the dof types, the fifth is the empty stencil of padding rows),
+ * stencil entries over all row classes, cell classes (distinct tuples of a 2 x 2
+ * cell's four row classes) if the interior stencils extracted from the assembled
+ * pattern are the couplings the cell kernels hard-code (cell2d.h) and every other
+ * row couples to a subset of them, else 0 (the cell kernels then stay off), rows that
+ * hold a dof}.  The stencils are those of the P2 matrices of Section 3 on this
+ * structured mesh. */
+pfc_status pfc_host_cells(int side, double length, int64_t* out4);
+
+/* 1 if the context's float32/float16 inner solves run the cell kernels
+ * (options.cells with 2D P2 structured stencils, the Chronopoulos-Gear form and room
+ * in shared memory), else 0 (also for NULL or float64 contexts).  Host only. */
+int pfc_cell_kernels(const pfc_ctx* ctx);
 
 /* Host-only inspection of the structured stencils (no GPU needed):
  * out3 = {rows that use the stencil, nonzeros of the rows that keep their

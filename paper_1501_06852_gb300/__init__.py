@@ -44,7 +44,8 @@ class _Options(ctypes.Structure):
                 ("degree", ctypes.c_int),
                 ("err_tol", ctypes.c_double),
                 ("tau_guard", ctypes.c_double),
-                ("grid_blocks", ctypes.c_int)]
+                ("grid_blocks", ctypes.c_int),
+                ("cells", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -77,6 +78,8 @@ def _load():
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_host_cells": (I, [I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_cell_kernels": (I, [P]),
         "pfc_host_partition": (I, [I, I, D, I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64)]),
         "pfc_batch_stage_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P),
@@ -222,6 +225,16 @@ def host_stencil(dim: int, side: int, length: float = 1.0) -> dict:
     return {"interior_rows": out[0], "boundary_nnz": out[1], "stencil_entries": out[2]}
 
 
+def host_cells(side: int, length: float = 1.0) -> dict:
+    """Row classes of the 2D P2 cell-major order from the host builder (no GPU needed)."""
+    out = (ctypes.c_int64 * 4)()
+    st = lib.pfc_host_cells(side, float(length), out)
+    if st != 0:
+        raise PFCError(st, "host_cells")
+    return {"classes": out[0], "entries": out[1], "pattern_ok": out[2] > 0, "cell_classes": out[2],
+            "rows": out[3]}
+
+
 class PFCSolver:
     """One PFC simulation instance on the current CUDA device.
 
@@ -235,7 +248,7 @@ class PFCSolver:
                  tau_max: float = 1e9, blocks_per_sm: int = 0, pcg_variant: int = 2,
                  inner_operator: int = 1, smem_window: int | None = None, model: int = 2, psi_min: float = -1.5,
                  schur: int = 0, schur_its: int = 20, degree: int = 2, err_tol: float = 1e-9,
-                 tau_guard: float = 0.0, grid_blocks: int = 0, stream=None):
+                 tau_guard: float = 0.0, grid_blocks: int = 0, cells: int | None = None, stream=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -261,6 +274,8 @@ class PFCSolver:
         o.err_tol = err_tol
         o.tau_guard = tau_guard
         o.grid_blocks = grid_blocks
+        if cells is not None:              # else the library's default (pfc_default_options)
+            o.cells = cells
         self.options = o
         self.dim, self.side, self.length, self.r, self.precision = dim, side, float(length), r, precision
         h = ctypes.c_void_p()
@@ -374,6 +389,11 @@ class PFCSolver:
 
     def set_timing(self, enable: bool = True):
         self._check(lib.pfc_set_timing(self._h, 1 if enable else 0))
+
+    @property
+    def cell_kernels(self) -> bool:
+        """Whether this context's float32/float16 inner solves run the cell kernels."""
+        return bool(lib.pfc_cell_kernels(self._h))
 
     def counters(self) -> dict:
         """Kernels launched by this context, persistent-solver launches and their summed event time."""

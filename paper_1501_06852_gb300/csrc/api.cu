@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -74,6 +75,15 @@ struct pfc_ctx {
   int st_halo = 0;              // largest |stencil offset|
   int win_cap = 0;              // floats of the shared-memory SpMV window (0: off)
   int tma = 0, tma_lat = 0, tma_plane = 0, tma_S = 0, tma_cap = 0;   // chunked windows (smem_window 2)
+  // cell kernels (2D P2 cell-major rows, float inner vectors): row classes and windows
+  int cells = 0;                // rows in cell-major order
+  int cell_ok = 0;              // the cell kernels run the Chronopoulos-Gear inner solves
+  int cell_S = 0;
+  int ccls_n = 0;               // cell classes
+  double *ccls_wM = nullptr, *ccls_wK = nullptr;
+  unsigned char* cellclass = nullptr;
+  int cell_rep[4] = {};         // an interior row of each dof type
+  int cell_wcap = 0, cell_rows_cap = 0;   // window and rows of the widest block (own grid)
   double *mass_tab = nullptr, *stiff_tab = nullptr;
   // float64 matrices
   double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
@@ -226,8 +236,122 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
     a.op_cK[k] = cK[k];
     a.op_cM[k] = cM[k];
   }
+  a.cells = (prec != 0 && c->cell_ok) ? 1 : 0;
+  a.cell_S = c->cell_S;
+  a.cell_wcap = c->cell_wcap;
+  a.cell_rows_cap = c->cell_rows_cap;
+  a.ccls_n = c->ccls_n;
+  a.ccls_wM = c->ccls_wM;
+  a.ccls_wK = c->ccls_wK;
+  a.cellclass = c->cellclass;
+  for (int t = 0; t < 4; ++t) a.cell_rep[t] = c->cell_rep[t];
   a.prof = c->timing ? 1 : 0;
   return a;
+}
+
+// Tables of the cell kernels built on the host from the row classes.
+struct CellTables {
+  int ncc = 0;                          // cell classes (class 0: four interior rows)
+  std::vector<unsigned char> cellclass; // n_pad / 4
+  std::vector<double> wM, wK;           // ncc x kCell2dEntries
+  int rep[4] = {-1, -1, -1, -1};        // an interior row of each dof type
+};
+
+// Whether the cell kernels may run on this cell-major setup, and their tables: the
+// interior stencil of each dof type must be exactly its couplings in cell2d.h, and
+// every other row's stencil a subset of the couplings of its type (true for the rows
+// on the sides of a structured mesh, whose elements are a subset of an interior
+// row's).  A cell's class is the tuple of its four rows' classes; its weights are
+// those of cell2d.h's couplings, 0 where a row lacks one.  At most 255 classes.
+bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
+  const int nt = S.ntypes_dof;
+  const int ncls = (int)S.cls_start.size() - 1;
+  if (!S.cells || nt != 4 || ncls > 255) return false;
+  struct Ent {
+    int t, q, sub;
+  };
+  static const Ent tab[pfc::kCell2dEntries] = {
+#define PFC_CELL_ENT(t, q, sub) {t, q, sub},
+      PFC_CELL2D_ENTRIES(PFC_CELL_ENT)
+#undef PFC_CELL_ENT
+  };
+  static const int dxq[pfc::kCell2dSrc] = PFC_CELL2D_DX, dyq[pfc::kCell2dSrc] = PFC_CELL2D_DY;
+  int off[pfc::kCell2dEntries];
+  for (int e = 0; e < pfc::kCell2dEntries; ++e)
+    off[e] = 4 * (dyq[tab[e].q] * S.cell_S + dxq[tab[e].q]) + tab[e].sub - tab[e].t;
+  // the interior stencils have exactly the couplings of their type
+  for (int t = 0; t < nt; ++t) {
+    int count = 0;
+    for (int e = 0; e < pfc::kCell2dEntries; ++e) {
+      if (tab[e].t != t) continue;
+      ++count;
+      bool found = false;
+      for (int j = S.cls_start[t]; j < S.cls_start[t + 1]; ++j) found = found || S.cls_off[j] == off[e];
+      if (!found) return false;
+    }
+    if (count != S.cls_start[t + 1] - S.cls_start[t]) return false;
+  }
+  CellTables T;
+  std::map<uint32_t, int> ids;
+  auto add_class = [&](uint32_t key) -> bool {
+    for (int t = 0; t < 4; ++t) {
+      const int k = (key >> (8 * t)) & 255u;
+      int used = 0;
+      for (int e = 0; e < pfc::kCell2dEntries; ++e) {
+        if (tab[e].t != t) continue;
+        for (int j = S.cls_start[k]; j < S.cls_start[k + 1]; ++j)
+          if (S.cls_off[j] == off[e]) ++used;
+      }
+      if (used != S.cls_start[k + 1] - S.cls_start[k]) return false;   // a coupling outside the pattern
+    }
+    for (int e = 0; e < pfc::kCell2dEntries; ++e) {
+      const int k = (key >> (8 * tab[e].t)) & 255u;
+      double m = 0.0, kk = 0.0;
+      for (int j = S.cls_start[k]; j < S.cls_start[k + 1]; ++j)
+        if (S.cls_off[j] == off[e]) {
+          m = S.cls_wM[j];
+          kk = S.cls_wK[j];
+        }
+      T.wM.push_back(m);
+      T.wK.push_back(kk);
+    }
+    const int id = (int)ids.size();
+    ids.emplace(key, id);
+    return true;
+  };
+  if (!add_class(0x03020100u)) return false;
+  const int ncell = S.n_pad / 4;
+  T.cellclass.resize(ncell);
+  for (int c = 0; c < ncell; ++c) {
+    const uint32_t key = (uint32_t)S.rowclass[4 * c] | ((uint32_t)S.rowclass[4 * c + 1] << 8) |
+                         ((uint32_t)S.rowclass[4 * c + 2] << 16) | ((uint32_t)S.rowclass[4 * c + 3] << 24);
+    auto it = ids.find(key);
+    if (it == ids.end()) {
+      if (ids.size() >= 255 || !add_class(key)) return false;
+      it = ids.find(key);
+    }
+    T.cellclass[c] = (unsigned char)it->second;
+    if (it->second == 0 && T.rep[0] < 0)
+      for (int t = 0; t < 4; ++t) T.rep[t] = 4 * c + t;
+  }
+  if (T.rep[0] < 0) return false;   // no interior cell
+  T.ncc = (int)ids.size();
+  if (out) *out = std::move(T);
+  return true;
+}
+
+// Window (cells) and rows of the widest block of the partition blk (G blocks, one
+// warp range each): block b owns cells [8 blk[b W], 8 blk[(b+1) W]) and keeps cell_S + 1
+// more on each side.
+void cell_caps(const pfc_ctx* c, const int* blk, int G, int& wcap, int& rows_cap) {
+  const int W = pfc::solve_threads() / 32;
+  wcap = 0;
+  rows_cap = 0;
+  for (int b = 0; b < G; ++b) {
+    const int s0 = blk[(size_t)b * W], s1 = blk[(size_t)(b + 1) * W];
+    wcap = std::max(wcap, 8 * (s1 - s0) + 2 * (c->cell_S + 1));
+    rows_cap = std::max(rows_cap, 32 * (s1 - s0));
+  }
 }
 
 pfc_status status_from_err(int err) {
@@ -560,7 +684,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
   pfc_ctx* c0 = ctxs[0];      // stream, device and precision are shared by all
   pfc_ctx* c = ctxs_in[0];    // errors are reported on the caller's first context
   int occ = 0;
-  CK(pfc::batch_occupancy(c0->prec, &occ));
+  CK(pfc::batch_occupancy(c0->prec, &occ, 0));
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
   int bps = occ;
@@ -582,6 +706,28 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
     pfc::SolveArgs* hargs = (pfc::SolveArgs*)(hbase + off);
     int* hseg = (int*)(hbase + off + sizeof(pfc::SolveArgs) * n);
     hseg[0] = 0;
+    // cell kernels: the wave's dynamic shared memory holds the widest block window of
+    // every instance in its segment partition; if that lowers the residency the wave
+    // needs, the wave's instances take the global-memory form instead
+    size_t dyn = 0;
+    bool cells_fit = true;
+    {
+      for (int i = 0; i < n; ++i) {
+        pfc_ctx* ck = ctxs[wv.first + i];
+        if (!(ck->prec != 0 && ck->cell_ok)) continue;
+        int wcap = 0, rcap = 0;
+        cell_caps(ck, ck->h_blk_b, Gs[wv.first + i], wcap, rcap);
+        dyn = std::max(dyn, pfc::cell_smem_bytes(wcap, ck->ccls_n, rcap));
+      }
+      if (dyn > 0) {
+        int occ_c = 0, blocks = 0;
+        for (int i = 0; i < n; ++i) blocks += Gs[wv.first + i];
+        const int need = (blocks + sms - 1) / sms;
+        cells_fit = pfc::batch_occupancy(c0->prec, &occ_c, dyn) == cudaSuccess && occ_c >= need;
+        cudaGetLastError();
+        if (!cells_fit) dyn = 0;
+      }
+    }
     for (int i = 0; i < n; ++i) {
       pfc_ctx* ck = ctxs[wv.first + i];
       c = ck;
@@ -593,6 +739,10 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
       a.b = ck->bv;
       a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)sk * 3 * ck->n_pad;
       a.blk = ck->blk_b;
+      if (a.cells) {
+        if (cells_fit) cell_caps(ck, ck->h_blk_b, Gs[wv.first + i], a.cell_wcap, a.cell_rows_cap);
+        else a.cells = 0;
+      }
       a.stats = ck->stats + sk;
       a.err = ck->errw + sk;
       hargs[i] = a;
@@ -608,7 +758,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
     ba.inst = (const pfc::SolveArgs*)(dbase + off);
     ba.seg = (const int*)(dbase + off + sizeof(pfc::SolveArgs) * n);
     ba.count = n;
-    CK(pfc::launch_solve_batch(c0->prec, hseg[n], ba, c0->stream));
+    CK(pfc::launch_solve_batch(c0->prec, hseg[n], ba, c0->stream, dyn));
     c0->launches += 1;
     c0->solver_launches += 1;
     off += (bytes + 255) & ~size_t(255);
@@ -664,6 +814,7 @@ void pfc_default_options(pfc_options* o) {
   o->err_tol = 1e-9;
   o->tau_guard = 0.0;
   o->grid_blocks = 0;
+  o->cells = 1;
 }
 
 double pfc_critical_tau(double r, double psi_bar) { return critical_tau(r, psi_bar); }
@@ -742,6 +893,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   if (!(c->opt.tau_guard >= 0.0) || !(c->opt.tau_guard < 1.0))
     return bail(fail(c, PFC_ERR_INVALID, "tau_guard must be in [0, 1)"));
   if (c->opt.grid_blocks < 0) return bail(fail(c, PFC_ERR_INVALID, "grid_blocks must be >= 0"));
+  if (c->opt.cells != 0 && c->opt.cells != 1) return bail(fail(c, PFC_ERR_INVALID, "cells must be 0 or 1"));
   c->model = c->opt.model;
   c->psi_min = c->opt.psi_min;
   if (!(c->opt.outer_tol > 0.0) || !(c->opt.inner_rtol > 0.0) || c->opt.max_outer < 1 || c->opt.max_inner < 1)
@@ -759,7 +911,15 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   pfc::HostSetup S;
   std::string err;
   const bool stencil = c->opt.inner_operator == 1;
-  if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma, c->opt.degree))
+  // Cell-major rows only where the cell kernels can run them (2D P2 structured
+  // stencils, float32/float16 Chronopoulos-Gear inner solves, no staged window);
+  // elsewhere, or when the checks below turn the kernels down, lexicographic rows
+  // (the per-warp gathers of the other paths are faster in that order).
+  bool try_cells = stencil && c->opt.cells && dim == 2 && c->opt.degree == 2 && c->prec != 0 &&
+                   c->opt.smem_window == 0 && (c->opt.pcg_variant == 2 || c->opt.pcg_variant == 3);
+retry_layout:
+  if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma, c->opt.degree,
+                        try_cells ? 1 : 0))
     return bail(fail(c, PFC_ERR_INVALID, err));
   if (stencil) {
     // the kernel pads every type to the longest stencil (rounded up to 4) and adds
@@ -822,6 +982,9 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
         for (int l = 0; l < 32; ++l)
           if (!(S.rowinfo[(size_t)s * 32 + l] & 8)) ++nb;
         cost += kBoundaryExtra * nb * width;
+        // cell kernels: every cell costs the same (its vector traffic and the couplings
+        // of cell2d.h, with its class's weights)
+        if (S.cells && c->prec != 0) cost = 64;
       }
       pre[s + 1] = pre[s] + cost;
     }
@@ -844,6 +1007,36 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
       for (int w = 0; w < W; ++w) blk[(size_t)b * W + w] = wb[w];
     }
     blk[(size_t)c->G * W] = S.nslices;
+  }
+
+  // Cell kernels (2D P2 rows in cell-major order): they run the Chronopoulos-Gear inner
+  // solves of float32/float16 contexts without a staged window, once the host has
+  // checked that the interior stencils it extracted are the couplings of cell2d.h,
+  // that every other row's stencil stays inside the block window (one lattice line of
+  // cells and one cell on each side), and that the window and tables of the widest
+  // block fit in shared memory at the grid's residency.
+  CellTables ct;
+  if (S.cells) {
+    c->cells = 1;
+    c->cell_S = S.cell_S;
+    bool ok = c->prec != 0 && c->opt.smem_window == 0 && (c->opt.pcg_variant == 2 || c->opt.pcg_variant == 3) &&
+              cell_pattern_ok(S, &ct);
+    if (ok) {
+      c->ccls_n = ct.ncc;
+      for (int t = 0; t < 4; ++t) c->cell_rep[t] = ct.rep[t];
+      cell_caps(c, blk.data(), c->G, c->cell_wcap, c->cell_rows_cap);
+      const size_t dyn = pfc::cell_smem_bytes(c->cell_wcap, c->ccls_n, c->cell_rows_cap);
+      const int need = (c->G + sms - 1) / sms;
+      int occ_c = 0;
+      ok = pfc::solve_occupancy(c->prec, &occ_c, dyn) == cudaSuccess && occ_c >= need;
+      cudaGetLastError();
+    }
+    c->cell_ok = ok ? 1 : 0;
+  }
+  if (S.cells && !c->cell_ok) {
+    try_cells = false;
+    c->cells = c->cell_S = c->ccls_n = 0;
+    goto retry_layout;
   }
 
   // Shared-memory window of the stencil SpMV (float inner vectors): block b reads
@@ -875,7 +1068,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   // shared-memory buffers.  Sizes: a chunk spans at most maxlines lines; 3D plane
   // segments sit S apart with S = plane (mod 4), so that each copy starts 16-byte
   // aligned.  Used only if two buffers keep the grid's residency.
-  if (stencil && c->prec != 0 && c->opt.smem_window == 2) {
+  if (stencil && c->prec != 0 && c->opt.smem_window == 2 && !S.cells) {   // lexicographic lines only
     const int chunk = pfc::solve_threads();
     const long long lat = (long long)c->opt.degree * side + 1;
     const long long plane = dim == 3 ? lat * lat : 0;
@@ -924,6 +1117,9 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   const size_t o_sto = L.take(sizeof(int) * std::max<size_t>(1, S.st_off.size()));
   const size_t o_stm = L.take(sizeof(double) * std::max<size_t>(1, S.st_wM.size()));
   const size_t o_stk = L.take(sizeof(double) * std::max<size_t>(1, S.st_wK.size()));
+  const size_t o_cm = L.take(sizeof(double) * std::max<size_t>(1, ct.wM.size()));
+  const size_t o_ck = L.take(sizeof(double) * std::max<size_t>(1, ct.wK.size()));
+  const size_t o_cc = L.take(std::max<size_t>(1, ct.cellclass.size()));
   const size_t o_mt = L.take(sizeof(double) * S.ref.mass.size());
   const size_t o_st = L.take(sizeof(double) * S.ref.stiff.size());
   const size_t vals = sizeof(double) * S.nnz_sell;
@@ -996,6 +1192,9 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   c->st_wM = (double*)(A + o_stm);
   c->st_wK = (double*)(A + o_stk);
   c->st_types = stencil ? S.ntypes_dof : 0;
+  c->ccls_wM = (double*)(A + o_cm);
+  c->ccls_wK = (double*)(A + o_ck);
+  c->cellclass = (unsigned char*)(A + o_cc);
   c->mass_tab = (double*)(A + o_mt);
   c->stiff_tab = (double*)(A + o_st);
   c->Mv = (double*)(A + o_M);
@@ -1080,6 +1279,11 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
     UP(c->st_off, S.st_off);
     UP(c->st_wM, S.st_wM);
     UP(c->st_wK, S.st_wK);
+  }
+  if (c->cell_ok) {
+    UP(c->ccls_wM, ct.wM);
+    UP(c->ccls_wK, ct.wK);
+    UP(c->cellclass, ct.cellclass);
   }
   UP(c->mass_tab, S.ref.mass);
   UP(c->stiff_tab, S.ref.stiff);
@@ -1608,6 +1812,24 @@ pfc_status pfc_host_partition(int dim, int side, double length, int degree, int 
   std::copy(z.begin(), z.end(), part_nnz);
   return PFC_OK;
 }
+
+pfc_status pfc_host_cells(int side, double length, int64_t* out4) {
+  if (!out4) return PFC_ERR_INVALID;
+  pfc::HostSetup S;
+  std::string err;
+  if (!pfc::build_setup(2, side, length, S, err, 1, 2, 1)) return PFC_ERR_INVALID;
+  CellTables T;
+  out4[0] = (int64_t)S.cls_start.size() - 1;
+  out4[1] = (int64_t)S.cls_off.size();
+  out4[2] = cell_pattern_ok(S, &T) ? T.ncc : 0;
+  int64_t rows = 0;
+  for (int p = 0; p < S.n_pad; ++p)
+    if (S.perm[p] >= 0) ++rows;
+  out4[3] = rows;
+  return PFC_OK;
+}
+
+int pfc_cell_kernels(const pfc_ctx* c) { return (c && c->prec != 0 && c->cell_ok) ? 1 : 0; }
 
 pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4) {
   if (!out4) return PFC_ERR_INVALID;

@@ -4,7 +4,10 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
+
+#include "cell2d.h"
 
 namespace pfc {
 
@@ -94,7 +97,31 @@ struct SolveArgs {
   int plane;               // rows per lattice plane (3D: lat^2); 0 in 2D (one window segment)
   int tma_S;               // 3D: shared-memory stride between plane segments (S = plane mod 4)
   int tma_cap;             // floats of one window buffer (two buffers in dynamic shared memory)
+  // cell kernels of the Chronopoulos-Gear inner solves (2D P2 rows in cell-major order,
+  // float inner vectors; pcg_cell in solver.cu): the block keeps u on its cells and
+  // the cells its stencils reach in dynamic shared memory (cell_smem_bytes)
+  int cells;               // 1: on (the host checked the stencils and the shared memory)
+  int cell_S;              // cells per lattice line (side + 1)
+  int cell_rows_cap;       // largest row count of a block (layout of the shared memory)
+  int cell_wcap;           // largest window of a block, in cells
+  int ccls_n;              // cell classes: distinct stencils of a cell's four rows (class 0: all interior)
+  const double* ccls_wM;   // ccls_n x kCell2dEntries: M and K weights of the couplings of cell2d.h
+  const double* ccls_wK;   //   for each cell class (0 where a row lacks the coupling)
+  const unsigned char* cellclass;  // n_pad / 4: class of each cell
+  int cell_rep[4];         // an interior row of each dof type (its Jacobi inverse is the type's)
 };
+
+// Dynamic shared memory of the cell kernels, in this order: the window of u (float4
+// per cell), the coupling weights of the four inner operators for every cell class
+// (kCell2dStride floats each), the classes of the block's cells.
+constexpr int kCell2dStride = 48;
+__host__ __device__ inline size_t cell_off_weights(int wcap) { return (size_t)wcap * 16; }
+__host__ __device__ inline size_t cell_off_classes(int wcap, int ncc) {
+  return cell_off_weights(wcap) + (size_t)4 * ncc * kCell2dStride * 4;
+}
+__host__ __device__ inline size_t cell_smem_bytes(int wcap, int ncc, int rows_cap) {
+  return cell_off_classes(wcap, ncc) + (((size_t)rows_cap / 4 + 15) & ~(size_t)15);
+}
 
 // A batched launch: instance k (arguments inst[k], in device memory) owns the
 // blocks seg[k] .. seg[k+1]-1 of the grid.

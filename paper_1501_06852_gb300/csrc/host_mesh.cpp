@@ -14,11 +14,13 @@
 // order IS the internal dof order of every device vector, so a SpMV writes y[row]
 // coalesced and a vector update touches 32 consecutive rows per warp.  Without
 // structured stencils rows are sorted by length (descending) inside windows of
-// kSellSigma lexicographic rows; with them (sigma = 1) the order is lexicographic.
-// Padding rows at the end hold no dof; padding slots point at their own row with
-// value 0.
+// kSellSigma lexicographic rows; with them (sigma = 1) the order is lexicographic,
+// or, for 2D P2 with cells = 1, cell-major (2 x 2 lattice cells of four consecutive
+// rows, cell2d.h).  Padding rows hold no dof; padding slots point at their own row
+// with value 0.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <numeric>
 
 #include "internal.h"
@@ -32,7 +34,8 @@ namespace pfc {
 void element_path(int dim, int t, int verts[4][3]);
 void local_edge(int dim, int e, int& a, int& b);
 
-bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma, int degree) {
+bool build_setup(int dim, int side, double length, HostSetup& S, std::string& err, int sigma, int degree,
+                 int cells) {
   if (dim != 2 && dim != 3) {
     err = "dim must be 2 or 3";
     return false;
@@ -126,18 +129,37 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   for (int i = 0; i < n; ++i) S.nnz += len[i];
 
   // --- internal row order ------------------------------------------------------
-  // perm: internal row -> lexicographic dof, -1 for the padding rows at the end.
+  // perm: internal row -> lexicographic dof, -1 for the padding rows.
   // SELL-32-sigma: rows sorted by length inside windows of sigma lexicographic rows
-  // (sigma = 1 with structured stencils: lexicographic).
+  // (sigma = 1 with structured stencils: lexicographic, padding rows at the end), or
+  // cell-major (2D P2 with structured stencils and cells = 1): row 4 c + sub holds
+  // lattice point (2 cx + (sub & 1), 2 cy + (sub >> 1)) of cell c = cy (side + 1) + cx;
+  // the points with x or y = 2 side + 1 and the rows past the last cell are padding.
   S.iperm.assign(n, -1);
-  S.n_pad = (n + kSellC - 1) / kSellC * kSellC;
-  S.perm.assign(S.n_pad, -1);
-  std::iota(S.perm.begin(), S.perm.begin() + n, 0);
-  for (int w0 = 0; w0 < n; w0 += S.sigma) {
-    int w1 = std::min(n, w0 + S.sigma);
-    std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
+  S.cells = (cells && dim == 2 && degree == 2 && S.sigma == 1) ? 1 : 0;
+  if (S.cells) {
+    const int64_t cs = side + 1, ncell = cs * cs;
+    S.cell_S = (int)cs;
+    S.n_pad = (int)((4 * ncell + kSellC - 1) / kSellC * kSellC);
+    S.perm.assign(S.n_pad, -1);
+    for (int64_t p = 0; p < 4 * ncell; ++p) {
+      const int64_t c = p >> 2, sub = p & 3;
+      const int64_t x = 2 * (c % cs) + (sub & 1), y = 2 * (c / cs) + (sub >> 1);
+      if (x < lat && y < lat) {
+        S.perm[p] = (int)(y * lat + x);
+        S.iperm[y * lat + x] = (int)p;
+      }
+    }
+  } else {
+    S.n_pad = (n + kSellC - 1) / kSellC * kSellC;
+    S.perm.assign(S.n_pad, -1);
+    std::iota(S.perm.begin(), S.perm.begin() + n, 0);
+    for (int w0 = 0; w0 < n; w0 += S.sigma) {
+      int w1 = std::min(n, w0 + S.sigma);
+      std::stable_sort(S.perm.begin() + w0, S.perm.begin() + w1, [&](int a, int b) { return len[a] > len[b]; });
+    }
+    for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
   }
-  for (int p = 0; p < n; ++p) S.iperm[S.perm[p]] = p;
   S.nslices = S.n_pad / kSellC;
   S.slice_ptr.assign(S.nslices + 1, 0);
   for (int s = 0; s < S.nslices; ++s) {
@@ -307,6 +329,75 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
         }
         S.rowinfo[p] = (unsigned char)(t | (interior ? 8 : 0));
       }
+    }
+  }
+
+  // --- row classes (cell-major order) ---------------------------------------------
+  // A row's stencil: its columns as offsets from the row with the M and K values of
+  // the slot (the same sums of element contributions the assembly kernel forms).  On
+  // the uniform mesh the rows with a missing element fall into a few classes (by
+  // dof type and the side or corner they lie on); rows with equal stencils share one.
+  if (S.cells) {
+    const int nt = S.ntypes_dof;
+    S.cls_start.assign(1, 0);
+    for (int t = 0; t < nt; ++t) {
+      for (int k = S.st_start[t]; k < S.st_start[t + 1]; ++k) {
+        S.cls_off.push_back(S.st_off[k]);
+        S.cls_wM.push_back(S.st_wM[k]);
+        S.cls_wK.push_back(S.st_wK[k]);
+      }
+      S.cls_start.push_back((int)S.cls_off.size());
+    }
+    S.cls_start.push_back((int)S.cls_off.size());   // class nt: no entries
+    S.rowclass.assign(S.n_pad, (unsigned char)nt);
+    struct Key {
+      std::vector<int> off;
+      std::vector<double> m, k;
+      bool operator<(const Key& o) const {
+        if (off != o.off) return off < o.off;
+        if (m != o.m) return m < o.m;
+        return k < o.k;
+      }
+    };
+    std::map<Key, int> seen;
+    std::vector<int> buf;
+    for (int p = 0; p < S.n_pad; ++p) {
+      const int i = S.perm[p];
+      if (i < 0) continue;
+      if (S.rowinfo[p] & 8) {
+        S.rowclass[p] = (unsigned char)(S.rowinfo[p] & 7);
+        continue;
+      }
+      row_cols(i, buf);
+      const int s_ = p / kSellC, lane = p % kSellC, base = S.slice_ptr[s_] + lane;
+      Key key;
+      for (int j = 0; j < (int)buf.size(); ++j) {
+        const int slot = base + j * kSellC;
+        double m = 0.0, k = 0.0;
+        for (int q = S.contrib_ptr[slot]; q < S.contrib_ptr[slot + 1]; ++q) {
+          const int idx = S.contrib_idx[q], pr = idx / E, e = idx - pr * E, et = e % ntypes;
+          m += R.mass[(size_t)et * R.npairs + pr];
+          k += R.stiff[(size_t)et * R.npairs + pr];
+        }
+        key.off.push_back(buf[j] - p);
+        key.m.push_back(m);
+        key.k.push_back(k);
+      }
+      auto it = seen.find(key);
+      int id;
+      if (it != seen.end()) {
+        id = it->second;
+      } else {
+        id = (int)S.cls_start.size() - 1;
+        for (size_t j = 0; j < key.off.size(); ++j) {
+          S.cls_off.push_back(key.off[j]);
+          S.cls_wM.push_back(key.m[j]);
+          S.cls_wK.push_back(key.k[j]);
+        }
+        S.cls_start.push_back((int)S.cls_off.size());
+        seen.emplace(std::move(key), id);
+      }
+      S.rowclass[p] = (unsigned char)std::min(id, 255);
     }
   }
   return true;

@@ -64,11 +64,23 @@ struct HostSetup {
   std::vector<int> st_off;
   std::vector<double> st_wM, st_wK;
   std::vector<unsigned char> rowinfo;  // n_pad: bits 0-2 dof type, bit 3 interior
+  // Cell-major row order (2D P2 with structured stencils, cells = 1; cell2d.h):
+  // row 4 c + sub holds lattice point (2 cx + (sub & 1), 2 cy + (sub >> 1)) of cell
+  // c = cy cell_S + cx.  Row classes (built in that order only): every row's stencil
+  // (column offsets with its M and K weights); class t < ntypes_dof is the interior
+  // stencil of dof type t, class ntypes_dof has no entries (rows that hold no dof),
+  // the others are the distinct stencils of the rows with a missing element.
+  int cells = 0;
+  int cell_S = 0;                 // cells per lattice line (side + 1)
+  std::vector<int> cls_start;     // classes + 1
+  std::vector<int> cls_off;
+  std::vector<double> cls_wM, cls_wK;
+  std::vector<unsigned char> rowclass;  // n_pad class of each row (empty unless cells)
 };
 
 bool build_reference(int dim, double h, RefTensors& out, std::string& err, int degree = 2);
 bool build_setup(int dim, int side, double length, HostSetup& out, std::string& err, int sigma = kSellSigma,
-                 int degree = 2);
+                 int degree = 2, int cells = 0);
 
 // Strip partition of the lexicographic rows over nparts devices (row-block solve):
 // begin (nparts + 1 row offsets), halo (ghost rows below / above each part), the

@@ -12,8 +12,9 @@ int solve_threads();
 int solve_ring();
 cudaError_t solve_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem = 0);
 cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t stream);
-cudaError_t batch_occupancy(int prec, int* blocks_per_sm);
-cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream);
+cudaError_t batch_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem = 0);
+// dyn_smem: dynamic shared memory per block (the cell kernels' window and tables)
+cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream, size_t dyn_smem = 0);
 
 // element and vector kernels (kernels.cu)
 // element kernels take the local node count nl: 6 / 10 (P2 triangles / tetrahedra), 3 / 4 (P1)

@@ -251,6 +251,16 @@ __device__ bool grid_sync(Grid& g, int tag, bool entry_sync = true) {
   return s_ok != 0;
 }
 
+// Adds the time since the last mark to the work of phase class tag (profiling only;
+// call after a __syncthreads, so that it times the whole block).
+__device__ __forceinline__ void prof_mark(const Grid& g, int tag) {
+  if (g.prof) {
+    const unsigned long long t = global_ns();
+    s_prof[tag] += (long long)(t - s_t_last);
+    s_t_last = t;
+  }
+}
+
 // Wait until every block whose rows this block's stencil reaches has finished the
 // current phase (a point-to-point replacement for a grid barrier before an SpMV
 // whose only cross-block inputs are the source vector's halo rows).  Each block
@@ -1440,12 +1450,294 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Cell kernels: Chronopoulos-Gear Jacobi-PCG with one grid barrier per iteration
+// (2D P2 rows in cell-major order, float inner vectors; cell2d.h).
+//
+// Every vector is read and written a float4 (one lattice cell, four rows) at a time,
+// block b owning the cells [8 b_lo, 8 b_hi) of its slices.  The block keeps the
+// preconditioned residual u of its own cells and of the H = side + 2 cells on each
+// side of them (every cell its rows' stencils reach) in a shared-memory window, so
+// the product w = A u reads no global memory.  Instead of a grid barrier that would
+// publish u before the product, the block recomputes u on those halo cells itself
+// from the owners' r, s and w of the previous iteration with the same arithmetic the
+// owners use (so the values agree bit for bit); r, s and w alternate between two
+// buffers, so that an owner writing iteration k + 1 never overwrites what a
+// neighbour still reads for iteration k.  One iteration:
+//   phase A, own cells: p = u + b p, s' = w + b s, x += a p, r' = r - a s', u' = D r'
+//            (partials (r', r'), (r', u')); halo cells: s', r', u' as above, u' only kept
+//   phase B, own cells: w' = A u' from the window (partial (w', u'))
+//   one grid sum of the three partials: stop test on (r', r'), then
+//   b = g' / g, a = g' / (d' - b g' / a)
+// The iterates are those of pcg_cg; its separate (r, r) barrier is gone (the test
+// comes one product later, after the same iterate x).  Interior cells (all four rows
+// interior) run the compile-time stencil of cell2d.h; the others walk their rows'
+// class stencils from shared memory.
+
+struct CellMem {
+  float4* win;               // u on cells [wlo, wlo + cell_wcap)
+  const float* wts;          // 4 operators x ccls_n x kCell2dStride coupling weights
+  const unsigned char* cc;   // class of cell 8 b_lo + k, k < cells of the block
+};
+
+__device__ __forceinline__ CellMem cell_mem(const SolveArgs& a) {
+  char* base = reinterpret_cast<char*>(s_win);
+  CellMem m;
+  m.win = reinterpret_cast<float4*>(base);
+  m.wts = reinterpret_cast<const float*>(base + cell_off_weights(a.cell_wcap));
+  m.cc = reinterpret_cast<const unsigned char*>(base + cell_off_classes(a.cell_wcap, a.ccls_n));
+  return m;
+}
+
+// Fills the tables of the cell kernels and zeroes the window cells outside the mesh
+// (read with weight 0 by the cells on its edges, never written); called by all
+// threads at the start of a launch.
+__device__ void cell_tables(const Grid& g, const SolveArgs& a) {
+  char* base = reinterpret_cast<char*>(s_win);
+  float* wts = reinterpret_cast<float*>(base + cell_off_weights(a.cell_wcap));
+  unsigned char* cc = reinterpret_cast<unsigned char*>(base + cell_off_classes(a.cell_wcap, a.ccls_n));
+  const int per_op = a.ccls_n * kCell2dStride;
+  for (int k = threadIdx.x; k < 4 * per_op; k += kThreads) {
+    const int op = k / per_op, r = k - op * per_op, cls = r / kCell2dStride, e = r - cls * kCell2dStride;
+    float w = 0.f;
+    if (e < kCell2dEntries) {
+      const int j = cls * kCell2dEntries + e;
+      w = (float)(a.op_cM[op] * __ldg(a.ccls_wM + j) + a.op_cK[op] * __ldg(a.ccls_wK + j));
+    }
+    wts[k] = w;
+  }
+  const int c_lo = 8 * g.b_lo, ncb = 8 * (g.b_hi - g.b_lo);
+  for (int k = threadIdx.x; k < ncb; k += kThreads) cc[k] = __ldg(a.cellclass + c_lo + k);
+  const int wlo = c_lo - (a.cell_S + 1), ncell = a.n_pad >> 2;
+  float4* win = reinterpret_cast<float4*>(base);
+  for (int k = threadIdx.x; k < a.cell_wcap; k += kThreads) {
+    const int c = wlo + k;
+    if (c < 0 || c >= ncell) win[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+template <int K>
+__device__ __forceinline__ float comp4(float4 v) {
+  return K == 0 ? v.x : K == 1 ? v.y : K == 2 ? v.z : v.w;
+}
+
+// s' = w + b s, r' = r - a s', u' = D r' on one cell: the one formula the owner and
+// the blocks that hold the cell in their halo both evaluate.
+__device__ __forceinline__ void cell_rsu(float4 w, float4 sv, float4 r, float4 d, float al, float be, float4& s1,
+                                         float4& r1, float4& u1) {
+  s1 = make_float4(fmaf(be, sv.x, w.x), fmaf(be, sv.y, w.y), fmaf(be, sv.z, w.z), fmaf(be, sv.w, w.w));
+  r1 = make_float4(fmaf(-al, s1.x, r.x), fmaf(-al, s1.y, r.y), fmaf(-al, s1.z, r.z), fmaf(-al, s1.w, r.w));
+  u1 = make_float4(d.x * r1.x, d.y * r1.y, d.z * r1.z, d.w * r1.w);
+}
+
+// The halo cells of this block: [max(0, wlo), c_lo) and [c_hi, min(ncell, c_hi + H)).
+struct CellRange {
+  int c_lo, c_hi, wlo, h0, nh0, h2, nh;
+};
+__device__ __forceinline__ CellRange cell_range(const Grid& g, const SolveArgs& a) {
+  CellRange r;
+  const int H = a.cell_S + 1, ncell = a.n_pad >> 2;
+  r.c_lo = 8 * g.b_lo;
+  r.c_hi = 8 * g.b_hi;
+  r.wlo = r.c_lo - H;
+  r.h0 = max(0, r.wlo);
+  r.nh0 = r.c_lo - r.h0;
+  r.h2 = r.c_hi;
+  r.nh = r.c_hi > r.c_lo ? r.nh0 + max(0, min(ncell, r.c_hi + H) - r.c_hi) : 0;
+  return r;
+}
+
+// u = D r on the block's cells and halo cells (the window); partial (r, u) on its own.
+__device__ __forceinline__ void cell_fill(const Grid& g, const SolveArgs& a, const float4* r, const float4* di, float& pg) {
+  const CellMem m = cell_mem(a);
+  const CellRange cr = cell_range(g, a);
+  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
+    const float4 rv = r[c], d = di[c];
+    const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
+    m.win[c - cr.wlo] = u;
+    pg = dot4(rv, u, pg);
+  }
+  for (int k = threadIdx.x; k < cr.nh; k += kThreads) {
+    const int c = k < cr.nh0 ? cr.h0 + k : cr.h2 + (k - cr.nh0);
+    const float4 rv = r[c], d = di[c];
+    m.win[c - cr.wlo] = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
+  }
+}
+
+// Inner vector k of the cell kernels (float4 per cell).  r, s and w alternate
+// between two buffers: iteration parity cur reads buffer cur and writes buffer !cur.
+__device__ __forceinline__ float4* cvec(const SolveArgs& a, int k) {
+  return reinterpret_cast<float4*>((float*)a.ivec + (size_t)k * a.n_pad);
+}
+__device__ __forceinline__ int cell_r(int cur) { return cur ? kVu : kVr; }
+__device__ __forceinline__ int cell_s(int cur) { return cur ? kVq : kVs; }
+__device__ __forceinline__ int cell_w(int cur) { return cur ? kVm0 : kVw; }
+
+// Phase A of one iteration (see above): reads r, s, w of parity cur, writes those of
+// !cur, updates p and x, keeps u' in the window.
+__device__ __forceinline__ void cell_phase_a(const Grid& g, const SolveArgs& a, float al, float be, int cur,
+                                             float4* x, const float4* di, float4 dint, float& prr, float& pg) {
+  const CellMem m = cell_mem(a);
+  const CellRange cr = cell_range(g, a);
+  float4* const pv = cvec(a, kVp);
+  const float4* const rc = cvec(a, cell_r(cur));
+  const float4* const sc = cvec(a, cell_s(cur));
+  const float4* const wc = cvec(a, cell_w(cur));
+  float4* const rn = cvec(a, cell_r(cur ^ 1));
+  float4* const sn = cvec(a, cell_s(cur ^ 1));
+  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
+    const float4 u = m.win[c - cr.wlo];
+    // a cell of four interior rows (class 0) has the Jacobi inverses of the interior dof types
+    const bool inner = m.cc[c - cr.c_lo] == 0;
+    const float4 p = pv[c], w = wc[c], sv = sc[c], r = rc[c], xx = x[c];
+    const float4 d = inner ? dint : di[c];
+    float4 s1, r1, u1;
+    cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+    const float4 p1 = make_float4(fmaf(be, p.x, u.x), fmaf(be, p.y, u.y), fmaf(be, p.z, u.z), fmaf(be, p.w, u.w));
+    pv[c] = p1;
+    sn[c] = s1;
+    rn[c] = r1;
+    x[c] = make_float4(fmaf(al, p1.x, xx.x), fmaf(al, p1.y, xx.y), fmaf(al, p1.z, xx.z), fmaf(al, p1.w, xx.w));
+    m.win[c - cr.wlo] = u1;
+    prr = dot4(r1, r1, prr);
+    pg = dot4(r1, u1, pg);
+  }
+  for (int k = threadIdx.x; k < cr.nh; k += kThreads) {
+    const int c = k < cr.nh0 ? cr.h0 + k : cr.h2 + (k - cr.nh0);
+    const float4 w = wc[c], sv = sc[c], r = rc[c], d = di[c];
+    float4 s1, r1, u1;
+    cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+    m.win[c - cr.wlo] = u1;
+  }
+}
+
+// Phase B: w = A_op u on the block's cells from the window; partial (w, u).  Every
+// cell runs the couplings of cell2d.h with the weights of its class (interior cells
+// all read the class-0 row, a broadcast); a coupling a row lacks has weight 0, and the
+// window cells outside the mesh hold zeros.
+__device__ __forceinline__ void cell_phase_b(const Grid& g, const SolveArgs& a, int op, float4* wn, float& pd) {
+  const CellMem m = cell_mem(a);
+  const CellRange cr = cell_range(g, a);
+  const int S = a.cell_S;
+  const float* wop = m.wts + op * a.ccls_n * kCell2dStride;
+  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
+    const int wi = c - cr.wlo;
+    const float* fw = wop + m.cc[c - cr.c_lo] * kCell2dStride;
+    const float4 v[kCell2dSrc] = {m.win[wi - S - 1], m.win[wi - S], m.win[wi - 1], m.win[wi],
+                                  m.win[wi + 1],     m.win[wi + S], m.win[wi + S + 1]};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int e = 0;
+#define PFC_CELL_FMA(t, q, sub)                   \
+  acc[t] = fmaf(fw[e], comp4<sub>(v[q]), acc[t]); \
+  ++e;
+    PFC_CELL2D_ENTRIES(PFC_CELL_FMA)
+#undef PFC_CELL_FMA
+    const float4 w1 = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    wn[c] = w1;
+    pd = dot4(w1, v[3], pd);
+  }
+}
+
+// Chronopoulos-Gear Jacobi-PCG on the cell kernels (see above); same contract as pcg_cg.
+template <class TM>
+__device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const float* DI, float* x,
+                                      RhsSpec<TM, float> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
+  float* const rb0 = (float*)cvec(a, kVr);
+  float* const sb0 = (float*)cvec(a, kVs);
+  float* const pv = (float*)cvec(a, kVp);
+  const int lane = threadIdx.x & 31;
+  // r = b, x = p = s = 0 on the block's rows
+  float pb = 0.f;
+  FOR_MY_GROUPS(g, s0, nsl) {
+#pragma unroll
+    for (int uu = 0; uu < kGroup; ++uu) {
+      if (uu < nsl) {
+        const int s = s0 + uu, row = s * 32 + lane;
+        const float rv = (float)rhs(g, a, s, lane, row);
+        x[row] = 0.f;
+        rb0[row] = rv;
+        sb0[row] = 0.f;
+        pv[row] = 0.f;
+        pb = fmaf(rv, rv, pb);
+      }
+    }
+  }
+  Sum4<float> red;
+  if (!grid_sum<float, 1>(g, pb, 0.f, 0.f, red, kPhInit)) return false;
+  its = 0;
+  cnt.calls += 1;
+  const double bb = red.x;
+  if (!isfinite(bb)) {
+    flag(g, kErrNonfinite);
+    return false;
+  }
+  if (bb == 0.0) return true;
+  const float thr = (float)(rtol * rtol * bb);
+  float4* const x4 = reinterpret_cast<float4*>(x);
+  const float4* const d4 = reinterpret_cast<const float4*>(DI);
+  // the Jacobi inverse of an interior row depends only on its dof type: read it at
+  // an interior row of each type (the same bits the halo cells read from memory)
+  const float4 dint = make_float4(DI[a.cell_rep[0]], DI[a.cell_rep[1]], DI[a.cell_rep[2]], DI[a.cell_rep[3]]);
+  float pg = 0.f, pd = 0.f;
+  cell_fill(g, a, cvec(a, kVr), d4, pg);
+  __syncthreads();
+  cell_phase_b(g, a, op, cvec(a, cell_w(0)), pd);
+  if (!grid_sum<float, 2>(g, pg, pd, 0.f, red, kPhSpmv)) return false;
+  float gam = red.x, del = red.y;
+  if (!(del > 0.f)) {
+    flag(g, kErrBreakdown);
+    return true;
+  }
+  float alpha = gam / del, beta = 0.f;
+  int cur = 0;
+  for (int it = 1; it <= maxit; ++it) {
+    float prr = 0.f;
+    pg = 0.f;
+    pd = 0.f;
+    cell_phase_a(g, a, alpha, beta, cur, x4, d4, dint, prr, pg);
+    __syncthreads();
+    prof_mark(g, kPhVec);
+    cell_phase_b(g, a, op, cvec(a, cell_w(cur ^ 1)), pd);
+    if (!grid_sum<float, 3>(g, prr, pg, pd, red, kPhSpmv)) return false;
+    its = it;
+    if (!isfinite(red.x)) {
+      flag(g, kErrNonfinite);
+      return false;
+    }
+    if (red.x <= thr) {
+      cnt.its += it;
+      return true;
+    }
+    const float gnew = red.y, dnew = red.z;
+    beta = gnew / gam;
+    const float den = dnew - beta * gnew / alpha;
+    if (!(den > 0.f) || !isfinite(den)) {
+      flag(g, kErrBreakdown);
+      cnt.its += it;
+      return true;
+    }
+    alpha = gnew / den;
+    gam = gnew;
+    cur ^= 1;
+  }
+  cnt.its += maxit;
+  cnt.capped += 1;
+  return true;
+}
+
 template <class TM, class TV>
 __device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, int op, const TV* DI, TV* x,
                                     RhsSpec<TM, TV> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
   if (c.a.pcg_variant == 3) {
     if constexpr (sizeof(TV) == 4) {
+      if (c.a.cells) return pcg_cell<TM>(g, c.a, op, DI, x, rhs, rtol, maxit, cnt, its);
       if (c.a.tma) return pcg_cg<TM, TV, true>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
     }
     return pcg_cg<TM, TV, false>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
@@ -1953,6 +2245,7 @@ __device__ __forceinline__ void solve_body(const SolveArgs& a, int bid, int G) {
       s_tma_uses[0] = s_tma_uses[1] = 0;
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (sizeof(TV) == 4 && a.cells) cell_tables(g, a);
     // this block's row-info bytes, 16 at a time (the row ranges start at multiples of 32)
     const int nrow = (g.b_hi - g.b_lo) * 32;
     g.ri_smem = nrow <= kRowInfoCap;
@@ -2042,19 +2335,24 @@ cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t
   void* params[] = {&local};
   size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
   if (prec != 0 && args.tma) dyn = 2 * (size_t)args.tma_cap * sizeof(float);
+  if (prec != 0 && args.cells) dyn = cell_smem_bytes(args.cell_wcap, args.ccls_n, args.cell_rows_cap);
   cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, dyn, stream);
 }
 
-cudaError_t batch_occupancy(int prec, int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(prec, true), kThreads, 0);
+cudaError_t batch_occupancy(int prec, int* blocks_per_sm, size_t dyn_smem) {
+  cudaError_t e = allow_dyn_smem(kernel_for(prec, true), dyn_smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel_for(prec, true), kThreads, dyn_smem);
 }
 
-cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream) {
+cudaError_t launch_solve_batch(int prec, int grid, const BatchArgs& args, cudaStream_t stream, size_t dyn_smem) {
   BatchArgs local = args;
   void* params[] = {&local};
-  return cudaLaunchCooperativeKernel(kernel_for(prec, true), dim3(grid), dim3(kThreads), params, 0, stream);
+  cudaError_t e = allow_dyn_smem(kernel_for(prec, true), dyn_smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel(kernel_for(prec, true), dim3(grid), dim3(kThreads), params, dyn_smem, stream);
 }
 
 }  // namespace pfc

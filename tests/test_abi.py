@@ -40,6 +40,7 @@ def test_default_options(pkg):
     assert o["pcg_variant"] == 2 and o["inner_operator"] == 1 and o["smem_window"] == 0
     assert o["model"] == 2 and o["psi_min"] == -1.5 and o["schur"] == 0 and o["schur_its"] == 20
     assert o["degree"] == 2 and o["err_tol"] == 1e-9 and o["tau_guard"] == 0.0 and o["grid_blocks"] == 0
+    assert o["cells"] == 1
 
 
 def test_status_strings(pkg):

@@ -353,7 +353,7 @@ def test_smem_window_gives_the_same_bits(case):
     x, b, yref = oracle_stage(case, 0.7)
     out = []
     for win in (1, 0):
-        with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", outer_tol=1e-11, smem_window=win) as s:
+        with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", outer_tol=1e-11, smem_window=win, cells=0) as s:
             s.assemble(cuda(x), 0.7)
             y, st = s.stage_solve(cuda(b))
             out.append((y, st))
@@ -377,7 +377,8 @@ def test_chunked_windows_match_oracle(case, tau):
     x, b, yref = oracle_stage(case, tau)
     out = {}
     for win in (2, 0):
-        with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", smem_window=win) as s:
+        # the chunk windows follow lexicographic lattice lines (cells = 0)
+        with pfc.PFCSolver(dim, side, L, r=r, precision="fp32", smem_window=win, cells=0) as s:
             s.assemble(cuda(x), tau)
             y, st = s.stage_solve(cuda(b))
             out[win] = (host(y), st)
