@@ -102,8 +102,10 @@ struct SolveArgs {
   // the cells its stencils reach in dynamic shared memory (cell_smem_bytes)
   int cells;               // 1: on (the host checked the stencils and the shared memory)
   int cell_S;              // cells per lattice line (side + 1)
-  int cell_rows_cap;       // largest row count of a block (layout of the shared memory)
-  int cell_wcap;           // largest window of a block, in cells
+  int cell_gx, cell_gy;    // tiles of the cell grid along x and y (block b owns tile (b % gx, b / gx))
+  int cell_ccap;           // largest tile, in cells (layout of the shared memory)
+  int cell_wcap;           // largest tile with its ring, in cells
+  int cell_rcap;           // largest ring, in cells
   int ccls_n;              // cell classes: distinct stencils of a cell's four rows (class 0: all interior)
   const double* ccls_wM;   // ccls_n x kCell2dEntries: M and K weights of the couplings of cell2d.h
   const double* ccls_wK;   //   for each cell class (0 where a row lacks the coupling)
@@ -112,15 +114,19 @@ struct SolveArgs {
 };
 
 // Dynamic shared memory of the cell kernels, in this order: the window of u (float4
-// per cell), the coupling weights of the four inner operators for every cell class
-// (kCell2dStride floats each), the classes of the block's cells.
+// per cell of the tile and its ring), the ring cells {window index, cell or -1}, the
+// coupling weights of the four inner operators for every cell class (kCell2dStride
+// floats each), the classes of the tile's cells.
 constexpr int kCell2dStride = 48;
-__host__ __device__ inline size_t cell_off_weights(int wcap) { return (size_t)wcap * 16; }
-__host__ __device__ inline size_t cell_off_classes(int wcap, int ncc) {
-  return cell_off_weights(wcap) + (size_t)4 * ncc * kCell2dStride * 4;
+__host__ __device__ inline size_t cell_off_ring(int wcap) { return (size_t)wcap * 16; }
+__host__ __device__ inline size_t cell_off_weights(int wcap, int rcap) {
+  return cell_off_ring(wcap) + (((size_t)rcap * 8 + 15) & ~(size_t)15);
 }
-__host__ __device__ inline size_t cell_smem_bytes(int wcap, int ncc, int rows_cap) {
-  return cell_off_classes(wcap, ncc) + (((size_t)rows_cap / 4 + 15) & ~(size_t)15);
+__host__ __device__ inline size_t cell_off_classes(int wcap, int rcap, int ncc) {
+  return cell_off_weights(wcap, rcap) + (size_t)4 * ncc * kCell2dStride * 4;
+}
+__host__ __device__ inline size_t cell_smem_bytes(int wcap, int rcap, int ncc, int ccap) {
+  return cell_off_classes(wcap, rcap, ncc) + (((size_t)ccap + 15) & ~(size_t)15);
 }
 
 // A batched launch: instance k (arguments inst[k], in device memory) owns the

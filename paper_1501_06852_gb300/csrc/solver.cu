@@ -1454,48 +1454,124 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
 // Cell kernels: Chronopoulos-Gear Jacobi-PCG with one grid barrier per iteration
 // (2D P2 rows in cell-major order, float inner vectors; cell2d.h).
 //
-// Every vector is read and written a float4 (one lattice cell, four rows) at a time,
-// block b owning the cells [8 b_lo, 8 b_hi) of its slices.  The block keeps the
-// preconditioned residual u of its own cells and of the H = side + 2 cells on each
-// side of them (every cell its rows' stencils reach) in a shared-memory window, so
-// the product w = A u reads no global memory.  Instead of a grid barrier that would
-// publish u before the product, the block recomputes u on those halo cells itself
-// from the owners' r, s and w of the previous iteration with the same arithmetic the
-// owners use (so the values agree bit for bit); r, s and w alternate between two
-// buffers, so that an owner writing iteration k + 1 never overwrites what a
-// neighbour still reads for iteration k.  One iteration:
-//   phase A, own cells: p = u + b p, s' = w + b s, x += a p, r' = r - a s', u' = D r'
-//            (partials (r', r'), (r', u')); halo cells: s', r', u' as above, u' only kept
-//   phase B, own cells: w' = A u' from the window (partial (w', u'))
+// Every vector is read and written a float4 (one lattice cell, four rows) at a time.
+// For these phases the cell grid (cell_S x cell_S cells) is cut into cell_gx x
+// cell_gy rectangular tiles, tile (b mod gx, b / gx) owned by block b (blocks past
+// gx gy own none).  A block keeps the preconditioned residual u of its tile and of
+// the ring of cells around it (every cell its rows' stencils reach) in a
+// shared-memory window, so the product w = A u reads no global memory.  Instead of
+// a grid barrier that would publish u before the product, the block recomputes u on
+// the ring itself from the owners' r, s and w of the previous iteration with the
+// same arithmetic the owners use (so the values agree bit for bit); r, s and w
+// alternate between two buffers, so that an owner writing iteration k + 1 never
+// overwrites what a neighbour still reads for iteration k.  A tile's ring is its
+// perimeter (a strip of rows would need two whole lattice lines of cells).  One
+// iteration:
+//   phase A, tile: p = u + b p, s' = w + b s, x += a p, r' = r - a s', u' = D r'
+//           (partials (r', r'), (r', u')); ring: s', r', u' as above, u' only kept
+//   phase B, tile: w' = A u' from the window (partial (w', u'))
 //   one grid sum of the three partials: stop test on (r', r'), then
 //   b = g' / g, a = g' / (d' - b g' / a)
 // The iterates are those of pcg_cg; its separate (r, r) barrier is gone (the test
-// comes one product later, after the same iterate x).  Interior cells (all four rows
-// interior) run the compile-time stencil of cell2d.h; the others walk their rows'
-// class stencils from shared memory.
+// comes one product later, after the same iterate x).  Every cell runs the couplings
+// of cell2d.h with the weights of its cell class (interior cells: class 0).  The
+// set-up before the loop (r = b etc.) and the caller's use of x go by the block's
+// slices as everywhere else; the grid barriers in between order the two ownerships.
 
 struct CellMem {
-  float4* win;               // u on cells [wlo, wlo + cell_wcap)
+  float4* win;               // u on the tile and its ring, (tw + 2) x (th + 2) cells
+  const int2* ring;          // ring cell j: {window index, cell index or -1 outside the grid}
   const float* wts;          // 4 operators x ccls_n x kCell2dStride coupling weights
-  const unsigned char* cc;   // class of cell 8 b_lo + k, k < cells of the block
+  const unsigned char* cc;   // class of each tile cell, tile order
 };
 
 __device__ __forceinline__ CellMem cell_mem(const SolveArgs& a) {
   char* base = reinterpret_cast<char*>(s_win);
   CellMem m;
   m.win = reinterpret_cast<float4*>(base);
-  m.wts = reinterpret_cast<const float*>(base + cell_off_weights(a.cell_wcap));
-  m.cc = reinterpret_cast<const unsigned char*>(base + cell_off_classes(a.cell_wcap, a.ccls_n));
+  m.ring = reinterpret_cast<const int2*>(base + cell_off_ring(a.cell_wcap));
+  m.wts = reinterpret_cast<const float*>(base + cell_off_weights(a.cell_wcap, a.cell_rcap));
+  m.cc = reinterpret_cast<const unsigned char*>(base + cell_off_classes(a.cell_wcap, a.cell_rcap, a.ccls_n));
   return m;
 }
 
-// Fills the tables of the cell kernels and zeroes the window cells outside the mesh
-// (read with weight 0 by the cells on its edges, never written); called by all
+
+// This block's tile: cells (cx, cy) with x0 <= cx < x0 + tw, y0 <= cy < y0 + th; tile
+// cell k = (cx - x0) + (cy - y0) tw sits at window index (k mod tw + 1) + (k / tw + 1) ws.
+// dq, dr: kThreads = dq tw + dr (the walk's step); inv_tw = 1 / tw.
+struct CellTile {
+  int x0, y0, tw, th, ws, own, ring, dq, dr;
+  float inv_tw;
+};
+__shared__ CellTile s_tile;   // set once per launch (cell_tables)
+
+__device__ __forceinline__ CellTile cell_tile_of(const Grid& g, const SolveArgs& a) {
+  CellTile t;
+  const int gx = a.cell_gx, gy = a.cell_gy, S = a.cell_S;
+  const bool has = g.bid < gx * gy;
+  const int ix = has ? g.bid % gx : 0, iy = has ? g.bid / gx : 0;
+  t.x0 = (int)((long long)ix * S / gx);
+  t.y0 = (int)((long long)iy * S / gy);
+  t.tw = has ? (int)((long long)(ix + 1) * S / gx) - t.x0 : 0;
+  t.th = has ? (int)((long long)(iy + 1) * S / gy) - t.y0 : 0;
+  t.ws = t.tw + 2;
+  t.own = t.tw * t.th;
+  t.ring = t.own > 0 ? 2 * (t.tw + 2) + 2 * t.th : 0;
+  t.dq = t.tw > 0 ? kThreads / t.tw : 0;
+  t.dr = t.tw > 0 ? kThreads % t.tw : 0;
+  t.inv_tw = t.tw > 0 ? 1.0f / (float)t.tw : 0.f;
+  return t;
+}
+__device__ __forceinline__ const CellTile& cell_tile() { return s_tile; }
+
+// Walks the tile cells k = threadIdx.x, + kThreads, ... of the block's tile: (lx, ly)
+// are the window coordinates (tile cell k at (k mod tw + 1, k / tw + 1)), advanced
+// without a division.  The first quotient comes from the float reciprocal: (k + 1/2) /
+// tw lies at least 1/(2 tw) from an integer and k < 2^10, so the rounding of one
+// float product cannot cross one.
+struct TileWalk {
+  int lx, ly, dq, dr, tw;
+  __device__ __forceinline__ explicit TileWalk(const CellTile& t) : dq(t.dq), dr(t.dr), tw(t.tw) {
+    const int k0 = threadIdx.x;
+    const int q = __float2int_rz(((float)k0 + 0.5f) * t.inv_tw);
+    ly = q + 1;
+    lx = k0 - q * t.tw + 1;
+  }
+  __device__ __forceinline__ void next() {
+    lx += dr;
+    ly += dq;
+    if (lx > tw) {
+      lx -= tw;
+      ly += 1;
+    }
+  }
+};
+// Ring cell j: the row below the tile, the row above (tw + 2 each, corners
+// included), then the column left of it and the column right (th each).
+__device__ __forceinline__ void ring_cell(const CellTile& t, int j, int& lx, int& ly) {
+  if (j < t.ws) {
+    lx = j;
+    ly = 0;
+  } else if (j < 2 * t.ws) {
+    lx = j - t.ws;
+    ly = t.th + 1;
+  } else if (j < 2 * t.ws + t.th) {
+    lx = 0;
+    ly = j - 2 * t.ws + 1;
+  } else {
+    lx = t.tw + 1;
+    ly = j - 2 * t.ws - t.th + 1;
+  }
+}
+
+// Fills the tables of the cell kernels and zeroes the window cells outside the cell
+// grid (read with weight 0 by the cells on its edges, never written); called by all
 // threads at the start of a launch.
 __device__ void cell_tables(const Grid& g, const SolveArgs& a) {
   char* base = reinterpret_cast<char*>(s_win);
-  float* wts = reinterpret_cast<float*>(base + cell_off_weights(a.cell_wcap));
-  unsigned char* cc = reinterpret_cast<unsigned char*>(base + cell_off_classes(a.cell_wcap, a.ccls_n));
+  int2* ring = reinterpret_cast<int2*>(base + cell_off_ring(a.cell_wcap));
+  float* wts = reinterpret_cast<float*>(base + cell_off_weights(a.cell_wcap, a.cell_rcap));
+  unsigned char* cc = reinterpret_cast<unsigned char*>(base + cell_off_classes(a.cell_wcap, a.cell_rcap, a.ccls_n));
   const int per_op = a.ccls_n * kCell2dStride;
   for (int k = threadIdx.x; k < 4 * per_op; k += kThreads) {
     const int op = k / per_op, r = k - op * per_op, cls = r / kCell2dStride, e = r - cls * kCell2dStride;
@@ -1506,13 +1582,25 @@ __device__ void cell_tables(const Grid& g, const SolveArgs& a) {
     }
     wts[k] = w;
   }
-  const int c_lo = 8 * g.b_lo, ncb = 8 * (g.b_hi - g.b_lo);
-  for (int k = threadIdx.x; k < ncb; k += kThreads) cc[k] = __ldg(a.cellclass + c_lo + k);
-  const int wlo = c_lo - (a.cell_S + 1), ncell = a.n_pad >> 2;
+  const CellTile t = cell_tile_of(g, a);
+  if (threadIdx.x == 0) s_tile = t;
+  const int S = a.cell_S;
+  for (int k = threadIdx.x; k < t.own; k += kThreads) {
+    const int cx = t.x0 + k % t.tw, cy = t.y0 + k / t.tw;
+    cc[k] = __ldg(a.cellclass + (size_t)cy * S + cx);
+  }
+  for (int j = threadIdx.x; j < t.ring; j += kThreads) {
+    int lx, ly;
+    ring_cell(t, j, lx, ly);
+    const int cx = t.x0 - 1 + lx, cy = t.y0 - 1 + ly;
+    const bool in = cx >= 0 && cx < S && cy >= 0 && cy < S;
+    ring[j] = make_int2(lx + ly * t.ws, in ? cy * S + cx : -1);
+  }
   float4* win = reinterpret_cast<float4*>(base);
-  for (int k = threadIdx.x; k < a.cell_wcap; k += kThreads) {
-    const int c = wlo + k;
-    if (c < 0 || c >= ncell) win[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int nw = t.own > 0 ? t.ws * (t.th + 2) : 0;
+  for (int k = threadIdx.x; k < nw; k += kThreads) {
+    const int cx = t.x0 - 1 + k % t.ws, cy = t.y0 - 1 + k / t.ws;
+    if (cx < 0 || cx >= S || cy < 0 || cy >= S) win[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -1528,46 +1616,12 @@ __device__ __forceinline__ float comp4(float4 v) {
 }
 
 // s' = w + b s, r' = r - a s', u' = D r' on one cell: the one formula the owner and
-// the blocks that hold the cell in their halo both evaluate.
+// the blocks that hold the cell in their ring both evaluate.
 __device__ __forceinline__ void cell_rsu(float4 w, float4 sv, float4 r, float4 d, float al, float be, float4& s1,
                                          float4& r1, float4& u1) {
   s1 = make_float4(fmaf(be, sv.x, w.x), fmaf(be, sv.y, w.y), fmaf(be, sv.z, w.z), fmaf(be, sv.w, w.w));
   r1 = make_float4(fmaf(-al, s1.x, r.x), fmaf(-al, s1.y, r.y), fmaf(-al, s1.z, r.z), fmaf(-al, s1.w, r.w));
   u1 = make_float4(d.x * r1.x, d.y * r1.y, d.z * r1.z, d.w * r1.w);
-}
-
-// The halo cells of this block: [max(0, wlo), c_lo) and [c_hi, min(ncell, c_hi + H)).
-struct CellRange {
-  int c_lo, c_hi, wlo, h0, nh0, h2, nh;
-};
-__device__ __forceinline__ CellRange cell_range(const Grid& g, const SolveArgs& a) {
-  CellRange r;
-  const int H = a.cell_S + 1, ncell = a.n_pad >> 2;
-  r.c_lo = 8 * g.b_lo;
-  r.c_hi = 8 * g.b_hi;
-  r.wlo = r.c_lo - H;
-  r.h0 = max(0, r.wlo);
-  r.nh0 = r.c_lo - r.h0;
-  r.h2 = r.c_hi;
-  r.nh = r.c_hi > r.c_lo ? r.nh0 + max(0, min(ncell, r.c_hi + H) - r.c_hi) : 0;
-  return r;
-}
-
-// u = D r on the block's cells and halo cells (the window); partial (r, u) on its own.
-__device__ __forceinline__ void cell_fill(const Grid& g, const SolveArgs& a, const float4* r, const float4* di, float& pg) {
-  const CellMem m = cell_mem(a);
-  const CellRange cr = cell_range(g, a);
-  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
-    const float4 rv = r[c], d = di[c];
-    const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
-    m.win[c - cr.wlo] = u;
-    pg = dot4(rv, u, pg);
-  }
-  for (int k = threadIdx.x; k < cr.nh; k += kThreads) {
-    const int c = k < cr.nh0 ? cr.h0 + k : cr.h2 + (k - cr.nh0);
-    const float4 rv = r[c], d = di[c];
-    m.win[c - cr.wlo] = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
-  }
 }
 
 // Inner vector k of the cell kernels (float4 per cell).  r, s and w alternate
@@ -1579,58 +1633,96 @@ __device__ __forceinline__ int cell_r(int cur) { return cur ? kVu : kVr; }
 __device__ __forceinline__ int cell_s(int cur) { return cur ? kVq : kVs; }
 __device__ __forceinline__ int cell_w(int cur) { return cur ? kVm0 : kVw; }
 
+// Jacobi inverse of a ring cell: the interior types' values for a cell of class 0
+// (the rule the owner applies), else the cell's own.
+__device__ __forceinline__ float4 ring_d(const SolveArgs& a, const float4* di, float4 dint, int c) {
+  return __ldg(a.cellclass + c) == 0 ? dint : di[c];
+}
+
+// u = D r on the tile and its ring (the window); partial (r, u) on the tile.
+__device__ __forceinline__ void cell_fill(const Grid& g, const SolveArgs& a, const float4* r, const float4* di,
+                                          float4 dint, float& pg) {
+  const CellMem m = cell_mem(a);
+  const CellTile& t = cell_tile();
+  const int S = a.cell_S;
+  TileWalk tk(t);
+  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next()) {
+    int wi, c;
+    if (k < t.own) {
+      wi = tk.lx + tk.ly * t.ws;
+      c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx);
+    } else {
+      const int2 rc = m.ring[k - t.own];
+      wi = rc.x;
+      c = rc.y;
+      if (c < 0) continue;
+    }
+    const float4 rv = r[c];
+    const float4 d = k < t.own ? (m.cc[k] == 0 ? dint : di[c]) : ring_d(a, di, dint, c);
+    const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
+    m.win[wi] = u;
+    if (k < t.own) pg = dot4(rv, u, pg);
+  }
+}
+
 // Phase A of one iteration (see above): reads r, s, w of parity cur, writes those of
 // !cur, updates p and x, keeps u' in the window.
 __device__ __forceinline__ void cell_phase_a(const Grid& g, const SolveArgs& a, float al, float be, int cur,
                                              float4* x, const float4* di, float4 dint, float& prr, float& pg) {
   const CellMem m = cell_mem(a);
-  const CellRange cr = cell_range(g, a);
+  const CellTile& t = cell_tile();
+  const int S = a.cell_S;
   float4* const pv = cvec(a, kVp);
   const float4* const rc = cvec(a, cell_r(cur));
   const float4* const sc = cvec(a, cell_s(cur));
   const float4* const wc = cvec(a, cell_w(cur));
   float4* const rn = cvec(a, cell_r(cur ^ 1));
   float4* const sn = cvec(a, cell_s(cur ^ 1));
-  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
-    const float4 u = m.win[c - cr.wlo];
-    // a cell of four interior rows (class 0) has the Jacobi inverses of the interior dof types
-    const bool inner = m.cc[c - cr.c_lo] == 0;
-    const float4 p = pv[c], w = wc[c], sv = sc[c], r = rc[c], xx = x[c];
-    const float4 d = inner ? dint : di[c];
-    float4 s1, r1, u1;
-    cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
-    const float4 p1 = make_float4(fmaf(be, p.x, u.x), fmaf(be, p.y, u.y), fmaf(be, p.z, u.z), fmaf(be, p.w, u.w));
-    pv[c] = p1;
-    sn[c] = s1;
-    rn[c] = r1;
-    x[c] = make_float4(fmaf(al, p1.x, xx.x), fmaf(al, p1.y, xx.y), fmaf(al, p1.z, xx.z), fmaf(al, p1.w, xx.w));
-    m.win[c - cr.wlo] = u1;
-    prr = dot4(r1, r1, prr);
-    pg = dot4(r1, u1, pg);
-  }
-  for (int k = threadIdx.x; k < cr.nh; k += kThreads) {
-    const int c = k < cr.nh0 ? cr.h0 + k : cr.h2 + (k - cr.nh0);
-    const float4 w = wc[c], sv = sc[c], r = rc[c], d = di[c];
-    float4 s1, r1, u1;
-    cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
-    m.win[c - cr.wlo] = u1;
+  TileWalk tk(t);
+  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next()) {
+    if (k < t.own) {
+      const int c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx), wi = tk.lx + tk.ly * t.ws;
+      const float4 u = m.win[wi];
+      const float4 p = pv[c], w = wc[c], sv = sc[c], r = rc[c], xx = x[c];
+      // a cell of four interior rows (class 0) has the Jacobi inverses of the interior dof types
+      const float4 d = m.cc[k] == 0 ? dint : di[c];
+      float4 s1, r1, u1;
+      cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+      const float4 p1 = make_float4(fmaf(be, p.x, u.x), fmaf(be, p.y, u.y), fmaf(be, p.z, u.z), fmaf(be, p.w, u.w));
+      pv[c] = p1;
+      sn[c] = s1;
+      rn[c] = r1;
+      x[c] = make_float4(fmaf(al, p1.x, xx.x), fmaf(al, p1.y, xx.y), fmaf(al, p1.z, xx.z), fmaf(al, p1.w, xx.w));
+      m.win[wi] = u1;
+      prr = dot4(r1, r1, prr);
+      pg = dot4(r1, u1, pg);
+    } else {
+      const int2 rg = m.ring[k - t.own];
+      const int c = rg.y;
+      if (c < 0) continue;
+      const float4 w = wc[c], sv = sc[c], r = rc[c], d = ring_d(a, di, dint, c);
+      float4 s1, r1, u1;
+      cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+      m.win[rg.x] = u1;
+    }
   }
 }
 
-// Phase B: w = A_op u on the block's cells from the window; partial (w, u).  Every
-// cell runs the couplings of cell2d.h with the weights of its class (interior cells
-// all read the class-0 row, a broadcast); a coupling a row lacks has weight 0, and the
-// window cells outside the mesh hold zeros.
+// Phase B: w = A_op u on the tile from the window; partial (w, u).  Every cell runs
+// the couplings of cell2d.h with the weights of its class (interior cells all read
+// the class-0 row, a broadcast); a coupling a row lacks has weight 0, and the window
+// cells outside the cell grid hold zeros.
 __device__ __forceinline__ void cell_phase_b(const Grid& g, const SolveArgs& a, int op, float4* wn, float& pd) {
   const CellMem m = cell_mem(a);
-  const CellRange cr = cell_range(g, a);
-  const int S = a.cell_S;
+  const CellTile& t = cell_tile();
+  const int S = a.cell_S, ws = t.ws;
   const float* wop = m.wts + op * a.ccls_n * kCell2dStride;
-  for (int c = cr.c_lo + (int)threadIdx.x; c < cr.c_hi; c += kThreads) {
-    const int wi = c - cr.wlo;
-    const float* fw = wop + m.cc[c - cr.c_lo] * kCell2dStride;
-    const float4 v[kCell2dSrc] = {m.win[wi - S - 1], m.win[wi - S], m.win[wi - 1], m.win[wi],
-                                  m.win[wi + 1],     m.win[wi + S], m.win[wi + S + 1]};
+  TileWalk tk(t);
+  for (int k = threadIdx.x; k < t.own; k += kThreads, tk.next()) {
+    const int c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx), wi = tk.lx + tk.ly * ws;
+    const float* fw = wop + m.cc[k] * kCell2dStride;
+    const float4 v[kCell2dSrc] = {m.win[wi - ws - 1], m.win[wi - ws], m.win[wi - 1], m.win[wi],
+                                  m.win[wi + 1],      m.win[wi + ws], m.win[wi + ws + 1]};
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     int e = 0;
 #define PFC_CELL_FMA(t, q, sub)                   \
@@ -1642,6 +1734,105 @@ __device__ __forceinline__ void cell_phase_b(const Grid& g, const SolveArgs& a, 
     wn[c] = w1;
     pd = dot4(w1, v[3], pd);
   }
+}
+
+// The grid sum of the cell iteration in three parts, so that the block can issue the
+// loads of its next phase-A cell while it waits (the values of its own cells need no
+// barrier: only this block writes them).  Same partial ring, barrier and bounded wait
+// as grid_sum / grid_sync; the read-back is done by one warp (at most kThreads / 32
+// partials per lane) and summed in a fixed order.
+__shared__ Sum4<float> s_cell_w[kWarps];
+__shared__ Sum4<float> s_cell_res;
+__shared__ int s_cell_ok;
+
+// Block partial of (x, y, z) into this sum's ring slot, then the release arrival.
+__device__ __forceinline__ int cell_sum_arrive(Grid& g, float x, float y, float z) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  x = warp_sum(x);
+  y = warp_sum(y);
+  z = warp_sum(z);
+  if (l == 0) s_cell_w[w] = Sum4<float>{x, y, z, 0.f};
+  __syncthreads();
+  const int slot = g.ring;
+  g.ring = (g.ring + 1) % kRing;
+  if (w == 0) {
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    if (l < kWarps) {
+      const Sum4<float> t = s_cell_w[l];
+      tx = t.x;
+      ty = t.y;
+      tz = t.z;
+    }
+    tx = warp_sum(tx);
+    ty = warp_sum(ty);
+    tz = warp_sum(tz);
+    if (l == 0) {
+      store_partial<float, 3>(g.part + slot * g.G + g.bid, tx, ty, tz);
+      if (g.prof) {
+        const unsigned long long t = global_ns();
+        s_prof[kPhSpmv] += (long long)(t - s_t_last);
+        s_t_last = t;
+      }
+      g.epoch += 1;
+      // release: the partial and every write of the block (ordered by the
+      // __syncthreads above) before the arrival
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(g.arrive) : "memory");
+    }
+  }
+  return slot;
+}
+
+// Thread 0 waits (bounded, as in grid_sync) for every block's arrival; then warp 0
+// reads the partials of the slot and every thread gets the sums.
+__device__ __forceinline__ bool cell_sum_finish(Grid& g, int slot, Sum4<float>& out) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    const unsigned target = g.epoch * (unsigned)g.expect;
+    unsigned spins = 0;
+    unsigned long long t0 = 0;
+    int ok = 1;
+    while (ld_acquire_u32(g.arrive) < target) {
+      if ((++spins & 255u) == 0u) {
+        if (ld_relaxed_i32(g.err) & kErrTimeout) {
+          ok = 0;
+          break;
+        }
+        const unsigned long long t = global_ns();
+        if (t0 == 0) {
+          t0 = t;
+        } else if (t - t0 > g.limit_ns) {
+          atomicOr(g.err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_cell_ok = ok;
+    if (g.prof) {
+      const unsigned long long t = global_ns();
+      s_prof[4 + kPhSpmv] += (long long)(t - s_t_last);
+      s_t_last = t;
+    }
+  }
+  __syncthreads();
+  if (!s_cell_ok) return false;
+  if (w == 0) {
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    for (int b = l; b < g.G; b += 32) {
+      float px, py, pz;
+      load_partial<float, 3>(g.part + slot * g.G + b, px, py, pz);
+      tx += px;
+      ty += py;
+      tz += pz;
+    }
+    tx = warp_sum(tx);
+    ty = warp_sum(ty);
+    tz = warp_sum(tz);
+    if (l == 0) s_cell_res = Sum4<float>{tx, ty, tz, 0.f};
+  }
+  __syncthreads();
+  out = s_cell_res;
+  return true;
 }
 
 // Chronopoulos-Gear Jacobi-PCG on the cell kernels (see above); same contract as pcg_cg.
@@ -1682,10 +1873,10 @@ __device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const
   float4* const x4 = reinterpret_cast<float4*>(x);
   const float4* const d4 = reinterpret_cast<const float4*>(DI);
   // the Jacobi inverse of an interior row depends only on its dof type: read it at
-  // an interior row of each type (the same bits the halo cells read from memory)
+  // an interior row of each type, and use it for every cell of class 0 (owner and ring)
   const float4 dint = make_float4(DI[a.cell_rep[0]], DI[a.cell_rep[1]], DI[a.cell_rep[2]], DI[a.cell_rep[3]]);
   float pg = 0.f, pd = 0.f;
-  cell_fill(g, a, cvec(a, kVr), d4, pg);
+  cell_fill(g, a, cvec(a, kVr), d4, dint, pg);
   __syncthreads();
   cell_phase_b(g, a, op, cvec(a, cell_w(0)), pd);
   if (!grid_sum<float, 2>(g, pg, pd, 0.f, red, kPhSpmv)) return false;
@@ -2335,7 +2526,7 @@ cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t
   void* params[] = {&local};
   size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
   if (prec != 0 && args.tma) dyn = 2 * (size_t)args.tma_cap * sizeof(float);
-  if (prec != 0 && args.cells) dyn = cell_smem_bytes(args.cell_wcap, args.ccls_n, args.cell_rows_cap);
+  if (prec != 0 && args.cells) dyn = cell_smem_bytes(args.cell_wcap, args.cell_rcap, args.ccls_n, args.cell_ccap);
   cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, dyn, stream);
