@@ -1736,105 +1736,6 @@ __device__ __forceinline__ void cell_phase_b(const Grid& g, const SolveArgs& a, 
   }
 }
 
-// The grid sum of the cell iteration in three parts, so that the block can issue the
-// loads of its next phase-A cell while it waits (the values of its own cells need no
-// barrier: only this block writes them).  Same partial ring, barrier and bounded wait
-// as grid_sum / grid_sync; the read-back is done by one warp (at most kThreads / 32
-// partials per lane) and summed in a fixed order.
-__shared__ Sum4<float> s_cell_w[kWarps];
-__shared__ Sum4<float> s_cell_res;
-__shared__ int s_cell_ok;
-
-// Block partial of (x, y, z) into this sum's ring slot, then the release arrival.
-__device__ __forceinline__ int cell_sum_arrive(Grid& g, float x, float y, float z) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  x = warp_sum(x);
-  y = warp_sum(y);
-  z = warp_sum(z);
-  if (l == 0) s_cell_w[w] = Sum4<float>{x, y, z, 0.f};
-  __syncthreads();
-  const int slot = g.ring;
-  g.ring = (g.ring + 1) % kRing;
-  if (w == 0) {
-    float tx = 0.f, ty = 0.f, tz = 0.f;
-    if (l < kWarps) {
-      const Sum4<float> t = s_cell_w[l];
-      tx = t.x;
-      ty = t.y;
-      tz = t.z;
-    }
-    tx = warp_sum(tx);
-    ty = warp_sum(ty);
-    tz = warp_sum(tz);
-    if (l == 0) {
-      store_partial<float, 3>(g.part + slot * g.G + g.bid, tx, ty, tz);
-      if (g.prof) {
-        const unsigned long long t = global_ns();
-        s_prof[kPhSpmv] += (long long)(t - s_t_last);
-        s_t_last = t;
-      }
-      g.epoch += 1;
-      // release: the partial and every write of the block (ordered by the
-      // __syncthreads above) before the arrival
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(g.arrive) : "memory");
-    }
-  }
-  return slot;
-}
-
-// Thread 0 waits (bounded, as in grid_sync) for every block's arrival; then warp 0
-// reads the partials of the slot and every thread gets the sums.
-__device__ __forceinline__ bool cell_sum_finish(Grid& g, int slot, Sum4<float>& out) {
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    const unsigned target = g.epoch * (unsigned)g.expect;
-    unsigned spins = 0;
-    unsigned long long t0 = 0;
-    int ok = 1;
-    while (ld_acquire_u32(g.arrive) < target) {
-      if ((++spins & 255u) == 0u) {
-        if (ld_relaxed_i32(g.err) & kErrTimeout) {
-          ok = 0;
-          break;
-        }
-        const unsigned long long t = global_ns();
-        if (t0 == 0) {
-          t0 = t;
-        } else if (t - t0 > g.limit_ns) {
-          atomicOr(g.err, kErrTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    s_cell_ok = ok;
-    if (g.prof) {
-      const unsigned long long t = global_ns();
-      s_prof[4 + kPhSpmv] += (long long)(t - s_t_last);
-      s_t_last = t;
-    }
-  }
-  __syncthreads();
-  if (!s_cell_ok) return false;
-  if (w == 0) {
-    float tx = 0.f, ty = 0.f, tz = 0.f;
-    for (int b = l; b < g.G; b += 32) {
-      float px, py, pz;
-      load_partial<float, 3>(g.part + slot * g.G + b, px, py, pz);
-      tx += px;
-      ty += py;
-      tz += pz;
-    }
-    tx = warp_sum(tx);
-    ty = warp_sum(ty);
-    tz = warp_sum(tz);
-    if (l == 0) s_cell_res = Sum4<float>{tx, ty, tz, 0.f};
-  }
-  __syncthreads();
-  out = s_cell_res;
-  return true;
-}
-
 // Chronopoulos-Gear Jacobi-PCG on the cell kernels (see above); same contract as pcg_cg.
 template <class TM>
 __device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const float* DI, float* x,
