@@ -608,8 +608,9 @@ def native(args, world, rank, local, pg):
                          + "), fp64 outer FGMRES(30)/Arnoldi/step control",
             "model": "PFC2 (H^-1 flow)" if args.model == 2 else "PFC1 (mobility psi + 1.5)",
             "inner_operator": "structured stencils for M, K, M+dK, M+sqrt(d)K ("
-                              + ("2x2-cell rows; rows off the interior stencil use their class stencil from "
-                                 "shared memory in the inner solves" if variant == 4 else
+                              + ("cell-major rows, 2x2 or 2x2x2 lattice cells; the inner solves read every "
+                                 "stencil from shared memory, cells on the sides with their class's weights"
+                                 if variant == 4 else
                                  "boundary rows assembled SELL-32") + ")",
             "outer_tol": args.outer_tol, "inner_rtol": 1e-3,
             "l2": "inputs larger than L2: matrices + Krylov bases ~3 GB per instance vs 129 MB L2",

@@ -142,16 +142,18 @@ typedef struct {
                          order, hence its results bit for bit, do not depend on what else
                          is in a batch (serving); 0 (default): alone it takes every
                          co-resident block, in a batch a share proportional to its rows */
-  int cells;          /* 2D P2 with structured stencils (inner_operator 1): 1 (default)
-                         numbers the rows by 2 x 2 lattice cells (the four dofs of a cell
-                         are consecutive rows, so a vector moves a cell per 16-byte
-                         access), and the float32/float16 Chronopoulos-Gear inner solves
-                         run one grid barrier per iteration: every block keeps u on its
-                         cells and on the cells its stencils reach in shared memory,
-                         recomputing the halo from its neighbours' r, s, w rather than
-                         waiting for them (same iterates in exact arithmetic); 0: the
-                         lexicographic order.  Ignored elsewhere (3D, P1, assembled
-                         inner matrices). */
+  int cells;          /* P2 with structured stencils (inner_operator 1) and float32/float16
+                         inner solves in the Chronopoulos-Gear form: 1 (default) numbers
+                         the rows by 2 x 2 (2D) or 2 x 2 x 2 (3D) lattice cells (a cell's
+                         dofs are consecutive rows, so a vector moves four of them per
+                         16-byte access), and the inner solves run one grid barrier per
+                         iteration: every block owns a tile of cells and keeps u on it
+                         and on the ring of cells around it in shared memory, recomputing
+                         the ring from its neighbours' r, s, w rather than waiting for
+                         them (same iterates in exact arithmetic); when the tile's window
+                         does not fit in shared memory the context keeps the
+                         lexicographic rows; 0: the lexicographic order.  Ignored
+                         elsewhere (float64, P1, assembled inner matrices). */
 } pfc_options;
 
 typedef struct {
@@ -362,16 +364,16 @@ pfc_status pfc_host_pattern(int dim, int side, double length, int64_t* out4);
 pfc_status pfc_host_partition(int dim, int side, double length, int degree, int nparts, int64_t* row_begin,
                               int64_t* halo, int64_t* part_nnz);
 
-/* Host-only inspection of the 2D P2 cell-major order (no GPU needed; options.cells):
+/* Host-only inspection of the P2 cell-major order (no GPU needed; options.cells; dim 2 or 3):
  * out4 = {row classes (distinct row stencils; the first four are the interior
  * stencils of the dof types, the fifth is the empty stencil of padding rows),
  * stencil entries over all row classes, cell classes (distinct tuples of a 2 x 2
- * cell's four row classes) if the interior stencils extracted from the assembled
- * pattern are the couplings the cell kernels hard-code (cell2d.h) and every other
+ * cell's rows' classes) if the interior stencils extracted from the assembled
+ * pattern are the couplings the cell kernels hard-code (cell2d.h, cell3d.h) and every other
  * row couples to a subset of them, else 0 (the cell kernels then stay off), rows that
  * hold a dof}.  The stencils are those of the P2 matrices of Section 3 on this
  * structured mesh. */
-pfc_status pfc_host_cells(int side, double length, int64_t* out4);
+pfc_status pfc_host_cells(int dim, int side, double length, int64_t* out4);
 
 /* 1 if the context's float32/float16 inner solves run the cell kernels
  * (options.cells with 2D P2 structured stencils, the Chronopoulos-Gear form and room

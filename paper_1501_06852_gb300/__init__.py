@@ -78,7 +78,7 @@ def _load():
         "pfc_selftest_barrier_timeout": (I, [P, D]),
         "pfc_host_pattern": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_host_stencil": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
-        "pfc_host_cells": (I, [I, D, ctypes.POINTER(ctypes.c_int64)]),
+        "pfc_host_cells": (I, [I, I, D, ctypes.POINTER(ctypes.c_int64)]),
         "pfc_cell_kernels": (I, [P]),
         "pfc_host_partition": (I, [I, I, D, I, I, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64)]),
@@ -225,10 +225,10 @@ def host_stencil(dim: int, side: int, length: float = 1.0) -> dict:
     return {"interior_rows": out[0], "boundary_nnz": out[1], "stencil_entries": out[2]}
 
 
-def host_cells(side: int, length: float = 1.0) -> dict:
-    """Row classes of the 2D P2 cell-major order from the host builder (no GPU needed)."""
+def host_cells(side: int, length: float = 1.0, dim: int = 2) -> dict:
+    """Row and cell classes of the P2 cell-major order from the host builder (no GPU needed)."""
     out = (ctypes.c_int64 * 4)()
-    st = lib.pfc_host_cells(side, float(length), out)
+    st = lib.pfc_host_cells(dim, side, float(length), out)
     if st != 0:
         raise PFCError(st, "host_cells")
     return {"classes": out[0], "entries": out[1], "pattern_ok": out[2] > 0, "cell_classes": out[2],

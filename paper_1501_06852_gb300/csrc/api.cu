@@ -82,8 +82,8 @@ struct pfc_ctx {
   int ccls_n = 0;               // cell classes
   double *ccls_wM = nullptr, *ccls_wK = nullptr;
   unsigned char* cellclass = nullptr;
-  int cell_rep[4] = {};         // an interior row of each dof type
-  int cell_gx = 0, cell_gy = 0, cell_wcap = 0, cell_ccap = 0, cell_rcap = 0;   // tiling of its own grid
+  int cell_rep[8] = {};         // an interior row of each dof type
+  int cell_gx = 0, cell_gy = 0, cell_gz = 0, cell_wcap = 0, cell_ccap = 0, cell_rcap = 0;   // tiling of its own grid
   double *mass_tab = nullptr, *stiff_tab = nullptr;
   // float64 matrices
   double *Mv = nullptr, *Kv = nullptr, *Av = nullptr, *MdKv = nullptr, *MsKv = nullptr;
@@ -238,7 +238,9 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   }
   a.cells = (prec != 0 && c->cell_ok) ? 1 : 0;
   a.cell_S = c->cell_S;
+  a.cell_dim = c->dim;
   a.cell_gx = c->cell_gx;
+  a.cell_gz = c->cell_gz;
   a.cell_gy = c->cell_gy;
   a.cell_wcap = c->cell_wcap;
   a.cell_ccap = c->cell_ccap;
@@ -247,45 +249,61 @@ pfc::SolveArgs base_args(pfc_ctx* c, int prec) {
   a.ccls_wM = c->ccls_wM;
   a.ccls_wK = c->ccls_wK;
   a.cellclass = c->cellclass;
-  for (int t = 0; t < 4; ++t) a.cell_rep[t] = c->cell_rep[t];
+  for (int t = 0; t < 8; ++t) a.cell_rep[t] = c->cell_rep[t];
   a.prof = c->timing ? 1 : 0;
   return a;
 }
 
 // Tables of the cell kernels built on the host from the row classes.
 struct CellTables {
-  int ncc = 0;                          // cell classes (class 0: four interior rows)
-  std::vector<unsigned char> cellclass; // n_pad / 4
-  std::vector<double> wM, wK;           // ncc x kCell2dEntries
-  int rep[4] = {-1, -1, -1, -1};        // an interior row of each dof type
+  int ncc = 0;                          // cell classes (class 0: every row interior)
+  std::vector<unsigned char> cellclass; // n_pad / 2^dim
+  std::vector<double> wM, wK;           // ncc x couplings (46 in 2D, 230 in 3D)
+  int rep[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   // an interior row of each dof type
 };
 
-// Whether the cell kernels may run on this cell-major setup, and their tables: the
-// interior stencil of each dof type must be exactly its couplings in cell2d.h, and
-// every other row's stencil a subset of the couplings of its type (true for the rows
-// on the sides of a structured mesh, whose elements are a subset of an interior
-// row's).  A cell's class is the tuple of its four rows' classes; its weights are
-// those of cell2d.h's couplings, 0 where a row lacks one.  At most 255 classes.
-bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
-  const int nt = S.ntypes_dof;
-  const int ncls = (int)S.cls_start.size() - 1;
-  if (!S.cells || nt != 4 || ncls > 255) return false;
-  struct Ent {
-    int t, q, sub;
-  };
-  static const Ent tab[pfc::kCell2dEntries] = {
+// The hard-coded couplings of an interior cell (cell2d.h, cell3d.h): output row type t,
+// source cell q at cell offset (dx, dy, dz), source row sub.
+struct CellEnt {
+  int t, q, sub;
+};
+const std::vector<CellEnt>& cell_entries(int dim) {
+  static const std::vector<CellEnt> e2 = {
 #define PFC_CELL_ENT(t, q, sub) {t, q, sub},
-      PFC_CELL2D_ENTRIES(PFC_CELL_ENT)
+      PFC_CELL2D_ENTRIES(PFC_CELL_ENT)};
+  static const std::vector<CellEnt> e3 = {
+#define PFC_CELL_NOP(q)
+      PFC_CELL3D_ENTRIES(PFC_CELL_ENT, PFC_CELL_NOP)};
+#undef PFC_CELL_NOP
 #undef PFC_CELL_ENT
-  };
-  static const int dxq[pfc::kCell2dSrc] = PFC_CELL2D_DX, dyq[pfc::kCell2dSrc] = PFC_CELL2D_DY;
-  int off[pfc::kCell2dEntries];
-  for (int e = 0; e < pfc::kCell2dEntries; ++e)
-    off[e] = 4 * (dyq[tab[e].q] * S.cell_S + dxq[tab[e].q]) + tab[e].sub - tab[e].t;
+  return dim == 2 ? e2 : e3;
+}
+
+// Whether the cell kernels may run on this cell-major setup, and their tables: the
+// interior stencil of each dof type must be exactly its couplings in cell2d.h /
+// cell3d.h, and every other row's stencil a subset of the couplings of its type (true
+// for the rows on the sides of a structured mesh, whose elements are a subset of an
+// interior row's).  A cell's class is the tuple of its rows' classes; its weights are
+// those of the couplings, 0 where a row lacks one.  At most 255 classes.
+bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
+  const int nt = S.ntypes_dof, dim = S.dim;
+  const int ncls = (int)S.cls_start.size() - 1;
+  if (!S.cells || nt != (1 << dim) || ncls > 255) return false;
+  const std::vector<CellEnt>& tab = cell_entries(dim);
+  static const int dx2[] = PFC_CELL2D_DX, dy2[] = PFC_CELL2D_DY;
+  static const int dx3[] = PFC_CELL3D_DX, dy3[] = PFC_CELL3D_DY, dz3[] = PFC_CELL3D_DZ;
+  const long long cs = S.cell_S;
+  const int E = (int)tab.size();
+  std::vector<long long> off(E);
+  for (int e = 0; e < E; ++e) {
+    const int q = tab[e].q;
+    const long long dc = dim == 2 ? dy2[q] * cs + dx2[q] : (dz3[q] * cs + dy3[q]) * cs + dx3[q];
+    off[e] = nt * dc + tab[e].sub - tab[e].t;
+  }
   // the interior stencils have exactly the couplings of their type
   for (int t = 0; t < nt; ++t) {
     int count = 0;
-    for (int e = 0; e < pfc::kCell2dEntries; ++e) {
+    for (int e = 0; e < E; ++e) {
       if (tab[e].t != t) continue;
       ++count;
       bool found = false;
@@ -295,20 +313,21 @@ bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
     if (count != S.cls_start[t + 1] - S.cls_start[t]) return false;
   }
   CellTables T;
-  std::map<uint32_t, int> ids;
-  auto add_class = [&](uint32_t key) -> bool {
-    for (int t = 0; t < 4; ++t) {
-      const int k = (key >> (8 * t)) & 255u;
+  std::map<uint64_t, int> ids;
+  auto row_class = [&](uint64_t key, int t) { return (int)((key >> (8 * t)) & 255u); };
+  auto add_class = [&](uint64_t key) -> bool {
+    for (int t = 0; t < nt; ++t) {
+      const int k = row_class(key, t);
       int used = 0;
-      for (int e = 0; e < pfc::kCell2dEntries; ++e) {
+      for (int e = 0; e < E; ++e) {
         if (tab[e].t != t) continue;
         for (int j = S.cls_start[k]; j < S.cls_start[k + 1]; ++j)
           if (S.cls_off[j] == off[e]) ++used;
       }
       if (used != S.cls_start[k + 1] - S.cls_start[k]) return false;   // a coupling outside the pattern
     }
-    for (int e = 0; e < pfc::kCell2dEntries; ++e) {
-      const int k = (key >> (8 * tab[e].t)) & 255u;
+    for (int e = 0; e < E; ++e) {
+      const int k = row_class(key, tab[e].t);
       double m = 0.0, kk = 0.0;
       for (int j = S.cls_start[k]; j < S.cls_start[k + 1]; ++j)
         if (S.cls_off[j] == off[e]) {
@@ -322,12 +341,14 @@ bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
     ids.emplace(key, id);
     return true;
   };
-  if (!add_class(0x03020100u)) return false;
-  const int ncell = S.n_pad / 4;
+  uint64_t interior = 0;
+  for (int t = 0; t < nt; ++t) interior |= (uint64_t)t << (8 * t);
+  if (!add_class(interior)) return false;
+  const int ncell = S.n_pad / nt;
   T.cellclass.resize(ncell);
   for (int c = 0; c < ncell; ++c) {
-    const uint32_t key = (uint32_t)S.rowclass[4 * c] | ((uint32_t)S.rowclass[4 * c + 1] << 8) |
-                         ((uint32_t)S.rowclass[4 * c + 2] << 16) | ((uint32_t)S.rowclass[4 * c + 3] << 24);
+    uint64_t key = 0;
+    for (int t = 0; t < nt; ++t) key |= (uint64_t)S.rowclass[(size_t)nt * c + t] << (8 * t);
     auto it = ids.find(key);
     if (it == ids.end()) {
       if (ids.size() >= 255 || !add_class(key)) return false;
@@ -335,7 +356,7 @@ bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
     }
     T.cellclass[c] = (unsigned char)it->second;
     if (it->second == 0 && T.rep[0] < 0)
-      for (int t = 0; t < 4; ++t) T.rep[t] = 4 * c + t;
+      for (int t = 0; t < nt; ++t) T.rep[t] = nt * c + t;
   }
   if (T.rep[0] < 0) return false;   // no interior cell
   T.ncc = (int)ids.size();
@@ -343,30 +364,34 @@ bool cell_pattern_ok(const pfc::HostSetup& S, CellTables* out) {
   return true;
 }
 
-// Tiles of the cell kernels for a grid of G blocks: gx x gy <= G rectangles of the
-// S x S cell grid (block b owns tile (b % gx, b / gx)), chosen to minimise the work of
-// the largest tile: its cells plus its ring of cell_S-independent perimeter cells,
-// which cost about 0.4 of an own cell (four reads against about ten accesses).
-// wcap: cells of the largest tile with its ring; ccap: of the largest tile; rcap: of
-// the largest ring.
-void cell_tiling(int S, int G, int& gx, int& gy, int& wcap, int& ccap, int& rcap) {
+// Tiles of the cell kernels for a grid of G blocks: gx x gy (x gz) <= G boxes of the
+// cell grid (S cells per axis; block b owns tile (b % gx, (b / gx) % gy, b / (gx gy))),
+// chosen to minimise the work of the largest tile: its cells plus its ring, which
+// costs about 0.4 of an own cell (four reads against about ten accesses).  wcap: cells
+// of the largest tile with its ring; ccap: of the largest tile; rcap: of the largest ring.
+void cell_tiling(int dim, int S, int G, int& gx, int& gy, int& gz, int& wcap, int& ccap, int& rcap) {
   double best = 1e300;
-  gx = gy = 1;
-  for (int x = 1; x <= std::min(G, S); ++x) {
-    const int y = std::min(G / x, S);
-    if (y < 1) break;
-    const double tw = (S + x - 1) / x, th = (S + y - 1) / y;
-    const double cost = tw * th + 0.4 * (2 * (tw + 2) + 2 * th);
-    if (cost < best) {
-      best = cost;
-      gx = x;
-      gy = y;
+  gx = gy = gz = 1;
+  for (int z = 1; z <= (dim == 3 ? std::min(G, S) : 1); ++z) {
+    for (int x = 1; x <= std::min(G / z, S); ++x) {
+      const int y = std::min(G / (x * z), S);
+      if (y < 1) break;
+      const double tw = (S + x - 1) / x, th = (S + y - 1) / y, td = dim == 3 ? (S + z - 1) / z : 1;
+      const double own = tw * th * td;
+      const double ring = dim == 3 ? (tw + 2) * (th + 2) * (td + 2) - own : (tw + 2) * (th + 2) - own;
+      const double cost = own + 0.4 * ring;
+      if (cost < best) {
+        best = cost;
+        gx = x;
+        gy = y;
+        gz = z;
+      }
     }
   }
-  const int tw = (S + gx - 1) / gx, th = (S + gy - 1) / gy;
-  wcap = (tw + 2) * (th + 2);
-  ccap = tw * th;
-  rcap = 2 * (tw + 2) + 2 * th;
+  const int tw = (S + gx - 1) / gx, th = (S + gy - 1) / gy, td = dim == 3 ? (S + gz - 1) / gz : 1;
+  wcap = (tw + 2) * (th + 2) * (dim == 3 ? td + 2 : 1);
+  ccap = tw * th * td;
+  rcap = wcap - ccap;
 }
 
 pfc_status status_from_err(int err) {
@@ -731,8 +756,10 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
         pfc_ctx* ck = ctxs[wv.first + i];
         if (!(ck->prec != 0 && ck->cell_ok)) continue;
         int gx = 0, gy = 0, wcap = 0, ccap = 0, rcap = 0;
-        cell_tiling(ck->cell_S, Gs[wv.first + i], gx, gy, wcap, ccap, rcap);
-        dyn = std::max(dyn, pfc::cell_smem_bytes(wcap, rcap, ck->ccls_n, ccap));
+        int gz = 0;
+        cell_tiling(ck->dim, ck->cell_S, Gs[wv.first + i], gx, gy, gz, wcap, ccap, rcap);
+        dyn = std::max(dyn, pfc::cell_smem_bytes(wcap, ck->dim == 3 ? 2 : 1, rcap, ck->ccls_n,
+                                                 ck->dim == 3 ? 232 : 48, ccap));
       }
       if (dyn > 0) {
         int occ_c = 0, blocks = 0;
@@ -756,7 +783,8 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
       a.blk = ck->blk_b;
       if (a.cells) {
         if (cells_fit)
-          cell_tiling(ck->cell_S, Gs[wv.first + i], a.cell_gx, a.cell_gy, a.cell_wcap, a.cell_ccap, a.cell_rcap);
+          cell_tiling(ck->dim, ck->cell_S, Gs[wv.first + i], a.cell_gx, a.cell_gy, a.cell_gz, a.cell_wcap,
+                      a.cell_ccap, a.cell_rcap);
         else a.cells = 0;
       }
       a.stats = ck->stats + sk;
@@ -931,7 +959,7 @@ pfc_status pfc_setup_mesh(pfc_ctx** out, int dim, int side, double length, const
   // stencils, float32/float16 Chronopoulos-Gear inner solves, no staged window);
   // elsewhere, or when the checks below turn the kernels down, lexicographic rows
   // (the per-warp gathers of the other paths are faster in that order).
-  bool try_cells = stencil && c->opt.cells && dim == 2 && c->opt.degree == 2 && c->prec != 0 &&
+  bool try_cells = stencil && c->opt.cells && c->opt.degree == 2 && c->prec != 0 &&
                    c->opt.smem_window == 0 && (c->opt.pcg_variant == 2 || c->opt.pcg_variant == 3);
 retry_layout:
   if (!pfc::build_setup(dim, side, length, S, err, stencil ? 1 : pfc::kSellSigma, c->opt.degree,
@@ -1039,9 +1067,11 @@ retry_layout:
               cell_pattern_ok(S, &ct);
     if (ok) {
       c->ccls_n = ct.ncc;
-      for (int t = 0; t < 4; ++t) c->cell_rep[t] = ct.rep[t];
-      cell_tiling(c->cell_S, c->G, c->cell_gx, c->cell_gy, c->cell_wcap, c->cell_ccap, c->cell_rcap);
-      const size_t dyn = pfc::cell_smem_bytes(c->cell_wcap, c->cell_rcap, c->ccls_n, c->cell_ccap);
+      for (int t = 0; t < 8; ++t) c->cell_rep[t] = ct.rep[t];
+      cell_tiling(dim, c->cell_S, c->G, c->cell_gx, c->cell_gy, c->cell_gz, c->cell_wcap, c->cell_ccap,
+                  c->cell_rcap);
+      const size_t dyn = pfc::cell_smem_bytes(c->cell_wcap, dim == 3 ? 2 : 1, c->cell_rcap, c->ccls_n,
+                                              dim == 3 ? 232 : 48, c->cell_ccap);
       const int need = (c->G + sms - 1) / sms;
       int occ_c = 0;
       ok = pfc::solve_occupancy(c->prec, &occ_c, dyn) == cudaSuccess && occ_c >= need;
@@ -1829,11 +1859,11 @@ pfc_status pfc_host_partition(int dim, int side, double length, int degree, int 
   return PFC_OK;
 }
 
-pfc_status pfc_host_cells(int side, double length, int64_t* out4) {
+pfc_status pfc_host_cells(int dim, int side, double length, int64_t* out4) {
   if (!out4) return PFC_ERR_INVALID;
   pfc::HostSetup S;
   std::string err;
-  if (!pfc::build_setup(2, side, length, S, err, 1, 2, 1)) return PFC_ERR_INVALID;
+  if (!pfc::build_setup(dim, side, length, S, err, 1, 2, 1)) return PFC_ERR_INVALID;
   CellTables T;
   out4[0] = (int64_t)S.cls_start.size() - 1;
   out4[1] = (int64_t)S.cls_off.size();

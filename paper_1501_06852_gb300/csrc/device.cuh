@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "cell2d.h"
+#include "cell3d.h"
 
 namespace pfc {
 
@@ -97,36 +98,37 @@ struct SolveArgs {
   int plane;               // rows per lattice plane (3D: lat^2); 0 in 2D (one window segment)
   int tma_S;               // 3D: shared-memory stride between plane segments (S = plane mod 4)
   int tma_cap;             // floats of one window buffer (two buffers in dynamic shared memory)
-  // cell kernels of the Chronopoulos-Gear inner solves (2D P2 rows in cell-major order,
-  // float inner vectors; pcg_cell in solver.cu): the block keeps u on its cells and
-  // the cells its stencils reach in dynamic shared memory (cell_smem_bytes)
+  // cell kernels of the Chronopoulos-Gear inner solves (P2 rows in cell-major order,
+  // float inner vectors; pcg_cell in solver.cu): the block keeps u on its tile of cells
+  // and the ring around it in dynamic shared memory (cell_smem_bytes)
   int cells;               // 1: on (the host checked the stencils and the shared memory)
-  int cell_S;              // cells per lattice line (side + 1)
-  int cell_gx, cell_gy;    // tiles of the cell grid along x and y (block b owns tile (b % gx, b / gx))
-  int cell_ccap;           // largest tile, in cells (layout of the shared memory)
+  int cell_dim;            // 2 or 3
+  int cell_S;              // cells per lattice axis (side + 1)
+  int cell_gx, cell_gy, cell_gz;  // tiles of the cell grid per axis (block b owns tile
+                                  // (b % gx, (b / gx) % gy, b / (gx gy)))
+  int cell_ccap;           // largest tile, in cells
   int cell_wcap;           // largest tile with its ring, in cells
   int cell_rcap;           // largest ring, in cells
-  int ccls_n;              // cell classes: distinct stencils of a cell's four rows (class 0: all interior)
-  const double* ccls_wM;   // ccls_n x kCell2dEntries: M and K weights of the couplings of cell2d.h
-  const double* ccls_wK;   //   for each cell class (0 where a row lacks the coupling)
-  const unsigned char* cellclass;  // n_pad / 4: class of each cell
-  int cell_rep[4];         // an interior row of each dof type (its Jacobi inverse is the type's)
+  int ccls_n;              // cell classes: distinct stencils of a cell's rows (class 0: all interior)
+  const double* ccls_wM;   // ccls_n x couplings (46 in 2D, 230 in 3D): M and K weights of the
+  const double* ccls_wK;   //   couplings of cell2d.h / cell3d.h (0 where a row lacks one)
+  const unsigned char* cellclass;  // n_pad / 2^dim: class of each cell
+  int cell_rep[8];         // an interior row of each dof type (its Jacobi inverse is the type's)
 };
 
-// Dynamic shared memory of the cell kernels, in this order: the window of u (float4
-// per cell of the tile and its ring), the ring cells {window index, cell or -1}, the
-// coupling weights of the four inner operators for every cell class (kCell2dStride
-// floats each), the classes of the tile's cells.
-constexpr int kCell2dStride = 48;
-__host__ __device__ inline size_t cell_off_ring(int wcap) { return (size_t)wcap * 16; }
-__host__ __device__ inline size_t cell_off_weights(int wcap, int rcap) {
-  return cell_off_ring(wcap) + (((size_t)rcap * 8 + 15) & ~(size_t)15);
+// Dynamic shared memory of the cell kernels, in this order: the window of u (U float4
+// per cell of the tile and its ring; U = 1 in 2D, 2 in 3D), the ring cells {window
+// cell, cell or -1}, the current operator's coupling weights for every cell class
+// (stride floats per class: 48 in 2D, 232 in 3D), the classes of the tile's cells.
+__host__ __device__ inline size_t cell_off_ring(int wcap, int U) { return (size_t)wcap * U * 16; }
+__host__ __device__ inline size_t cell_off_weights(int wcap, int U, int rcap) {
+  return cell_off_ring(wcap, U) + (((size_t)rcap * 8 + 15) & ~(size_t)15);
 }
-__host__ __device__ inline size_t cell_off_classes(int wcap, int rcap, int ncc) {
-  return cell_off_weights(wcap, rcap) + (size_t)4 * ncc * kCell2dStride * 4;
+__host__ __device__ inline size_t cell_off_classes(int wcap, int U, int rcap, int ncc, int stride) {
+  return cell_off_weights(wcap, U, rcap) + (size_t)ncc * stride * 4;
 }
-__host__ __device__ inline size_t cell_smem_bytes(int wcap, int rcap, int ncc, int ccap) {
-  return cell_off_classes(wcap, rcap, ncc) + (((size_t)ccap + 15) & ~(size_t)15);
+__host__ __device__ inline size_t cell_smem_bytes(int wcap, int U, int rcap, int ncc, int stride, int ccap) {
+  return cell_off_classes(wcap, U, rcap, ncc, stride) + (((size_t)ccap + 15) & ~(size_t)15);
 }
 
 // A batched launch: instance k (arguments inst[k], in device memory) owns the

@@ -15,8 +15,8 @@
 // coalesced and a vector update touches 32 consecutive rows per warp.  Without
 // structured stencils rows are sorted by length (descending) inside windows of
 // kSellSigma lexicographic rows; with them (sigma = 1) the order is lexicographic,
-// or, for 2D P2 with cells = 1, cell-major (2 x 2 lattice cells of four consecutive
-// rows, cell2d.h).  Padding rows hold no dof; padding slots point at their own row
+// or, for P2 with cells = 1, cell-major (2 x 2 or 2 x 2 x 2 lattice cells of four or
+// eight consecutive rows, cell2d.h / cell3d.h).  Padding rows hold no dof; padding slots point at their own row
 // with value 0.
 #include <algorithm>
 #include <cstring>
@@ -132,22 +132,27 @@ bool build_setup(int dim, int side, double length, HostSetup& S, std::string& er
   // perm: internal row -> lexicographic dof, -1 for the padding rows.
   // SELL-32-sigma: rows sorted by length inside windows of sigma lexicographic rows
   // (sigma = 1 with structured stencils: lexicographic, padding rows at the end), or
-  // cell-major (2D P2 with structured stencils and cells = 1): row 4 c + sub holds
-  // lattice point (2 cx + (sub & 1), 2 cy + (sub >> 1)) of cell c = cy (side + 1) + cx;
-  // the points with x or y = 2 side + 1 and the rows past the last cell are padding.
+  // cell-major (P2 with structured stencils and cells = 1): in 2D row 4 c + sub holds
+  // lattice point (2 cx + (sub & 1), 2 cy + (sub >> 1)) of cell c = cy (side + 1) + cx,
+  // in 3D row 8 c + sub likewise with z; the points with a coordinate 2 side + 1 and the
+  // rows past the last cell are padding.
   S.iperm.assign(n, -1);
-  S.cells = (cells && dim == 2 && degree == 2 && S.sigma == 1) ? 1 : 0;
+  S.cells = (cells && degree == 2 && S.sigma == 1) ? 1 : 0;
   if (S.cells) {
-    const int64_t cs = side + 1, ncell = cs * cs;
+    // 2^dim rows per cell: row cr c + sub holds (2 cx + (sub & 1), 2 cy + ((sub >> 1) & 1),
+    // 2 cz + (sub >> 2)) of cell c = (cz cs + cy) cs + cx
+    const int64_t cs = side + 1, cr = dim == 2 ? 4 : 8, ncell = dim == 2 ? cs * cs : cs * cs * cs;
     S.cell_S = (int)cs;
-    S.n_pad = (int)((4 * ncell + kSellC - 1) / kSellC * kSellC);
+    S.n_pad = (int)((cr * ncell + kSellC - 1) / kSellC * kSellC);
     S.perm.assign(S.n_pad, -1);
-    for (int64_t p = 0; p < 4 * ncell; ++p) {
-      const int64_t c = p >> 2, sub = p & 3;
-      const int64_t x = 2 * (c % cs) + (sub & 1), y = 2 * (c / cs) + (sub >> 1);
-      if (x < lat && y < lat) {
-        S.perm[p] = (int)(y * lat + x);
-        S.iperm[y * lat + x] = (int)p;
+    for (int64_t p = 0; p < cr * ncell; ++p) {
+      const int64_t c = p / cr, sub = p % cr;
+      const int64_t x = 2 * (c % cs) + (sub & 1), y = 2 * ((c / cs) % cs) + ((sub >> 1) & 1);
+      const int64_t z = dim == 3 ? 2 * (c / (cs * cs)) + (sub >> 2) : 0;
+      if (x < lat && y < lat && z < (dim == 3 ? lat : 1)) {
+        const int64_t i = (z * lat + y) * lat + x;
+        S.perm[p] = (int)i;
+        S.iperm[i] = (int)p;
       }
     }
   } else {

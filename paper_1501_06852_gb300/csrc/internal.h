@@ -64,9 +64,9 @@ struct HostSetup {
   std::vector<int> st_off;
   std::vector<double> st_wM, st_wK;
   std::vector<unsigned char> rowinfo;  // n_pad: bits 0-2 dof type, bit 3 interior
-  // Cell-major row order (2D P2 with structured stencils, cells = 1; cell2d.h):
-  // row 4 c + sub holds lattice point (2 cx + (sub & 1), 2 cy + (sub >> 1)) of cell
-  // c = cy cell_S + cx.  Row classes (built in that order only): every row's stencil
+  // Cell-major row order (P2 with structured stencils, cells = 1; cell2d.h, cell3d.h):
+  // row 2^dim c + sub holds lattice point (2 cx + (sub & 1), 2 cy + ((sub >> 1) & 1),
+  // 2 cz + (sub >> 2)) of cell c = (cz cell_S + cy) cell_S + cx.  Row classes (built in that order only): every row's stencil
   // (column offsets with its M and K weights); class t < ntypes_dof is the interior
   // stencil of dof type t, class ntypes_dof has no entries (rows that hold no dof),
   // the others are the distinct stencils of the rows with a missing element.

@@ -1452,21 +1452,20 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
 
 // ---------------------------------------------------------------------------
 // Cell kernels: Chronopoulos-Gear Jacobi-PCG with one grid barrier per iteration
-// (2D P2 rows in cell-major order, float inner vectors; cell2d.h).
+// (P2 rows in cell-major order, float inner vectors; cell2d.h, cell3d.h).
 //
-// Every vector is read and written a float4 (one lattice cell, four rows) at a time.
-// For these phases the cell grid (cell_S x cell_S cells) is cut into cell_gx x
-// cell_gy rectangular tiles, tile (b mod gx, b / gx) owned by block b (blocks past
-// gx gy own none).  A block keeps the preconditioned residual u of its tile and of
-// the ring of cells around it (every cell its rows' stencils reach) in a
-// shared-memory window, so the product w = A u reads no global memory.  Instead of
-// a grid barrier that would publish u before the product, the block recomputes u on
-// the ring itself from the owners' r, s and w of the previous iteration with the
-// same arithmetic the owners use (so the values agree bit for bit); r, s and w
-// alternate between two buffers, so that an owner writing iteration k + 1 never
-// overwrites what a neighbour still reads for iteration k.  A tile's ring is its
-// perimeter (a strip of rows would need two whole lattice lines of cells).  One
-// iteration:
+// A cell is 2 x 2 (2D) or 2 x 2 x 2 (3D) lattice points, its rows consecutive, so a
+// vector is read and written one float4 "unit" (four rows) at a time: U = 1 unit per
+// cell in 2D, 2 in 3D.  For these phases the cell grid (cell_S cells per axis) is cut
+// into cell_gx x cell_gy (x cell_gz) boxes, tile (b % gx, (b / gx) % gy, b / (gx gy))
+// owned by block b (blocks past gx gy gz own none).  A block keeps the preconditioned
+// residual u of its tile and of the ring of cells around it (every cell its rows'
+// stencils reach) in a shared-memory window, so the product w = A u reads no global
+// memory.  Instead of a grid barrier that would publish u before the product, the
+// block recomputes u on the ring itself from the owners' r, s and w of the previous
+// iteration with the same arithmetic the owners use (so the values agree bit for
+// bit); r, s and w alternate between two buffers, so that an owner writing iteration
+// k + 1 never overwrites what a neighbour still reads for iteration k.  One iteration:
 //   phase A, tile: p = u + b p, s' = w + b s, x += a p, r' = r - a s', u' = D r'
 //           (partials (r', r'), (r', u')); ring: s', r', u' as above, u' only kept
 //   phase B, tile: w' = A u' from the window (partial (w', u'))
@@ -1474,133 +1473,166 @@ __device__ __noinline__ bool pcg_cg(Grid& g, const SolveArgs& a, const TM* AV, i
 //   b = g' / g, a = g' / (d' - b g' / a)
 // The iterates are those of pcg_cg; its separate (r, r) barrier is gone (the test
 // comes one product later, after the same iterate x).  Every cell runs the couplings
-// of cell2d.h with the weights of its cell class (interior cells: class 0).  The
-// set-up before the loop (r = b etc.) and the caller's use of x go by the block's
-// slices as everywhere else; the grid barriers in between order the two ownerships.
+// of cell2d.h / cell3d.h with the weights of its cell class (interior cells: class 0;
+// a coupling a row lacks has weight 0).  The set-up before the loop (r = b etc.) and
+// the caller's use of x go by the block's slices as everywhere else; the grid barriers
+// in between order the two ownerships.
 
-struct CellMem {
-  float4* win;               // u on the tile and its ring, (tw + 2) x (th + 2) cells
-  const int2* ring;          // ring cell j: {window index, cell index or -1 outside the grid}
-  const float* wts;          // 4 operators x ccls_n x kCell2dStride coupling weights
-  const unsigned char* cc;   // class of each tile cell, tile order
+template <int DIM> struct CellDim;
+template <> struct CellDim<2> {
+  static constexpr int U = 1, E = kCell2dEntries, stride = 48;
 };
+template <> struct CellDim<3> {
+  static constexpr int U = 2, E = kCell3dEntries, stride = 232;
+};
+__host__ __device__ constexpr int cell_stride(int dim) { return dim == 2 ? 48 : 232; }
 
-__device__ __forceinline__ CellMem cell_mem(const SolveArgs& a) {
-  char* base = reinterpret_cast<char*>(s_win);
-  CellMem m;
-  m.win = reinterpret_cast<float4*>(base);
-  m.ring = reinterpret_cast<const int2*>(base + cell_off_ring(a.cell_wcap));
-  m.wts = reinterpret_cast<const float*>(base + cell_off_weights(a.cell_wcap, a.cell_rcap));
-  m.cc = reinterpret_cast<const unsigned char*>(base + cell_off_classes(a.cell_wcap, a.cell_rcap, a.ccls_n));
-  return m;
-}
-
-
-// This block's tile: cells (cx, cy) with x0 <= cx < x0 + tw, y0 <= cy < y0 + th; tile
-// cell k = (cx - x0) + (cy - y0) tw sits at window index (k mod tw + 1) + (k / tw + 1) ws.
-// dq, dr: kThreads = dq tw + dr (the walk's step); inv_tw = 1 / tw.
+// This block's tile: cells (x0 + i, y0 + j, z0 + l), i < tw, j < th, l < td (td = 1,
+// z0 = 0 in 2D).  Window coordinates (lx, ly, lz) = (i + 1, j + 1, l + wz) with wz = 1
+// in 3D, 0 in 2D; window cell index lx + ly sx + lz sxy.  The walk over the tile cells
+// k = threadIdx.x, + kThreads, ... steps by (dx, dy, dz) with kThreads = (dz th + dy) tw
+// + dx; inv_tw, inv_th are the float reciprocals for the first quotients.
 struct CellTile {
-  int x0, y0, tw, th, ws, own, ring, dq, dr;
-  float inv_tw;
+  int x0, y0, z0, tw, th, td, wz, sx, sxy, own, win, ring, dx, dy, dz;
+  float inv_tw, inv_th;
 };
 __shared__ CellTile s_tile;   // set once per launch (cell_tables)
+__shared__ int s_ring_n;
+__device__ __forceinline__ const CellTile& cell_tile() { return s_tile; }
 
 __device__ __forceinline__ CellTile cell_tile_of(const Grid& g, const SolveArgs& a) {
   CellTile t;
-  const int gx = a.cell_gx, gy = a.cell_gy, S = a.cell_S;
-  const bool has = g.bid < gx * gy;
-  const int ix = has ? g.bid % gx : 0, iy = has ? g.bid / gx : 0;
+  const int gx = a.cell_gx, gy = a.cell_gy, gz = a.cell_dim == 3 ? a.cell_gz : 1, S = a.cell_S;
+  const bool has = g.bid < gx * gy * gz;
+  const int ix = has ? g.bid % gx : 0, iy = has ? (g.bid / gx) % gy : 0, iz = has ? g.bid / (gx * gy) : 0;
   t.x0 = (int)((long long)ix * S / gx);
   t.y0 = (int)((long long)iy * S / gy);
+  t.z0 = a.cell_dim == 3 ? (int)((long long)iz * S / gz) : 0;
   t.tw = has ? (int)((long long)(ix + 1) * S / gx) - t.x0 : 0;
   t.th = has ? (int)((long long)(iy + 1) * S / gy) - t.y0 : 0;
-  t.ws = t.tw + 2;
-  t.own = t.tw * t.th;
-  t.ring = t.own > 0 ? 2 * (t.tw + 2) + 2 * t.th : 0;
-  t.dq = t.tw > 0 ? kThreads / t.tw : 0;
-  t.dr = t.tw > 0 ? kThreads % t.tw : 0;
+  t.td = !has ? 0 : a.cell_dim == 3 ? (int)((long long)(iz + 1) * S / gz) - t.z0 : 1;
+  t.wz = a.cell_dim == 3 ? 1 : 0;
+  t.sx = t.tw + 2;
+  t.sxy = (t.tw + 2) * (t.th + 2);
+  t.own = t.tw * t.th * t.td;
+  t.win = t.own > 0 ? t.sxy * (t.td + 2 * t.wz) : 0;
+  t.ring = t.win - t.own;
+  const int plane = t.tw * t.th;
+  t.dz = plane > 0 ? kThreads / plane : 0;
+  const int rem = plane > 0 ? kThreads - t.dz * plane : 0;
+  t.dy = t.tw > 0 ? rem / t.tw : 0;
+  t.dx = t.tw > 0 ? rem - t.dy * t.tw : 0;
   t.inv_tw = t.tw > 0 ? 1.0f / (float)t.tw : 0.f;
+  t.inv_th = t.th > 0 ? 1.0f / (float)t.th : 0.f;
   return t;
 }
-__device__ __forceinline__ const CellTile& cell_tile() { return s_tile; }
 
-// Walks the tile cells k = threadIdx.x, + kThreads, ... of the block's tile: (lx, ly)
-// are the window coordinates (tile cell k at (k mod tw + 1, k / tw + 1)), advanced
-// without a division.  The first quotient comes from the float reciprocal: (k + 1/2) /
-// tw lies at least 1/(2 tw) from an integer and k < 2^10, so the rounding of one
-// float product cannot cross one.
+// Walks the tile cells k = threadIdx.x, + kThreads, ... of the block's tile without a
+// division per cell.  The first quotients come from float reciprocals: (k + 1/2) / n
+// lies at least 1/(2n) from an integer and k < 2^10, so the rounding of one float
+// product cannot cross one.  In 2D a tile cell never needs the z carry (k < tw th).
+template <int DIM>
 struct TileWalk {
-  int lx, ly, dq, dr, tw;
-  __device__ __forceinline__ explicit TileWalk(const CellTile& t) : dq(t.dq), dr(t.dr), tw(t.tw) {
+  int lx, ly, lz;
+  __device__ __forceinline__ explicit TileWalk(const CellTile& t) {
     const int k0 = threadIdx.x;
-    const int q = __float2int_rz(((float)k0 + 0.5f) * t.inv_tw);
-    ly = q + 1;
-    lx = k0 - q * t.tw + 1;
-  }
-  __device__ __forceinline__ void next() {
-    lx += dr;
-    ly += dq;
-    if (lx > tw) {
-      lx -= tw;
-      ly += 1;
+    const int q1 = __float2int_rz(((float)k0 + 0.5f) * t.inv_tw);
+    lx = k0 - q1 * t.tw + 1;
+    if constexpr (DIM == 3) {
+      const int q2 = __float2int_rz(((float)q1 + 0.5f) * t.inv_th);
+      ly = q1 - q2 * t.th + 1;
+      lz = q2 + 1;
+    } else {
+      ly = q1 + 1;
+      lz = 0;
     }
+  }
+  __device__ __forceinline__ void next(const CellTile& t) {
+    if constexpr (DIM == 3) {
+      lx += t.dx;
+      if (lx > t.tw) {
+        lx -= t.tw;
+        ly += 1;
+      }
+      ly += t.dy;
+      if (ly > t.th) {
+        ly -= t.th;
+        lz += 1;
+      }
+      lz += t.dz;
+    } else {
+      // kThreads = q tw + r with q = dz th + dy, r = dx
+      lx += t.dx;
+      ly += t.dz * t.th + t.dy;
+      if (lx > t.tw) {
+        lx -= t.tw;
+        ly += 1;
+      }
+    }
+  }
+  __device__ __forceinline__ int wi(const CellTile& t) const {
+    return DIM == 3 ? lx + ly * t.sx + lz * t.sxy : lx + ly * t.sx;
+  }
+  __device__ __forceinline__ int cell(const CellTile& t, int S) const {
+    return DIM == 3 ? ((t.z0 - 1 + lz) * S + (t.y0 - 1 + ly)) * S + (t.x0 - 1 + lx) : (t.y0 - 1 + ly) * S + (t.x0 - 1 + lx);
   }
 };
-// Ring cell j: the row below the tile, the row above (tw + 2 each, corners
-// included), then the column left of it and the column right (th each).
-__device__ __forceinline__ void ring_cell(const CellTile& t, int j, int& lx, int& ly) {
-  if (j < t.ws) {
-    lx = j;
-    ly = 0;
-  } else if (j < 2 * t.ws) {
-    lx = j - t.ws;
-    ly = t.th + 1;
-  } else if (j < 2 * t.ws + t.th) {
-    lx = 0;
-    ly = j - 2 * t.ws + 1;
-  } else {
-    lx = t.tw + 1;
-    ly = j - 2 * t.ws - t.th + 1;
-  }
+
+// Dynamic shared memory of the cell kernels (layout: cell_smem_bytes).
+struct CellMem {
+  float4* win;               // u: U float4 per window cell
+  const int2* ring;          // ring cell j: {window cell, cell index or -1 outside the grid}
+  float* wts;                // the current operator's coupling weights, one row per cell class
+  const unsigned char* cc;   // class of each tile cell, tile order
+};
+__device__ __forceinline__ CellMem cell_mem(const SolveArgs& a) {
+  char* base = reinterpret_cast<char*>(s_win);
+  const int U = a.cell_dim == 3 ? 2 : 1;
+  CellMem m;
+  m.win = reinterpret_cast<float4*>(base);
+  m.ring = reinterpret_cast<const int2*>(base + cell_off_ring(a.cell_wcap, U));
+  m.wts = reinterpret_cast<float*>(base + cell_off_weights(a.cell_wcap, U, a.cell_rcap));
+  m.cc = reinterpret_cast<const unsigned char*>(
+      base + cell_off_classes(a.cell_wcap, U, a.cell_rcap, a.ccls_n, cell_stride(a.cell_dim)));
+  return m;
 }
 
-// Fills the tables of the cell kernels and zeroes the window cells outside the cell
-// grid (read with weight 0 by the cells on its edges, never written); called by all
-// threads at the start of a launch.
+// Fills the tile record, the ring list and the tile's cell classes, and zeroes the
+// window cells outside the cell grid (read with weight 0 by the cells on its edges,
+// never written); called by all threads at the start of a launch.
 __device__ void cell_tables(const Grid& g, const SolveArgs& a) {
   char* base = reinterpret_cast<char*>(s_win);
-  int2* ring = reinterpret_cast<int2*>(base + cell_off_ring(a.cell_wcap));
-  float* wts = reinterpret_cast<float*>(base + cell_off_weights(a.cell_wcap, a.cell_rcap));
-  unsigned char* cc = reinterpret_cast<unsigned char*>(base + cell_off_classes(a.cell_wcap, a.cell_rcap, a.ccls_n));
-  const int per_op = a.ccls_n * kCell2dStride;
-  for (int k = threadIdx.x; k < 4 * per_op; k += kThreads) {
-    const int op = k / per_op, r = k - op * per_op, cls = r / kCell2dStride, e = r - cls * kCell2dStride;
-    float w = 0.f;
-    if (e < kCell2dEntries) {
-      const int j = cls * kCell2dEntries + e;
-      w = (float)(a.op_cM[op] * __ldg(a.ccls_wM + j) + a.op_cK[op] * __ldg(a.ccls_wK + j));
-    }
-    wts[k] = w;
-  }
+  const int U = a.cell_dim == 3 ? 2 : 1;
+  int2* ring = reinterpret_cast<int2*>(base + cell_off_ring(a.cell_wcap, U));
+  unsigned char* cc = reinterpret_cast<unsigned char*>(
+      base + cell_off_classes(a.cell_wcap, U, a.cell_rcap, a.ccls_n, cell_stride(a.cell_dim)));
   const CellTile t = cell_tile_of(g, a);
-  if (threadIdx.x == 0) s_tile = t;
+  if (threadIdx.x == 0) {
+    s_tile = t;
+    s_ring_n = 0;
+  }
+  __syncthreads();
   const int S = a.cell_S;
-  for (int k = threadIdx.x; k < t.own; k += kThreads) {
-    const int cx = t.x0 + k % t.tw, cy = t.y0 + k / t.tw;
-    cc[k] = __ldg(a.cellclass + (size_t)cy * S + cx);
-  }
-  for (int j = threadIdx.x; j < t.ring; j += kThreads) {
-    int lx, ly;
-    ring_cell(t, j, lx, ly);
-    const int cx = t.x0 - 1 + lx, cy = t.y0 - 1 + ly;
-    const bool in = cx >= 0 && cx < S && cy >= 0 && cy < S;
-    ring[j] = make_int2(lx + ly * t.ws, in ? cy * S + cx : -1);
-  }
   float4* win = reinterpret_cast<float4*>(base);
-  const int nw = t.own > 0 ? t.ws * (t.th + 2) : 0;
-  for (int k = threadIdx.x; k < nw; k += kThreads) {
-    const int cx = t.x0 - 1 + k % t.ws, cy = t.y0 - 1 + k / t.ws;
-    if (cx < 0 || cx >= S || cy < 0 || cy >= S) win[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = threadIdx.x; k < t.win; k += kThreads) {
+    const int lx = k % t.sx, ly = (k / t.sx) % (t.th + 2), lz = k / t.sxy;
+    const int cx = t.x0 - 1 + lx, cy = t.y0 - 1 + ly, cz = t.z0 - t.wz + lz;
+    const bool inside_tile = lx >= 1 && lx <= t.tw && ly >= 1 && ly <= t.th && lz >= t.wz && lz < t.wz + t.td;
+    const bool in_grid = cx >= 0 && cx < S && cy >= 0 && cy < S && cz >= 0 && cz < (t.wz ? S : 1);
+    if (!in_grid)
+      for (int h = 0; h < U; ++h) win[U * k + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!inside_tile) {
+      // the order of the ring list does not matter: each ring cell is computed alone
+      const int j = atomicAdd(&s_ring_n, 1);
+      ring[j] = make_int2(k, in_grid ? (cz * S + cy) * S + cx : -1);
+    }
+  }
+  if (a.cell_dim == 3) {
+    TileWalk<3> tk(t);
+    for (int k = threadIdx.x; k < t.own; k += kThreads, tk.next(t)) cc[k] = __ldg(a.cellclass + tk.cell(t, S));
+  } else {
+    TileWalk<2> tk(t);
+    for (int k = threadIdx.x; k < t.own; k += kThreads, tk.next(t)) cc[k] = __ldg(a.cellclass + tk.cell(t, S));
   }
 }
 
@@ -1614,8 +1646,12 @@ template <int K>
 __device__ __forceinline__ float comp4(float4 v) {
   return K == 0 ? v.x : K == 1 ? v.y : K == 2 ? v.z : v.w;
 }
+template <int K>
+__device__ __forceinline__ float comp8(float4 lo, float4 hi) {
+  return K < 4 ? comp4<K & 3>(lo) : comp4<K & 3>(hi);
+}
 
-// s' = w + b s, r' = r - a s', u' = D r' on one cell: the one formula the owner and
+// s' = w + b s, r' = r - a s', u' = D r' on one unit: the one formula the owner and
 // the blocks that hold the cell in their ring both evaluate.
 __device__ __forceinline__ void cell_rsu(float4 w, float4 sv, float4 r, float4 d, float al, float be, float4& s1,
                                          float4& r1, float4& u1) {
@@ -1624,8 +1660,8 @@ __device__ __forceinline__ void cell_rsu(float4 w, float4 sv, float4 r, float4 d
   u1 = make_float4(d.x * r1.x, d.y * r1.y, d.z * r1.z, d.w * r1.w);
 }
 
-// Inner vector k of the cell kernels (float4 per cell).  r, s and w alternate
-// between two buffers: iteration parity cur reads buffer cur and writes buffer !cur.
+// Inner vector k of the cell kernels (float4 units).  r, s and w alternate between two
+// buffers: iteration parity cur reads buffer cur and writes buffer !cur.
 __device__ __forceinline__ float4* cvec(const SolveArgs& a, int k) {
   return reinterpret_cast<float4*>((float*)a.ivec + (size_t)k * a.n_pad);
 }
@@ -1633,44 +1669,67 @@ __device__ __forceinline__ int cell_r(int cur) { return cur ? kVu : kVr; }
 __device__ __forceinline__ int cell_s(int cur) { return cur ? kVq : kVs; }
 __device__ __forceinline__ int cell_w(int cur) { return cur ? kVm0 : kVw; }
 
-// Jacobi inverse of a ring cell: the interior types' values for a cell of class 0
-// (the rule the owner applies), else the cell's own.
-__device__ __forceinline__ float4 ring_d(const SolveArgs& a, const float4* di, float4 dint, int c) {
-  return __ldg(a.cellclass + c) == 0 ? dint : di[c];
+// The current operator's coupling weights for every cell class into shared memory
+// (one row of cell_stride floats per class); called by all threads before the first
+// product of an inner solve.
+__device__ __forceinline__ void cell_weights(const SolveArgs& a, int op) {
+  const CellMem m = cell_mem(a);
+  const int stride = cell_stride(a.cell_dim), E = a.cell_dim == 3 ? kCell3dEntries : kCell2dEntries;
+  const double cM = a.op_cM[op], cK = a.op_cK[op];
+  for (int k = threadIdx.x; k < a.ccls_n * stride; k += kThreads) {
+    const int cls = k / stride, e = k - cls * stride;
+    float w = 0.f;
+    if (e < E) w = (float)(cM * __ldg(a.ccls_wM + cls * E + e) + cK * __ldg(a.ccls_wK + cls * E + e));
+    m.wts[k] = w;
+  }
+}
+
+// Jacobi inverse of unit h of cell c of class cls: the interior types' values for class
+// 0 (the rule owner and ring both apply; d0, d1 for units 0 and 1), else the cell's own.
+__device__ __forceinline__ float4 cell_d(int cls, const float4* di, float4 d0, float4 d1, int unit, int h) {
+  return cls == 0 ? (h == 0 ? d0 : d1) : di[unit];
 }
 
 // u = D r on the tile and its ring (the window); partial (r, u) on the tile.
-__device__ __forceinline__ void cell_fill(const Grid& g, const SolveArgs& a, const float4* r, const float4* di,
-                                          float4 dint, float& pg) {
+template <int DIM>
+__device__ __forceinline__ void cell_fill(const SolveArgs& a, const float4* r, const float4* di, float4 d0, float4 d1,
+                                          float& pg) {
   const CellMem m = cell_mem(a);
   const CellTile& t = cell_tile();
+  constexpr int U = CellDim<DIM>::U;
   const int S = a.cell_S;
-  TileWalk tk(t);
-  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next()) {
-    int wi, c;
+  TileWalk<DIM> tk(t);
+  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next(t)) {
+    int wi, c, cls;
     if (k < t.own) {
-      wi = tk.lx + tk.ly * t.ws;
-      c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx);
+      wi = tk.wi(t);
+      c = tk.cell(t, S);
+      cls = m.cc[k];
     } else {
-      const int2 rc = m.ring[k - t.own];
-      wi = rc.x;
-      c = rc.y;
+      const int2 rg = m.ring[k - t.own];
+      wi = rg.x;
+      c = rg.y;
       if (c < 0) continue;
+      cls = __ldg(a.cellclass + c);
     }
-    const float4 rv = r[c];
-    const float4 d = k < t.own ? (m.cc[k] == 0 ? dint : di[c]) : ring_d(a, di, dint, c);
-    const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
-    m.win[wi] = u;
-    if (k < t.own) pg = dot4(rv, u, pg);
+#pragma unroll
+    for (int h = 0; h < U; ++h) {
+      const float4 rv = r[U * c + h], d = cell_d(cls, di, d0, d1, U * c + h, h);
+      const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
+      m.win[U * wi + h] = u;
+      if (k < t.own) pg = dot4(rv, u, pg);
+    }
   }
 }
 
 // Phase A of one iteration (see above): reads r, s, w of parity cur, writes those of
 // !cur, updates p and x, keeps u' in the window.
-__device__ __forceinline__ void cell_phase_a(const Grid& g, const SolveArgs& a, float al, float be, int cur,
-                                             float4* x, const float4* di, float4 dint, float& prr, float& pg) {
+template <int DIM>
+__device__ __forceinline__ void cell_phase_a(const SolveArgs& a, float al, float be, int cur, float4* x,
+                                             const float4* di, float4 d0, float4 d1, float& prr, float& pg) {
   const CellMem m = cell_mem(a);
   const CellTile& t = cell_tile();
+  constexpr int U = CellDim<DIM>::U;
   const int S = a.cell_S;
   float4* const pv = cvec(a, kVp);
   const float4* const rc = cvec(a, cell_r(cur));
@@ -1678,72 +1737,111 @@ __device__ __forceinline__ void cell_phase_a(const Grid& g, const SolveArgs& a, 
   const float4* const wc = cvec(a, cell_w(cur));
   float4* const rn = cvec(a, cell_r(cur ^ 1));
   float4* const sn = cvec(a, cell_s(cur ^ 1));
-  TileWalk tk(t);
-  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next()) {
+  TileWalk<DIM> tk(t);
+  for (int k = threadIdx.x; k < t.own + t.ring; k += kThreads, tk.next(t)) {
     if (k < t.own) {
-      const int c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx), wi = tk.lx + tk.ly * t.ws;
-      const float4 u = m.win[wi];
-      const float4 p = pv[c], w = wc[c], sv = sc[c], r = rc[c], xx = x[c];
-      // a cell of four interior rows (class 0) has the Jacobi inverses of the interior dof types
-      const float4 d = m.cc[k] == 0 ? dint : di[c];
-      float4 s1, r1, u1;
-      cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
-      const float4 p1 = make_float4(fmaf(be, p.x, u.x), fmaf(be, p.y, u.y), fmaf(be, p.z, u.z), fmaf(be, p.w, u.w));
-      pv[c] = p1;
-      sn[c] = s1;
-      rn[c] = r1;
-      x[c] = make_float4(fmaf(al, p1.x, xx.x), fmaf(al, p1.y, xx.y), fmaf(al, p1.z, xx.z), fmaf(al, p1.w, xx.w));
-      m.win[wi] = u1;
-      prr = dot4(r1, r1, prr);
-      pg = dot4(r1, u1, pg);
+      const int c = tk.cell(t, S), wi = tk.wi(t), cls = m.cc[k];
+#pragma unroll 1
+      for (int h = 0; h < U; ++h) {
+        const int un = U * c + h, wu = U * wi + h;
+        const float4 u = m.win[wu];
+        const float4 p = pv[un], w = wc[un], sv = sc[un], r = rc[un], xx = x[un];
+        // a cell of interior rows (class 0) has the Jacobi inverses of the interior dof types
+        const float4 d = cell_d(cls, di, d0, d1, un, h);
+        float4 s1, r1, u1;
+        cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+        const float4 p1 = make_float4(fmaf(be, p.x, u.x), fmaf(be, p.y, u.y), fmaf(be, p.z, u.z), fmaf(be, p.w, u.w));
+        pv[un] = p1;
+        sn[un] = s1;
+        rn[un] = r1;
+        x[un] = make_float4(fmaf(al, p1.x, xx.x), fmaf(al, p1.y, xx.y), fmaf(al, p1.z, xx.z), fmaf(al, p1.w, xx.w));
+        m.win[wu] = u1;
+        prr = dot4(r1, r1, prr);
+        pg = dot4(r1, u1, pg);
+      }
     } else {
       const int2 rg = m.ring[k - t.own];
       const int c = rg.y;
       if (c < 0) continue;
-      const float4 w = wc[c], sv = sc[c], r = rc[c], d = ring_d(a, di, dint, c);
-      float4 s1, r1, u1;
-      cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
-      m.win[rg.x] = u1;
+      const int cls = __ldg(a.cellclass + c);
+#pragma unroll 1
+      for (int h = 0; h < U; ++h) {
+        const int un = U * c + h;
+        const float4 w = wc[un], sv = sc[un], r = rc[un], d = cell_d(cls, di, d0, d1, un, h);
+        float4 s1, r1, u1;
+        cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
+        m.win[U * rg.x + h] = u1;
+      }
     }
   }
 }
 
 // Phase B: w = A_op u on the tile from the window; partial (w, u).  Every cell runs
-// the couplings of cell2d.h with the weights of its class (interior cells all read
-// the class-0 row, a broadcast); a coupling a row lacks has weight 0, and the window
-// cells outside the cell grid hold zeros.
-__device__ __forceinline__ void cell_phase_b(const Grid& g, const SolveArgs& a, int op, float4* wn, float& pd) {
+// the couplings of cell2d.h / cell3d.h with the weights of its class (interior cells
+// all read the class-0 row, a broadcast); the window cells outside the cell grid hold
+// zeros.
+template <int DIM>
+__device__ __forceinline__ void cell_phase_b(const SolveArgs& a, float4* wn, float& pd) {
   const CellMem m = cell_mem(a);
   const CellTile& t = cell_tile();
-  const int S = a.cell_S, ws = t.ws;
-  const float* wop = m.wts + op * a.ccls_n * kCell2dStride;
-  TileWalk tk(t);
-  for (int k = threadIdx.x; k < t.own; k += kThreads, tk.next()) {
-    const int c = (t.y0 - 1 + tk.ly) * S + (t.x0 - 1 + tk.lx), wi = tk.lx + tk.ly * ws;
-    const float* fw = wop + m.cc[k] * kCell2dStride;
-    const float4 v[kCell2dSrc] = {m.win[wi - ws - 1], m.win[wi - ws], m.win[wi - 1], m.win[wi],
-                                  m.win[wi + 1],      m.win[wi + ws], m.win[wi + ws + 1]};
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int S = a.cell_S;
+  TileWalk<DIM> tk(t);
+  for (int k = threadIdx.x; k < t.own; k += kThreads, tk.next(t)) {
+    const int c = tk.cell(t, S), wi = tk.wi(t);
+    const float* fw = m.wts + m.cc[k] * CellDim<DIM>::stride;
     int e = 0;
+    if constexpr (DIM == 2) {
+      constexpr int DX[kCell2dSrc] = PFC_CELL2D_DX, DY[kCell2dSrc] = PFC_CELL2D_DY;
+      const int sx = t.sx;
+      float4 v[kCell2dSrc];
+#pragma unroll
+      for (int q = 0; q < kCell2dSrc; ++q) v[q] = m.win[wi + DY[q] * sx + DX[q]];
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #define PFC_CELL_FMA(t, q, sub)                   \
   acc[t] = fmaf(fw[e], comp4<sub>(v[q]), acc[t]); \
   ++e;
-    PFC_CELL2D_ENTRIES(PFC_CELL_FMA)
+      PFC_CELL2D_ENTRIES(PFC_CELL_FMA)
 #undef PFC_CELL_FMA
-    const float4 w1 = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    wn[c] = w1;
-    pd = dot4(w1, v[3], pd);
+      const float4 w1 = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      wn[c] = w1;
+      pd = dot4(w1, v[3], pd);
+    } else {
+      constexpr int DX[kCell3dSrc] = PFC_CELL3D_DX, DY[kCell3dSrc] = PFC_CELL3D_DY, DZ[kCell3dSrc] = PFC_CELL3D_DZ;
+      const int sx = t.sx, sxy = t.sxy;
+      float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float4 lo, hi;
+#define PFC_CELL_LOAD(q)                                        \
+  {                                                             \
+    const int wq = wi + DZ[q] * sxy + DY[q] * sx + DX[q];       \
+    lo = m.win[2 * wq];                                         \
+    hi = m.win[2 * wq + 1];                                     \
+  }
+#define PFC_CELL_FMA(t, q, sub)                       \
+  acc[t] = fmaf(fw[e], comp8<sub>(lo, hi), acc[t]);   \
+  ++e;
+      PFC_CELL3D_ENTRIES(PFC_CELL_FMA, PFC_CELL_LOAD)
+#undef PFC_CELL_FMA
+#undef PFC_CELL_LOAD
+      const float4 w0 = make_float4(acc[0], acc[1], acc[2], acc[3]), w1 = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      wn[2 * c] = w0;
+      wn[2 * c + 1] = w1;
+      pd = dot4(w0, m.win[2 * wi], pd);
+      pd = dot4(w1, m.win[2 * wi + 1], pd);
+    }
   }
 }
 
+
 // Chronopoulos-Gear Jacobi-PCG on the cell kernels (see above); same contract as pcg_cg.
-template <class TM>
+template <class TM, int DIM>
 __device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const float* DI, float* x,
                                       RhsSpec<TM, float> rhs, double rtol, int maxit, InnerCount& cnt, int& its) {
   float* const rb0 = (float*)cvec(a, kVr);
   float* const sb0 = (float*)cvec(a, kVs);
   float* const pv = (float*)cvec(a, kVp);
   const int lane = threadIdx.x & 31;
+  // this operator's weights (read after the grid sum below)
+  cell_weights(a, op);
   // r = b, x = p = s = 0 on the block's rows
   float pb = 0.f;
   FOR_MY_GROUPS(g, s0, nsl) {
@@ -1773,13 +1871,15 @@ __device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const
   const float thr = (float)(rtol * rtol * bb);
   float4* const x4 = reinterpret_cast<float4*>(x);
   const float4* const d4 = reinterpret_cast<const float4*>(DI);
-  // the Jacobi inverse of an interior row depends only on its dof type: read it at
-  // an interior row of each type, and use it for every cell of class 0 (owner and ring)
-  const float4 dint = make_float4(DI[a.cell_rep[0]], DI[a.cell_rep[1]], DI[a.cell_rep[2]], DI[a.cell_rep[3]]);
+  // the Jacobi inverse of an interior row depends only on its dof type: read it at an
+  // interior row of each type, and use it for every cell of class 0 (owner and ring)
+  const float4 d0 = make_float4(DI[a.cell_rep[0]], DI[a.cell_rep[1]], DI[a.cell_rep[2]], DI[a.cell_rep[3]]);
+  const float4 d1 = DIM == 3 ? make_float4(DI[a.cell_rep[4]], DI[a.cell_rep[5]], DI[a.cell_rep[6]], DI[a.cell_rep[7]])
+                             : d0;
   float pg = 0.f, pd = 0.f;
-  cell_fill(g, a, cvec(a, kVr), d4, dint, pg);
+  cell_fill<DIM>(a, cvec(a, kVr), d4, d0, d1, pg);
   __syncthreads();
-  cell_phase_b(g, a, op, cvec(a, cell_w(0)), pd);
+  cell_phase_b<DIM>(a, cvec(a, cell_w(0)), pd);
   if (!grid_sum<float, 2>(g, pg, pd, 0.f, red, kPhSpmv)) return false;
   float gam = red.x, del = red.y;
   if (!(del > 0.f)) {
@@ -1792,10 +1892,10 @@ __device__ __noinline__ bool pcg_cell(Grid& g, const SolveArgs& a, int op, const
     float prr = 0.f;
     pg = 0.f;
     pd = 0.f;
-    cell_phase_a(g, a, alpha, beta, cur, x4, d4, dint, prr, pg);
+    cell_phase_a<DIM>(a, alpha, beta, cur, x4, d4, d0, d1, prr, pg);
     __syncthreads();
     prof_mark(g, kPhVec);
-    cell_phase_b(g, a, op, cvec(a, cell_w(cur ^ 1)), pd);
+    cell_phase_b<DIM>(a, cvec(a, cell_w(cur ^ 1)), pd);
     if (!grid_sum<float, 3>(g, prr, pg, pd, red, kPhSpmv)) return false;
     its = it;
     if (!isfinite(red.x)) {
@@ -1829,7 +1929,10 @@ __device__ __forceinline__ bool pcg(Grid& g, Ctx<TM, TV>& c, const TM* AV, int o
   if (c.a.pcg_variant == 1) return pcg_pipelined<TM, TV>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
   if (c.a.pcg_variant == 3) {
     if constexpr (sizeof(TV) == 4) {
-      if (c.a.cells) return pcg_cell<TM>(g, c.a, op, DI, x, rhs, rtol, maxit, cnt, its);
+      if (c.a.cells) {
+        if (c.a.cell_dim == 3) return pcg_cell<TM, 3>(g, c.a, op, DI, x, rhs, rtol, maxit, cnt, its);
+        return pcg_cell<TM, 2>(g, c.a, op, DI, x, rhs, rtol, maxit, cnt, its);
+      }
       if (c.a.tma) return pcg_cg<TM, TV, true>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
     }
     return pcg_cg<TM, TV, false>(g, c.a, AV, op, DI, x, rhs, rtol, maxit, cnt, its);
@@ -2427,7 +2530,9 @@ cudaError_t launch_solve(int prec, int grid, const SolveArgs& args, cudaStream_t
   void* params[] = {&local};
   size_t dyn = (prec != 0 && args.win_cap > 0) ? (size_t)args.win_cap * sizeof(float) : 0;
   if (prec != 0 && args.tma) dyn = 2 * (size_t)args.tma_cap * sizeof(float);
-  if (prec != 0 && args.cells) dyn = cell_smem_bytes(args.cell_wcap, args.cell_rcap, args.ccls_n, args.cell_ccap);
+  if (prec != 0 && args.cells)
+    dyn = cell_smem_bytes(args.cell_wcap, args.cell_dim == 3 ? 2 : 1, args.cell_rcap, args.ccls_n,
+                          args.cell_dim == 3 ? 232 : 48, args.cell_ccap);
   cudaError_t e = allow_dyn_smem(kernel_for(prec), dyn);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(kernel_for(prec), dim3(grid), dim3(kThreads), params, dyn, stream);

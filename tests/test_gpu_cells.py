@@ -1,4 +1,4 @@
-"""Cell kernels of the float inner solves (2D P2, cell-major rows) against the oracle.
+"""Cell kernels of the float inner solves (P2, cell-major rows) against the oracle.
 
 The cell kernels run the Chronopoulos-Gear Jacobi-PCG of the P_CH inner solves
 (Table 2) with one grid barrier per iteration: each block recomputes the halo of
@@ -7,9 +7,9 @@ they give the iterates of the textbook Jacobi-PCG, so every solve is compared wi
 oracle's ``pcg_jacobi`` (float64): the float32 solve meets its residual target in the
 float64 norm (up to the float32 rounding of the iteration), takes the same number of
 iterations within 2, and lands on the same iterate to 1e-4 relative.  Stage solves
-(Eq. 3.10) meet the method's 1e-8 against the oracle.  Sizes: 2 to 32 cells per side
-(one slice per block), 256 per side at h = 0.5 (several lattice lines per block, the
-multi-line halo), and the 512^2 benchmark mesh (1.05M rows per field).
+(Eq. 3.10) meet the method's 1e-8 against the oracle.  Sizes: 2D sides 2 to 32 (tiny
+tiles), 256 at h = 0.5 and the 512^2 benchmark mesh (1.05M rows per field); 3D sides 2
+to 16 (cells of eight rows, 3D tiles and rings).
 """
 import math
 
@@ -71,6 +71,8 @@ def test_cell_kernels_run_where_they_apply():
         with pfc.PFCSolver(2, 8, 8.0, **kw) as s:
             assert not s.cell_kernels, kw
     with pfc.PFCSolver(3, 4, 4.0, precision="fp32") as s:
+        assert s.cell_kernels
+    with pfc.PFCSolver(3, 4, 4.0, precision="fp32", cells=0) as s:
         assert not s.cell_kernels
     # a single-cell mesh has no interior row: the host keeps the cell kernels off
     with pfc.PFCSolver(2, 1, 1.0, precision="fp32") as s:
@@ -170,3 +172,59 @@ def test_cell_pcg_on_the_benchmark_mesh():
             assert abs(its - ref.iterations) <= 2, (which, its, ref.iterations)
             if its == ref.iterations:
                 assert np.linalg.norm(got - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+
+
+# ---------------------------------------------------------------------------- 3D
+_probs3 = {}
+
+
+def problem3(side, L, r=-0.3):
+    key = (side, L, r)
+    if key not in _probs3:
+        _probs3[key] = PFCProblem(structured_mesh(3, side, L), r)
+    return _probs3[key]
+
+
+SIDES3 = [(4, 4.0), (2, 2.0), (7, 7.0), (16, 16.0)]
+
+
+@pytest.mark.parametrize("side,L", SIDES3, ids=[f"3d-s{s}" for s, _ in SIDES3])
+def test_cell3d_pcg_matches_oracle(side, L):
+    prob = problem3(side, L)
+    n = prob.n
+    x = np.concatenate([synth.random_vector(n, 101), synth.initial_psi(3, side, -0.35, 0.05, 1),
+                        synth.random_vector(n, 201)])
+    tau = 2.3
+    b = synth.random_vector(n, 8)
+    with pfc.PFCSolver(3, side, L, r=-0.3, precision="fp32") as s:
+        assert s.cell_kernels
+        s.assemble(cuda(x), tau)
+        for which, A in enumerate(inner_matrices(prob, tau)):
+            for rtol in (1e-3, 1e-5):
+                got, its = s.pcg(which, cuda(b), rtol)
+                got = host(got)
+                ref = pcg_jacobi(A, b, rtol, 10000)
+                res = np.linalg.norm(b - A @ got) / np.linalg.norm(b)
+                assert res <= rtol * 1.05 + 2e-6, (which, rtol, res)
+                assert abs(its - ref.iterations) <= 2, (which, rtol, its, ref.iterations)
+                if its == ref.iterations:
+                    assert np.linalg.norm(got - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("side,L,tau", [(4, 4.0, 0.1), (6, 6.0, 5.0), (2, 2.0, 1.0)],
+                         ids=["3d-s4-tau0.1", "3d-s6-tau5", "3d-s2-tau1"])
+def test_cell3d_stage_solves_match_oracle(side, L, tau, precision):
+    prob = problem3(side, L)
+    x = prob.consistent_state(synth.initial_psi(3, side, -0.35, 0.05, 1), tol=1e-15, solver="pcg")
+    A = prob.stage_matrix(x[prob.n:2 * prob.n], tau)
+    b = prob.stage_rhs(x, [], [], tau)
+    yref, ost = prob.stage_solve(A, b, tau, tol=1e-13, err_tol=1e-11)
+    assert ost.converged
+    with pfc.PFCSolver(3, side, L, r=-0.3, precision=precision) as s:
+        assert s.cell_kernels
+        s.assemble(cuda(x), tau)
+        y, st = s.stage_solve(cuda(b))
+        y = host(y)
+    err = np.linalg.norm(y - yref) / np.linalg.norm(yref)
+    assert st.status == 0 and err <= 1e-8, (err, st)
