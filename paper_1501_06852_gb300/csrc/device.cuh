@@ -116,8 +116,8 @@ struct SolveArgs {
   int cell_rep[8];         // an interior row of each dof type (its Jacobi inverse is the type's)
 };
 
-// Dynamic shared memory of the cell kernels, in this order: the window of u (U float4
-// per cell of the tile and its ring; U = 1 in 2D, 2 in 3D), the ring cells {window
+// Dynamic shared memory of the cell kernels, in this order: the window of u (U planes
+// of one float4 per cell of the tile and its ring; U = 1 in 2D, 2 in 3D), the ring cells {window
 // cell, cell or -1}, the current operator's coupling weights for every cell class
 // (stride floats per class: 48 in 2D, 232 in 3D), the classes of the tile's cells.
 __host__ __device__ inline size_t cell_off_ring(int wcap, int U) { return (size_t)wcap * U * 16; }

@@ -1580,7 +1580,8 @@ struct TileWalk {
 
 // Dynamic shared memory of the cell kernels (layout: cell_smem_bytes).
 struct CellMem {
-  float4* win;               // u: U float4 per window cell
+  float4* win;               // u: unit h of window cell j at h cell_wcap + j (planes of units,
+                             //   so that lanes reading consecutive cells read consecutive float4)
   const int2* ring;          // ring cell j: {window cell, cell index or -1 outside the grid}
   float* wts;                // the current operator's coupling weights, one row per cell class
   const unsigned char* cc;   // class of each tile cell, tile order
@@ -1620,7 +1621,7 @@ __device__ void cell_tables(const Grid& g, const SolveArgs& a) {
     const bool inside_tile = lx >= 1 && lx <= t.tw && ly >= 1 && ly <= t.th && lz >= t.wz && lz < t.wz + t.td;
     const bool in_grid = cx >= 0 && cx < S && cy >= 0 && cy < S && cz >= 0 && cz < (t.wz ? S : 1);
     if (!in_grid)
-      for (int h = 0; h < U; ++h) win[U * k + h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int h = 0; h < U; ++h) win[h * a.cell_wcap + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (!inside_tile) {
       // the order of the ring list does not matter: each ring cell is computed alone
       const int j = atomicAdd(&s_ring_n, 1);
@@ -1716,7 +1717,7 @@ __device__ __forceinline__ void cell_fill(const SolveArgs& a, const float4* r, c
     for (int h = 0; h < U; ++h) {
       const float4 rv = r[U * c + h], d = cell_d(cls, di, d0, d1, U * c + h, h);
       const float4 u = make_float4(d.x * rv.x, d.y * rv.y, d.z * rv.z, d.w * rv.w);
-      m.win[U * wi + h] = u;
+      m.win[h * a.cell_wcap + wi] = u;
       if (k < t.own) pg = dot4(rv, u, pg);
     }
   }
@@ -1743,7 +1744,7 @@ __device__ __forceinline__ void cell_phase_a(const SolveArgs& a, float al, float
       const int c = tk.cell(t, S), wi = tk.wi(t), cls = m.cc[k];
 #pragma unroll 1
       for (int h = 0; h < U; ++h) {
-        const int un = U * c + h, wu = U * wi + h;
+        const int un = U * c + h, wu = h * a.cell_wcap + wi;
         const float4 u = m.win[wu];
         const float4 p = pv[un], w = wc[un], sv = sc[un], r = rc[un], xx = x[un];
         // a cell of interior rows (class 0) has the Jacobi inverses of the interior dof types
@@ -1770,7 +1771,7 @@ __device__ __forceinline__ void cell_phase_a(const SolveArgs& a, float al, float
         const float4 w = wc[un], sv = sc[un], r = rc[un], d = cell_d(cls, di, d0, d1, un, h);
         float4 s1, r1, u1;
         cell_rsu(w, sv, r, d, al, be, s1, r1, u1);
-        m.win[U * rg.x + h] = u1;
+        m.win[h * a.cell_wcap + rg.x] = u1;
       }
     }
   }
@@ -1807,14 +1808,14 @@ __device__ __forceinline__ void cell_phase_b(const SolveArgs& a, float4* wn, flo
       pd = dot4(w1, v[3], pd);
     } else {
       constexpr int DX[kCell3dSrc] = PFC_CELL3D_DX, DY[kCell3dSrc] = PFC_CELL3D_DY, DZ[kCell3dSrc] = PFC_CELL3D_DZ;
-      const int sx = t.sx, sxy = t.sxy;
+      const int sx = t.sx, sxy = t.sxy, wcap = a.cell_wcap;
       float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       float4 lo, hi;
 #define PFC_CELL_LOAD(q)                                        \
   {                                                             \
     const int wq = wi + DZ[q] * sxy + DY[q] * sx + DX[q];       \
-    lo = m.win[2 * wq];                                         \
-    hi = m.win[2 * wq + 1];                                     \
+    lo = m.win[wq];                                             \
+    hi = m.win[wcap + wq];                                      \
   }
 #define PFC_CELL_FMA(t, q, sub)                       \
   acc[t] = fmaf(fw[e], comp8<sub>(lo, hi), acc[t]);   \
@@ -1825,8 +1826,8 @@ __device__ __forceinline__ void cell_phase_b(const SolveArgs& a, float4* wn, flo
       const float4 w0 = make_float4(acc[0], acc[1], acc[2], acc[3]), w1 = make_float4(acc[4], acc[5], acc[6], acc[7]);
       wn[2 * c] = w0;
       wn[2 * c + 1] = w1;
-      pd = dot4(w0, m.win[2 * wi], pd);
-      pd = dot4(w1, m.win[2 * wi + 1], pd);
+      pd = dot4(w0, m.win[wi], pd);
+      pd = dot4(w1, m.win[wcap + wi], pd);
     }
   }
 }
