@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -746,28 +747,33 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
     pfc::SolveArgs* hargs = (pfc::SolveArgs*)(hbase + off);
     int* hseg = (int*)(hbase + off + sizeof(pfc::SolveArgs) * n);
     hseg[0] = 0;
-    // cell kernels: the wave's dynamic shared memory holds the widest block window of
-    // every instance in its segment partition; if that lowers the residency the wave
-    // needs, the wave's instances take the global-memory form instead
+    // cell kernels: the wave's dynamic shared memory holds the widest tile window among
+    // the instances that can have one at the residency the wave needs (in their segment
+    // partition); an instance whose window does not fit takes the per-warp form
+    std::vector<size_t> needs(n, 0);
     size_t dyn = 0;
-    bool cells_fit = true;
     {
       for (int i = 0; i < n; ++i) {
         pfc_ctx* ck = ctxs[wv.first + i];
         if (!(ck->prec != 0 && ck->cell_ok)) continue;
-        int gx = 0, gy = 0, wcap = 0, ccap = 0, rcap = 0;
-        int gz = 0;
+        int gx = 0, gy = 0, gz = 0, wcap = 0, ccap = 0, rcap = 0;
         cell_tiling(ck->dim, ck->cell_S, Gs[wv.first + i], gx, gy, gz, wcap, ccap, rcap);
-        dyn = std::max(dyn, pfc::cell_smem_bytes(wcap, ck->dim == 3 ? 2 : 1, rcap, ck->ccls_n,
-                                                 ck->dim == 3 ? 232 : 48, ccap));
+        needs[i] = pfc::cell_smem_bytes(wcap, ck->dim == 3 ? 2 : 1, rcap, ck->ccls_n, ck->dim == 3 ? 232 : 48, ccap);
       }
-      if (dyn > 0) {
-        int occ_c = 0, blocks = 0;
-        for (int i = 0; i < n; ++i) blocks += Gs[wv.first + i];
-        const int need = (blocks + sms - 1) / sms;
-        cells_fit = pfc::batch_occupancy(c0->prec, &occ_c, dyn) == cudaSuccess && occ_c >= need;
+      std::vector<size_t> cand(needs.begin(), needs.end());
+      std::sort(cand.begin(), cand.end(), std::greater<size_t>());
+      int blocks = 0;
+      for (int i = 0; i < n; ++i) blocks += Gs[wv.first + i];
+      const int need_bps = (blocks + sms - 1) / sms;
+      for (size_t k = 0; k < cand.size() && cand[k] > 0; ++k) {
+        if (k > 0 && cand[k] == cand[k - 1]) continue;
+        int occ_c = 0;
+        const bool ok = pfc::batch_occupancy(c0->prec, &occ_c, cand[k]) == cudaSuccess && occ_c >= need_bps;
         cudaGetLastError();
-        if (!cells_fit) dyn = 0;
+        if (ok) {
+          dyn = cand[k];
+          break;
+        }
       }
     }
     for (int i = 0; i < n; ++i) {
@@ -782,7 +788,7 @@ pfc_status run_batch(pfc_ctx* const* ctxs_in, int count, int slot, bool to_tmp, 
       a.y = to_tmp ? ck->tmp3 : ck->ys + (size_t)sk * 3 * ck->n_pad;
       a.blk = ck->blk_b;
       if (a.cells) {
-        if (cells_fit)
+        if (needs[i] > 0 && needs[i] <= dyn)
           cell_tiling(ck->dim, ck->cell_S, Gs[wv.first + i], a.cell_gx, a.cell_gy, a.cell_gz, a.cell_wcap,
                       a.cell_ccap, a.cell_rcap);
         else a.cells = 0;
