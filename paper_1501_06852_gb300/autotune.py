@@ -4,7 +4,10 @@ For a problem class (dimension, side, inner precision) it times the inner solve
 of each candidate configuration on the device and keeps the fastest:
 
 * ``inner_operator``: assembled SELL-32 values and indices, or structured stencils;
-* ``pcg_variant``: textbook, pipelined or Chronopoulos-Gear Jacobi-PCG.
+* ``pcg_variant``: textbook, pipelined or Chronopoulos-Gear Jacobi-PCG;
+* ``cells`` (structured stencils, Chronopoulos-Gear, float inner solves): the cell
+  kernels (one grid barrier per iteration, rings recomputed in shared memory) or the
+  per-warp form in lexicographic rows.
 
 (The persistent kernel runs 1024-thread blocks, one per SM, so the grid's
 residency is not a candidate.)
@@ -32,7 +35,13 @@ _CACHE: dict = {}
 
 def candidates(precision: str):
     variants = (0, 1, 3) if precision == "fp64" else (0, 3)
-    return [dict(inner_operator=io, pcg_variant=v) for io, v in itertools.product((0, 1), variants)]
+    out = []
+    for io, v in itertools.product((0, 1), variants):
+        if precision != "fp64" and io == 1 and v == 3:
+            out += [dict(inner_operator=io, pcg_variant=v, cells=1), dict(inner_operator=io, pcg_variant=v, cells=0)]
+        else:
+            out.append(dict(inner_operator=io, pcg_variant=v, cells=0))
+    return out
 
 
 def size_class(side: int) -> int:
